@@ -1,0 +1,366 @@
+"""Benchmark: VM-steps/s of the batched word RASP on GB300.
+
+Workload (default): 1,048,576 template programs of 64 instructions (straight-
+line arithmetic plus 1..3 counter-bounded loops, trips U[1,64]), n = 256
+int64 words, 16-word input tapes U[-1000,1000], step cap 4096, seed 2.
+
+One timed step = re-pack c_0 for every VM from the device-resident programs
+and tapes (k_pack) + rasp_run to completion (k_persist): the whole hot path
+on inputs already in HBM. M alone is 2 GiB, far larger than L2, so no flush is
+needed between steps. `e2e` times the same work through the C ABI with host
+buffers: rasp_load_programs + rasp_load_inputs from pinned host memory,
+rasp_run, rasp_read_state of the per-VM results (i, a, steps, status, heads,
+y). `roofline` rates the persistent kernel's algorithmic bytes (bytes of VM
+state each executed opcode touches, weighted by the measured opcode mix)
+against the measured HBM copy bandwidth. `cpu_baseline` is the serial C
+oracle on a time-bounded prefix of the same workload.
+
+Multi-GPU (torchrun): every rank runs its own disjoint 2^20-VM shard (no
+collective on the data path); value = all ranks' steps / max rank time.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "VM-steps/sec on 1 GB300 (and % of HBM roofline) vs plain form and CPU oracle"
+UNIT = "VM-steps/s"
+# bytes of VM state touched per executed step, by opcode (fetch 16 B; an M
+# operand read or write 8 B; RD reads a tape word and writes M; PRI reads M
+# and, when y has room, writes y)
+BYTES_PER_OP = {1: 16, 2: 24, 3: 24, 4: 24, 5: 16, 6: 32, 7: 32}
+PRI_FULL_BYTES = 24
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.Q,
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.th = threading.Thread(target=self._read, daemon=True)
+            self.th.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if not self.proc:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx.append(float(parts[2]))
+            except ValueError:
+                continue
+            for k, nm in enumerate(names):
+                if parts[5 + k].lower() == "active":
+                    reasons.add(nm)
+        if not sm:
+            return None
+        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": float(max(mx)),
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def make_workload(name: str, rank: int):
+    from paper_2604_12902_gb300 import workloads as W
+    if name == "templates":
+        return W.template_programs(num_vms=1 << 20, seed=2, first_vm=rank << 20), \
+            "1,048,576 template programs (64 instr, 1-3 loops, trips U[1,64]), n=256, l=16, s=8, cap 4096"
+    if name == "random":
+        return W.random_programs(num_vms=1024, seed=1, first_vm=rank * 1024), \
+            "1,024 random programs (32 instr, opcodes U{1..7}, operands U[0,63]), n=64, l=4, s=8, cap 256"
+    raise SystemExit("unknown workload %s" % name)
+
+
+def algorithmic_bytes(stats) -> float:
+    ops = stats["op_steps"]
+    b = sum(BYTES_PER_OP[k] * ops[k] for k in range(1, 8))
+    b -= (BYTES_PER_OP[7] - PRI_FULL_BYTES) * stats["pri_full"]
+    return float(b)
+
+
+def cpu_baseline(wl, budget_s: float = 15.0, threads: int = 1):
+    """The serial oracle on a prefix of the workload, chunk by chunk until
+    `budget_s` seconds have passed."""
+    from oracle import oracle
+    chunk = 8192
+    done_vms, steps, t_used = 0, 0, 0.0
+    while done_vms < wl.num_vms and t_used < budget_s:
+        hi = min(wl.num_vms, done_vms + chunk)
+        sub = wl.subset(np.arange(done_vms, hi))
+        t0 = time.perf_counter()
+        st, _ = oracle.run_packed(sub.programs, sub.prog_off, sub.mem_words, sub.tapes, sub.tape_off,
+                                  sub.ell, sub.s, caps=sub.caps, threads=threads)
+        t_used += time.perf_counter() - t0
+        steps += int(st.steps.sum())
+        done_vms = hi
+    return {"value": steps / t_used, "unit": UNIT, "cores": threads, "kind": "oracle",
+            "sample": "first %d of %d VMs (%d VM-steps, pack+run, %.1f s)" % (done_vms, wl.num_vms, steps, t_used)}
+
+
+def run_reference(args, ws, rank):
+    """Reference arm: the CPU oracle as it stands, on bounded samples."""
+    if rank != 0:
+        return
+    from oracle import oracle
+    wl, desc = make_workload(args.workload, 0)
+    threads = os.cpu_count() or 1
+    sample = min(wl.num_vms, 1 << 16)
+    sub = wl.subset(np.arange(sample))
+    times, steps = [], 0
+    for it in range(args.warmup + args.steps):
+        t0 = time.perf_counter()
+        st, _ = oracle.run_packed(sub.programs, sub.prog_off, sub.mem_words, sub.tapes, sub.tape_off,
+                                  sub.ell, sub.s, caps=sub.caps, threads=threads)
+        dt = time.perf_counter() - t0
+        if it >= args.warmup:
+            times.append(dt)
+            steps += int(st.steps.sum())
+    value = steps / sum(times)
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": 1,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * sum(times) / len(times),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int64",
+            "data": "synthetic", "config": {"workload": desc + " (first %d VMs per step)" % sample},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": threads, "kind": "oracle",
+                             "sample": "first %d VMs, pack+run, %d threads" % (sample, threads)},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--workload", default="templates", choices=["templates", "random"])
+    ap.add_argument("--flags", type=lambda x: int(x, 0), default=0, help="rasp_config.flags (schedule)")
+    ap.add_argument("--epoch", type=int, default=0)
+    ap.add_argument("--no-cpu", action="store_true", help="skip the CPU-oracle baseline")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-plain", action="store_true")
+    ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    args = ap.parse_args()
+    ws, rank, local = dist_env()
+    if args.impl == "reference":
+        run_reference(args, ws, rank)
+        return
+    if args.warmup < 3:
+        args.warmup = 3
+    import torch
+    torch.cuda.set_device(local)
+    dist = None
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    from paper_2604_12902_gb300 import rasp as R
+
+    wl, desc = make_workload(args.workload, rank)
+    stream = torch.cuda.current_stream()
+    b = R.Batch(wl.mem_words, wl.ell, wl.s, flags=args.flags, epoch=args.epoch)
+    b.load_workload(wl)
+
+    # opcode mix (and total steps) from an untimed counting run
+    with R.Batch(wl.mem_words, wl.ell, wl.s, flags=args.flags | R.COLLECT_STATS, epoch=args.epoch) as bs:
+        bs.load_workload(wl)
+        bs.run()
+        stats = bs.stats()
+    total_steps = stats["vm_steps"]
+    alg_bytes = algorithmic_bytes(stats)
+
+    def step(evs=None):
+        if evs:
+            evs[0].record(stream)
+        b.reset()
+        if evs:
+            evs[1].record(stream)
+        b.run()
+        if evs:
+            evs[2].record(stream)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    evs = [[torch.cuda.Event(enable_timing=True) for _ in range(3)] for _ in range(args.steps)]
+    clk = ClockSampler(torch.cuda.current_device())
+    clk.start()
+    time.sleep(0.3)
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    t_start = torch.cuda.Event(enable_timing=True)
+    t_end = torch.cuda.Event(enable_timing=True)
+    t_start.record(stream)
+    for k in range(args.steps):
+        step(evs[k])
+    t_end.record(stream)
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    clocks = clk.stop()
+    elapsed_ms = t_start.elapsed_time(t_end)
+    run_ms = [e[1].elapsed_time(e[2]) for e in evs]
+    pack_ms = [e[0].elapsed_time(e[1]) for e in evs]
+    b.sync()
+    st = b.stats()
+    assert st["vm_steps"] == total_steps, "timed runs disagree with the counting run"
+
+    ms_total = torch.tensor([elapsed_ms], device="cuda")
+    steps_total = torch.tensor([float(total_steps)], device="cuda", dtype=torch.float64)
+    if dist:
+        dist.all_reduce(ms_total, op=dist.ReduceOp.MAX)
+        dist.all_reduce(steps_total, op=dist.ReduceOp.SUM)
+    ms_per_step = float(ms_total.item()) / args.steps
+    value = float(steps_total.item()) / (ms_per_step * 1e-3)
+
+    hbm, peak_kind = peaks()
+    run_avg = float(np.mean(run_ms))
+    achieved = alg_bytes / (run_avg * 1e-3) / 1e9
+    roofline = {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
+                "frac": achieved / hbm, "traffic": None,
+                "kernel": "k_persist", "peak_kind": peak_kind,
+                "bytes_per_step": alg_bytes / max(total_steps, 1),
+                "kernel_ms": run_avg, "pack_ms": float(np.mean(pack_ms))}
+
+    # plain one-launch-per-batch form on the same workload (untimed by the contract)
+    plain = None
+    if not args.no_plain:
+        with R.Batch(wl.mem_words, wl.ell, wl.s, flags=R.SCHED_PLAIN) as bp:
+            bp.load_workload(wl)
+            bp.run()
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            ts = []
+            for _ in range(3):
+                bp.reset()
+                e0.record(stream)
+                bp.run()
+                e1.record(stream)
+                torch.cuda.synchronize()
+                ts.append(e0.elapsed_time(e1))
+            plain = {"value": total_steps / (np.median(ts) * 1e-3), "unit": UNIT, "kernel_ms": float(np.median(ts)),
+                     "persistent_speedup": float(np.median(ts)) / run_avg}
+
+    # end to end through the C ABI with host buffers
+    e2e = None
+    if not args.no_e2e:
+        pin = lambda a: _pinned_copy(torch, a)
+        h_prog, h_poff = pin(wl.programs), pin(wl.prog_off)
+        h_tape, h_toff, h_caps = pin(wl.tapes), pin(wl.tape_off), pin(wl.caps)
+        out = {k: pin(np.empty(wl.num_vms, dt)) for k, dt in
+               (("i", np.int64), ("a", np.int64), ("steps", np.uint64), ("status", np.uint8),
+                ("uhead", np.uint32), ("ylen", np.uint32))}
+        out["y"] = pin(np.empty(wl.num_vms * wl.s, np.int64))
+        h2d = sum(x.nbytes for x in (h_prog, h_poff, h_tape, h_toff, h_caps))
+        d2h = sum(x.nbytes for x in out.values())
+        view = R.rasp_state_view(*(R._p(out[k]) for k in ("i", "a", "steps", "status", "uhead", "ylen", "y")),
+                                 None, 0)
+
+        def e2e_step():
+            R.rasp_load_programs(b.h, h_prog, h_poff)
+            R.rasp_load_inputs(b.h, h_tape, h_toff, h_caps)
+            R.rasp_run(b.h)
+            R.rasp_read_state(b.h, 0, wl.num_vms, view)
+
+        for _ in range(2):
+            e2e_step()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        n_e2e = max(3, args.steps // 2)
+        for _ in range(n_e2e):
+            e2e_step()
+        torch.cuda.synchronize()
+        dt = (time.perf_counter() - t0) / n_e2e
+        assert int(out["steps"].sum()) == total_steps
+        e2e_val = total_steps / dt
+        if dist:
+            t = torch.tensor([dt], device="cuda")
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            e2e_val = float(steps_total.item()) / float(t.item())
+        e2e = {"value": e2e_val, "unit": UNIT, "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h),
+               "ms_per_step": dt * 1e3}
+
+    cpu = None
+    if rank == 0 and ws == 1 and not args.no_cpu:
+        cpu = cpu_baseline(wl, args.cpu_seconds)
+    b.close()
+
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": "int64", "data": "synthetic",
+                "config": {"workload": desc, "vms_per_gpu": wl.num_vms, "vm_steps_per_gpu": total_steps,
+                           "l2": "inputs larger than L2 (M = %.1f GiB)" % (wl.num_vms * 256 * 8 / 2 ** 30
+                                                                          if args.workload == "templates" else 0.0),
+                           "schedule_flags": args.flags, "parallelism": "vm shards x%d" % ws},
+                "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "plain": plain,
+                "gpu_launches": 2 * args.steps, "clocks": clocks}
+        print(json.dumps(line), flush=True)
+    if dist:
+        dist.destroy_process_group()
+
+
+_PINNED = []
+
+
+def _pinned_copy(torch, a):
+    """A copy of `a` in page-locked host memory (kept alive for the run)."""
+    t = torch.empty(max(a.nbytes, 1), dtype=torch.uint8, pin_memory=True)
+    _PINNED.append(t)
+    arr = t.numpy()[: a.nbytes].view(a.dtype).reshape(a.shape)
+    arr[...] = a
+    return arr
+
+
+if __name__ == "__main__":
+    main()

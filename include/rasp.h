@@ -1,0 +1,193 @@
+/*
+ * rasp.h -- C ABI of the GB300 batched word-RASP engine (librasp_gb300.so).
+ *
+ * The engine advances many independent word-RASP machines
+ *     c = <i, a, M, u, y>  in  C_w = W x W x W^n x W^(l+1) x W^(s+1)
+ * ("Towards a Linear-Algebraic Hypervisor", Sec. 2.1) through the one-step
+ * transition of Sec. 2.1 until each reaches a fixed point (F = {c : c -> c})
+ * or its step cap -- the vectorised map Phi of Sec. 2 iterated on the GPU.
+ *
+ * Conventions shared by every call:
+ *  - Return value: RASP_OK (0) or a negative rasp_err. Nothing throws across
+ *    the ABI. rasp_last_error() returns a thread-local message describing the
+ *    last failure on the calling thread.
+ *  - Words are int64 two's complement; the machine treats them as w-bit
+ *    vectors (Sec. 2.1, W = F_2^w), so "x mod n" uses the unsigned value.
+ *  - Host pointers passed in are read before the call returns; the library
+ *    keeps no reference to them. Device memory belongs to the batch, or is
+ *    carved from the caller's arena (rasp_config.arena) which the caller owns
+ *    and must keep alive until rasp_batch_destroy.
+ *  - All device work of a batch is ordered on rasp_config.stream. rasp_run is
+ *    asynchronous; rasp_read_state, rasp_read_stats and rasp_sync synchronise
+ *    that stream.
+ *  - VM outcomes (halt, timeout, fault) are status values, never errors.
+ */
+#ifndef RASP_GB300_RASP_H
+#define RASP_GB300_RASP_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- error codes ------------------------------------------------------- */
+enum rasp_err {
+    RASP_OK = 0,
+    RASP_EINVAL = -1,    /* bad argument (see each call)                     */
+    RASP_ENOMEM = -2,    /* device memory (or the arena) too small            */
+    RASP_ECUDA = -3,     /* a CUDA call failed; message in rasp_last_error    */
+    RASP_ESTATE = -4,    /* call out of order (e.g. rasp_run before loads)    */
+    RASP_EDEVICE = -5    /* a kernel reported an internal error (bounded wait
+                            expired); the batch state is not trustworthy      */
+};
+
+/* ---- VM status (per machine) -------------------------------------------- */
+enum rasp_status {
+    RASP_RUNNING = 0,        /* neither halted nor out of steps              */
+    RASP_HALTED = 1,         /* configuration is a fixed point (Sec. 2.1 F)  */
+    RASP_TIMEOUT = 2,        /* steps == cap without reaching F              */
+    RASP_FAULT_OVERFLOW = 3, /* CHECKED only: signed overflow in ADD or MUL  */
+    RASP_FAULT_ADDR = 4      /* CHECKED only: fetch or operand out of [0, n) */
+};
+
+/* ---- semantics ---------------------------------------------------------- */
+enum rasp_semantics {
+    RASP_WRAP = 0,    /* the paper's machine: arithmetic mod 2^w, circular
+                         memory (Sec. 2.1); never faults                      */
+    RASP_CHECKED = 1  /* no counterpart in the paper: w must be 64; memory is
+                         not circular and ADD/MUL are signed 64-bit. Per step,
+                         in order: fetch needs 0 <= i < n-1 (else FAULT_ADDR);
+                         a fixed point halts; ADD, MUL, STO, PRI and a firing
+                         RD need 0 <= j < n (else FAULT_ADDR); ADD/MUL signed
+                         overflow gives FAULT_OVERFLOW. A faulting step is not
+                         applied and not counted.                           */
+};
+
+/* ---- flags -------------------------------------------------------------- */
+#define RASP_SCHED_AUTO        0x00u  /* autotuned choice per memory bucket   */
+#define RASP_SCHED_PLAIN       0x10u  /* one thread per VM, state in HBM      */
+#define RASP_SCHED_PERSIST     0x20u  /* persistent workers, M staged in SMEM */
+#define RASP_SCHED_PERSIST_GL  0x30u  /* persistent workers, M in HBM via L1  */
+#define RASP_SCHED_MASK        0xF0u
+#define RASP_DISPATCH_SELECT   0x000u /* branch-free guarded-sum step         */
+#define RASP_DISPATCH_VOTE     0x100u /* warp opcode voting, one handler/group */
+#define RASP_COLLECT_STATS     0x1000u /* count executed steps per opcode      */
+#define RASP_SHARED_PROGRAM    0x2000u /* programs indexed by prog_of_vm       */
+
+typedef struct rasp_config {
+    uint32_t word_bits;  /* w, 2..64 (64 for RASP_CHECKED)                     */
+    uint32_t semantics;  /* enum rasp_semantics                                */
+    uint32_t in_cap;     /* l: input tape capacity (u holds l+1 words)         */
+    uint32_t out_cap;    /* s: output capacity (y holds s+1 words)             */
+    uint32_t flags;      /* RASP_SCHED_* | RASP_DISPATCH_* | RASP_COLLECT_STATS */
+    uint32_t epoch;      /* steps between warp scheduling points; 0 = default  */
+    void*    stream;     /* cudaStream_t for all work of the batch; NULL = the
+                            legacy default stream                              */
+    void*    arena;      /* optional caller-owned device memory for the batch;
+                            NULL = the library allocates with cudaMalloc       */
+    uint64_t arena_bytes;/* size of arena (see rasp_batch_bytes)               */
+} rasp_config;
+
+typedef struct rasp_batch rasp_batch;   /* opaque */
+
+/* Host-side view of machine state for reading and restoring.
+ * Arrays are indexed by VM within the requested range [first, first+count).
+ * Any pointer may be NULL to skip that field. */
+typedef struct rasp_state_view {
+    int64_t*  i;        /* [count] instruction counter (full w-bit word)      */
+    int64_t*  a;        /* [count] accumulator                                */
+    uint64_t* steps;    /* [count] applied transitions (= tau_h when halted)  */
+    uint8_t*  status;   /* [count] enum rasp_status                           */
+    uint32_t* uhead;    /* [count] u_0, the input read head                   */
+    uint32_t* ylen;     /* [count] y_0, the output count                      */
+    int64_t*  y;        /* [count * out_cap] y_1..y_s of each VM              */
+    int64_t*  mem;      /* M of the VMs, concatenated in VM order (n_v words
+                           each); NULL to skip                                */
+    uint64_t  mem_words;/* capacity of mem in words (checked)                 */
+} rasp_state_view;
+
+typedef struct rasp_stats {
+    uint64_t vm_steps;      /* sum of steps over all VMs                       */
+    uint64_t running, halted, timeout, fault_overflow, fault_addr;
+    uint64_t op_steps[8];   /* applied steps per opcode 1..7 (index 0 unused);
+                               only with RASP_COLLECT_STATS                    */
+    uint64_t pri_full;      /* PRI steps that found y full (same condition)   */
+    uint64_t bnz_taken;     /* taken BNZ steps (same condition)               */
+    uint64_t launches;      /* kernel launches of the last rasp_run            */
+} rasp_stats;
+
+/* Bytes of device memory a batch needs (for sizing rasp_config.arena).
+ * Same argument rules as rasp_batch_create. */
+int rasp_batch_bytes(const rasp_config* cfg, uint64_t num_vms,
+                     const uint32_t* mem_words, uint64_t* out_bytes);
+
+/* Create a batch of num_vms machines; mem_words[v] = n of VM v (>= 1).
+ * Allocates the structure-of-arrays state store (i, a, steps, cap, status,
+ * u_0, y_0 per VM), the per-VM M slabs, the tapes and outputs, and buckets
+ * the VMs by n for scheduling. No machine is runnable until both
+ * rasp_load_programs and rasp_load_inputs have been called.
+ * EINVAL: cfg NULL, w outside 2..64, CHECKED with w != 64, num_vms 0 or
+ * >= 2^32, some n = 0 or n >= 2^31. ENOMEM: allocation or arena too small. */
+int rasp_batch_create(const rasp_config* cfg, uint64_t num_vms,
+                      const uint32_t* mem_words, rasp_batch** out);
+
+/* Load programs and pack M = P 0^(n-2m) for every VM (c_0, Sec. 2.1).
+ * words: flat program words; offsets[num_programs+1] delimit program p.
+ * prog_of_vm: NULL (then num_programs must equal num_vms and VM v runs
+ * program v) or [num_vms] program index per VM (one program shared by many
+ * VMs, e.g. a rollout of one candidate over many inputs).
+ * Resets i = a = 0, steps = 0, status = RUNNING, u_0 = y_0 = 0, y = 0.
+ * EINVAL: odd program length, 2m > n of a VM using it, bad index. */
+int rasp_load_programs(rasp_batch* b, const int64_t* words,
+                       const uint64_t* offsets, uint64_t num_programs,
+                       const uint32_t* prog_of_vm);
+
+/* Load input tapes x (u = [0, x, 0^(l-|x|)], Sec. 2.1) and per-VM step
+ * caps. tape/offsets[num_vms+1] as for programs; caps NULL = no cap
+ * (UINT64_MAX). Resets u_0 = 0. EINVAL: |x| > l. */
+int rasp_load_inputs(rasp_batch* b, const int64_t* tape,
+                     const uint64_t* offsets, const uint64_t* caps);
+
+/* Re-pack c_0 for every VM from the programs and inputs already loaded
+ * (device-side; no host copy). ESTATE if either is missing. */
+int rasp_reset(rasp_batch* b);
+
+/* Advance every RUNNING machine until it halts (fixed point), faults, or has
+ * taken min(max_steps, cap_v) steps in total. steps is cumulative, so
+ * rasp_run(T1) followed by rasp_run(T2) equals rasp_run(T2). A VM that stops
+ * on the budget (max_steps < cap) stays RUNNING unless it is a fixed point.
+ * Asynchronous on the batch stream. ESTATE before both loads. */
+int rasp_run(rasp_batch* b, uint64_t max_steps);
+
+/* Wait for the batch stream; EDEVICE if a kernel flagged an internal error. */
+int rasp_sync(rasp_batch* b);
+
+/* Copy state of VMs [first, first+count) into caller-owned host arrays
+ * (synchronises the stream). EINVAL: range outside the batch, mem too small. */
+int rasp_read_state(rasp_batch* b, uint64_t first, uint64_t count,
+                    rasp_state_view* out);
+
+/* Overwrite state of VMs [first, first+count) from host arrays (checkpoint
+ * restore). NULL fields are left unchanged. EINVAL: u_0 > l, y_0 > s,
+ * status outside the enum, mem too small. */
+int rasp_load_state(rasp_batch* b, uint64_t first, uint64_t count,
+                    const rasp_state_view* in);
+
+/* Aggregate counters of the batch (synchronises the stream). */
+int rasp_read_stats(rasp_batch* b, rasp_stats* out);
+
+/* Free the batch (synchronises its stream first). NULL is a no-op. */
+void rasp_batch_destroy(rasp_batch* b);
+
+/* Thread-local description of the last error on this thread ("" if none). */
+const char* rasp_last_error(void);
+
+/* Library version string. */
+const char* rasp_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* RASP_GB300_RASP_H */

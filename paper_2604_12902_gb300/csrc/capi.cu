@@ -1,0 +1,606 @@
+// capi.cu -- the C ABI of include/rasp.h: batch state store, loading of
+// programs and tapes (c_0 of Sec. 2.1), scheduling by memory-size bucket,
+// read-back and checkpoint restore.
+#include <algorithm>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <numeric>
+#include <string>
+#include <vector>
+
+#include "../../include/rasp.h"
+#include "engine.cuh"
+#include "internal.h"
+
+using namespace rasp;
+
+namespace {
+
+thread_local std::string g_err;
+
+int fail(int code, const char* fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof(buf), fmt, ap);
+  va_end(ap);
+  g_err = buf;
+  return code;
+}
+
+#define CK(call)                                                                         \
+  do {                                                                                   \
+    cudaError_t e_ = (call);                                                             \
+    if (e_ != cudaSuccess) return fail(RASP_ECUDA, "%s: %s", #call, cudaGetErrorString(e_)); \
+  } while (0)
+
+constexpr size_t ALIGN = 256;
+inline size_t align_up(size_t x) { return (x + ALIGN - 1) & ~(ALIGN - 1); }
+
+// Memory-size buckets: VMs whose n falls in the same class share a slot size.
+constexpr uint32_t kBucketBounds[] = {64, 128, 256, 512, 768, 1024, 2048, 4096, 1u << 31};
+constexpr int kNumBuckets = sizeof(kBucketBounds) / sizeof(kBucketBounds[0]);
+
+struct Bucket {
+  uint32_t first = 0;      // position in the id list
+  uint32_t count = 0;
+  uint32_t ncap = 0;       // largest padded n in the bucket
+  uint32_t sched = 0;      // RASP_SCHED_PLAIN / PERSIST / PERSIST_GL
+  PersistShape shape{};
+};
+
+struct Layout {
+  size_t off_i, off_a, off_steps, off_cap, off_status, off_uhead, off_ylen, off_n, off_memoff;
+  size_t off_mem, off_prog, off_progoff, off_progvm, off_tape, off_y, off_ids, off_heads, off_err,
+      off_hist, off_stats;
+  size_t total;
+};
+
+}  // namespace
+
+struct rasp_batch {
+  rasp_config cfg{};
+  cudaStream_t stream = nullptr;
+  uint32_t V = 0;
+  uint32_t ell = 0, s = 0, ellp = 0, sp = 0;
+  uint64_t wmask = ~0ull;
+  std::vector<uint32_t> h_n;
+  std::vector<uint64_t> h_memoff;
+  uint64_t mem_words = 0;      // sum of padded n
+  Layout L{};
+  char* base = nullptr;
+  bool owns = false;
+  DevState S{};
+  uint64_t* d_prog = nullptr;
+  uint64_t* d_progoff = nullptr;
+  uint32_t* d_progvm = nullptr;
+  uint32_t* d_ids = nullptr;
+  uint32_t* d_heads = nullptr;
+  int* d_err = nullptr;
+  unsigned long long* d_hist = nullptr;
+  unsigned long long* d_stats = nullptr;
+  uint64_t* d_cap = nullptr;
+  bool shared_programs = false;
+  bool programs_loaded = false, inputs_loaded = false;
+  std::vector<uint32_t> h_ids;  // bucket-ordered VM ids
+  std::vector<Bucket> buckets;
+  uint64_t launches = 0;
+};
+
+namespace {
+
+int validate_config(const rasp_config* cfg, uint64_t num_vms, const uint32_t* mem_words) {
+  if (!cfg) return fail(RASP_EINVAL, "config is NULL");
+  if (cfg->word_bits < 2 || cfg->word_bits > 64) return fail(RASP_EINVAL, "word_bits must be in 2..64");
+  if (cfg->semantics != RASP_WRAP && cfg->semantics != RASP_CHECKED)
+    return fail(RASP_EINVAL, "unknown semantics %u", cfg->semantics);
+  if (cfg->semantics == RASP_CHECKED && cfg->word_bits != 64)
+    return fail(RASP_EINVAL, "CHECKED semantics needs word_bits = 64");
+  if (num_vms == 0 || num_vms >= (1ull << 32)) return fail(RASP_EINVAL, "num_vms must be in 1..2^32-1");
+  if (!mem_words) return fail(RASP_EINVAL, "mem_words is NULL");
+  const uint32_t sched = cfg->flags & RASP_SCHED_MASK;
+  if (sched != RASP_SCHED_AUTO && sched != RASP_SCHED_PLAIN && sched != RASP_SCHED_PERSIST &&
+      sched != RASP_SCHED_PERSIST_GL)
+    return fail(RASP_EINVAL, "unknown schedule flag 0x%x", sched);
+  if (cfg->word_bits < 64) {
+    const uint64_t lim = 1ull << cfg->word_bits;
+    if (cfg->in_cap >= lim || cfg->out_cap >= lim)
+      return fail(RASP_EINVAL, "l and s must be representable in w bits");
+  }
+  for (uint64_t v = 0; v < num_vms; ++v)
+    if (mem_words[v] == 0 || mem_words[v] >= (1u << 31))
+      return fail(RASP_EINVAL, "mem_words[%llu] = %u is outside 1..2^31-1", (unsigned long long)v, mem_words[v]);
+  return RASP_OK;
+}
+
+Layout make_layout(uint64_t V, uint64_t mem_words, uint32_t ellp, uint32_t sp) {
+  Layout L{};
+  size_t o = 0;
+  auto take = [&](size_t bytes) {
+    size_t r = o;
+    o = align_up(o + bytes);
+    return r;
+  };
+  L.off_i = take(8 * V);
+  L.off_a = take(8 * V);
+  L.off_steps = take(8 * V);
+  L.off_cap = take(8 * V);
+  L.off_status = take(V);
+  L.off_uhead = take(4 * V);
+  L.off_ylen = take(4 * V);
+  L.off_n = take(4 * V);
+  L.off_memoff = take(8 * V);
+  L.off_mem = take(8 * mem_words);
+  L.off_prog = take(8 * mem_words);           // programs never exceed the M arena
+  L.off_progoff = take(8 * (V + 1));
+  L.off_progvm = take(4 * V);
+  L.off_tape = take(8 * V * (uint64_t)ellp);
+  L.off_y = take(8 * V * (uint64_t)sp);
+  L.off_ids = take(4 * V);
+  L.off_heads = take(4 * kNumBuckets);
+  L.off_err = take(16);
+  L.off_hist = take(8 * 10);
+  L.off_stats = take(8 * 6);
+  L.total = o;
+  return L;
+}
+
+uint32_t even(uint32_t x) { return (x + 1u) & ~1u; }
+
+StepVariant variant_of(const rasp_batch* b) {
+  StepVariant v{};
+  v.masked = b->cfg.word_bits < 64;
+  v.checked = b->cfg.semantics == RASP_CHECKED;
+  v.hist = (b->cfg.flags & RASP_COLLECT_STATS) != 0;
+  v.vote = (b->cfg.flags & RASP_DISPATCH_VOTE) != 0;
+  return v;
+}
+
+// Choose a schedule and launch shape per bucket.
+void plan_buckets(rasp_batch* b) {
+  const uint32_t forced = b->cfg.flags & RASP_SCHED_MASK;
+  const StepVariant var = variant_of(b);
+  for (Bucket& k : b->buckets) {
+    if (!k.count) continue;
+    uint32_t sched = forced;
+    const uint32_t slot = [&] {
+      uint32_t w = k.ncap + b->ellp + b->sp;
+      w = even(w);
+      if ((w & 3u) == 0) w += 2u;          // stride = 2 mod 4 words: conflict-free 16-byte rows
+      return w;
+    }();
+    const size_t staged_bytes = (size_t)(32u + 32u * slot) * 8u;
+    if (sched == RASP_SCHED_AUTO) sched = (staged_bytes <= 80u * 1024u) ? RASP_SCHED_PERSIST : RASP_SCHED_PERSIST_GL;
+    if (sched == RASP_SCHED_PERSIST && staged_bytes > 220u * 1024u) sched = RASP_SCHED_PERSIST_GL;
+    k.sched = sched;
+    PersistShape& sh = k.shape;
+    sh.ncap = k.ncap;
+    sh.slot_words = slot;
+    sh.epoch = b->cfg.epoch ? b->cfg.epoch : 32u;
+    if (sched == RASP_SCHED_PERSIST) {
+      sh.staged = true;
+      sh.warps = 1;
+      sh.refill_min = 8;
+    } else {
+      sh.staged = false;
+      sh.warps = 4;
+      sh.refill_min = 1;
+    }
+    if (sched != RASP_SCHED_PLAIN) {
+      if (persist_configure(var, sh) == 0) {
+        k.sched = RASP_SCHED_PLAIN;        // cannot be resident: fall back to the plain form
+      }
+    }
+  }
+}
+
+int check_device_error(rasp_batch* b) {
+  int err = 0;
+  CK(cudaMemcpyAsync(&err, b->d_err, sizeof(int), cudaMemcpyDeviceToHost, b->stream));
+  CK(cudaStreamSynchronize(b->stream));
+  if (err) return fail(RASP_EDEVICE, "a kernel reported internal error %d (bounded wait expired)", err);
+  return RASP_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* rasp_last_error(void) { return g_err.c_str(); }
+
+const char* rasp_version(void) { return "rasp_gb300 1.0 (sm_103a)"; }
+
+int rasp_batch_bytes(const rasp_config* cfg, uint64_t num_vms, const uint32_t* mem_words, uint64_t* out_bytes) {
+  int rc = validate_config(cfg, num_vms, mem_words);
+  if (rc) return rc;
+  if (!out_bytes) return fail(RASP_EINVAL, "out_bytes is NULL");
+  uint64_t mw = 0;
+  for (uint64_t v = 0; v < num_vms; ++v) mw += even(mem_words[v]);
+  *out_bytes = make_layout(num_vms, mw, even(cfg->in_cap), even(cfg->out_cap)).total + ALIGN;
+  return RASP_OK;
+}
+
+int rasp_batch_create(const rasp_config* cfg, uint64_t num_vms, const uint32_t* mem_words, rasp_batch** out) {
+  if (!out) return fail(RASP_EINVAL, "out is NULL");
+  *out = nullptr;
+  int rc = validate_config(cfg, num_vms, mem_words);
+  if (rc) return rc;
+  rasp_batch* b = new (std::nothrow) rasp_batch();
+  if (!b) return fail(RASP_ENOMEM, "host allocation failed");
+  b->cfg = *cfg;
+  b->stream = (cudaStream_t)cfg->stream;
+  b->V = (uint32_t)num_vms;
+  b->ell = cfg->in_cap;
+  b->s = cfg->out_cap;
+  b->ellp = even(cfg->in_cap);
+  b->sp = even(cfg->out_cap);
+  b->wmask = cfg->word_bits >= 64 ? ~0ull : ((1ull << cfg->word_bits) - 1ull);
+  b->h_n.assign(mem_words, mem_words + num_vms);
+  b->h_memoff.resize(num_vms);
+  uint64_t off = 0;
+  for (uint64_t v = 0; v < num_vms; ++v) {
+    b->h_memoff[v] = off;
+    off += even(mem_words[v]);
+  }
+  b->mem_words = off;
+  b->L = make_layout(num_vms, off, b->ellp, b->sp);
+  if (cfg->arena) {
+    const uintptr_t p = (uintptr_t)cfg->arena;
+    const uintptr_t aligned = (p + ALIGN - 1) & ~(uintptr_t)(ALIGN - 1);
+    if (aligned - p + b->L.total > cfg->arena_bytes) {
+      delete b;
+      return fail(RASP_ENOMEM, "arena of %llu bytes is smaller than the %llu the batch needs",
+                  (unsigned long long)cfg->arena_bytes, (unsigned long long)(b->L.total + ALIGN));
+    }
+    b->base = (char*)aligned;
+    b->owns = false;
+  } else {
+    void* p = nullptr;
+    cudaError_t e = cudaMalloc(&p, b->L.total);
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      delete b;
+      return fail(RASP_ENOMEM, "cudaMalloc(%llu) failed: %s", (unsigned long long)b->L.total, cudaGetErrorString(e));
+    }
+    b->base = (char*)p;
+    b->owns = true;
+  }
+  const Layout& L = b->L;
+  char* B = b->base;
+  DevState& S = b->S;
+  S.i = (uint64_t*)(B + L.off_i);
+  S.a = (uint64_t*)(B + L.off_a);
+  S.steps = (uint64_t*)(B + L.off_steps);
+  b->d_cap = (uint64_t*)(B + L.off_cap);
+  S.cap = b->d_cap;
+  S.status = (uint8_t*)(B + L.off_status);
+  S.uhead = (uint32_t*)(B + L.off_uhead);
+  S.ylen = (uint32_t*)(B + L.off_ylen);
+  S.n = (const uint32_t*)(B + L.off_n);
+  S.mem_off = (const uint64_t*)(B + L.off_memoff);
+  S.mem = (uint64_t*)(B + L.off_mem);
+  S.tape = (const uint64_t*)(B + L.off_tape);
+  S.y = (uint64_t*)(B + L.off_y);
+  b->d_prog = (uint64_t*)(B + L.off_prog);
+  b->d_progoff = (uint64_t*)(B + L.off_progoff);
+  b->d_progvm = (uint32_t*)(B + L.off_progvm);
+  b->d_ids = (uint32_t*)(B + L.off_ids);
+  b->d_heads = (uint32_t*)(B + L.off_heads);
+  b->d_err = (int*)(B + L.off_err);
+  b->d_hist = (unsigned long long*)(B + L.off_hist);
+  b->d_stats = (unsigned long long*)(B + L.off_stats);
+
+  // buckets by memory size (stable: VM id order within a bucket)
+  std::vector<uint32_t> cls(num_vms);
+  std::vector<uint32_t> counts(kNumBuckets, 0), ncap(kNumBuckets, 0);
+  for (uint64_t v = 0; v < num_vms; ++v) {
+    int k = 0;
+    while (even(mem_words[v]) > kBucketBounds[k]) ++k;
+    cls[v] = (uint32_t)k;
+    counts[k]++;
+    ncap[k] = std::max(ncap[k], even(mem_words[v]));
+  }
+  b->buckets.resize(kNumBuckets);
+  uint32_t pos = 0;
+  for (int k = 0; k < kNumBuckets; ++k) {
+    b->buckets[k].first = pos;
+    b->buckets[k].count = counts[k];
+    b->buckets[k].ncap = ncap[k];
+    pos += counts[k];
+  }
+  b->h_ids.resize(num_vms);
+  std::vector<uint32_t> fill(kNumBuckets, 0);
+  for (uint64_t v = 0; v < num_vms; ++v) {
+    const uint32_t k = cls[v];
+    b->h_ids[b->buckets[k].first + fill[k]++] = (uint32_t)v;
+  }
+  plan_buckets(b);
+
+  cudaStream_t st = b->stream;
+  auto cleanup_fail = [&](int code) {
+    if (b->owns) cudaFree(b->base);
+    delete b;
+    return code;
+  };
+#define CKC(call)                                                                              \
+  do {                                                                                         \
+    cudaError_t e_ = (call);                                                                   \
+    if (e_ != cudaSuccess) return cleanup_fail(fail(RASP_ECUDA, "%s: %s", #call, cudaGetErrorString(e_))); \
+  } while (0)
+  CKC(cudaMemcpyAsync((void*)S.n, mem_words, 4 * num_vms, cudaMemcpyHostToDevice, st));
+  CKC(cudaMemcpyAsync((void*)S.mem_off, b->h_memoff.data(), 8 * num_vms, cudaMemcpyHostToDevice, st));
+  CKC(cudaMemcpyAsync(b->d_ids, b->h_ids.data(), 4 * num_vms, cudaMemcpyHostToDevice, st));
+  CKC(cudaMemsetAsync(b->base + L.off_status, RASP_RUNNING, num_vms, st));
+  CKC(cudaMemsetAsync(b->d_err, 0, 16, st));
+  CKC(cudaMemsetAsync(b->d_hist, 0, 8 * 10, st));
+  CKC(cudaMemsetAsync(b->d_cap, 0xff, 8 * num_vms, st));
+  CKC(cudaStreamSynchronize(st));
+#undef CKC
+  *out = b;
+  g_err.clear();
+  return RASP_OK;
+}
+
+int rasp_load_programs(rasp_batch* b, const int64_t* words, const uint64_t* offsets, uint64_t num_programs,
+                       const uint32_t* prog_of_vm) {
+  if (!b) return fail(RASP_EINVAL, "batch is NULL");
+  if (!offsets || num_programs == 0) return fail(RASP_EINVAL, "offsets NULL or no programs");
+  if (!prog_of_vm && num_programs != b->V)
+    return fail(RASP_EINVAL, "without prog_of_vm there must be one program per VM (%llu != %u)",
+                (unsigned long long)num_programs, b->V);
+  if (num_programs > b->V) return fail(RASP_EINVAL, "more programs (%llu) than VMs (%u)",
+                                       (unsigned long long)num_programs, b->V);
+  if (offsets[0] != 0) return fail(RASP_EINVAL, "offsets[0] must be 0");
+  for (uint64_t p = 0; p < num_programs; ++p) {
+    if (offsets[p + 1] < offsets[p]) return fail(RASP_EINVAL, "offsets decrease at program %llu", (unsigned long long)p);
+    if ((offsets[p + 1] - offsets[p]) & 1ull)
+      return fail(RASP_EINVAL, "program %llu has odd length (instructions are word pairs)", (unsigned long long)p);
+  }
+  const uint64_t total = offsets[num_programs];
+  if (total > b->mem_words) return fail(RASP_EINVAL, "programs (%llu words) exceed the batch memory", (unsigned long long)total);
+  if (total && !words) return fail(RASP_EINVAL, "words is NULL");
+  for (uint32_t v = 0; v < b->V; ++v) {
+    const uint64_t p = prog_of_vm ? prog_of_vm[v] : v;
+    if (p >= num_programs) return fail(RASP_EINVAL, "prog_of_vm[%u] = %llu out of range", v, (unsigned long long)p);
+    if (offsets[p + 1] - offsets[p] > b->h_n[v])
+      return fail(RASP_EINVAL, "program of VM %u has %llu words > n = %u (need 2m <= n)", v,
+                  (unsigned long long)(offsets[p + 1] - offsets[p]), b->h_n[v]);
+  }
+  cudaStream_t st = b->stream;
+  if (total) CK(cudaMemcpyAsync(b->d_prog, words, 8 * total, cudaMemcpyHostToDevice, st));
+  CK(cudaMemcpyAsync(b->d_progoff, offsets, 8 * (num_programs + 1), cudaMemcpyHostToDevice, st));
+  b->shared_programs = prog_of_vm != nullptr;
+  if (prog_of_vm) CK(cudaMemcpyAsync(b->d_progvm, prog_of_vm, 4ull * b->V, cudaMemcpyHostToDevice, st));
+  CK(cudaMemsetAsync(b->d_hist, 0, 8 * 10, st));
+  CK(launch_pack(b->S, b->d_prog, b->d_progoff, b->shared_programs ? b->d_progvm : nullptr, b->V, b->wmask, b->sp, st));
+  b->programs_loaded = true;
+  g_err.clear();
+  return RASP_OK;
+}
+
+int rasp_load_inputs(rasp_batch* b, const int64_t* tape, const uint64_t* offsets, const uint64_t* caps) {
+  if (!b) return fail(RASP_EINVAL, "batch is NULL");
+  if (!offsets) return fail(RASP_EINVAL, "offsets is NULL");
+  if (offsets[0] != 0) return fail(RASP_EINVAL, "offsets[0] must be 0");
+  bool regular = true;
+  for (uint32_t v = 0; v < b->V; ++v) {
+    if (offsets[v + 1] < offsets[v]) return fail(RASP_EINVAL, "offsets decrease at VM %u", v);
+    const uint64_t len = offsets[v + 1] - offsets[v];
+    if (len > b->ell) return fail(RASP_EINVAL, "input of VM %u has %llu words > l = %u", v, (unsigned long long)len, b->ell);
+    regular = regular && (len == b->ellp);
+  }
+  if (offsets[b->V] && !tape) return fail(RASP_EINVAL, "tape is NULL");
+  cudaStream_t st = b->stream;
+  uint64_t* d_tape = (uint64_t*)b->S.tape;
+  const bool masked = b->wmask != ~0ull;
+  if (b->ellp) {
+    if (regular && !masked) {
+      CK(cudaMemcpyAsync(d_tape, tape, 8ull * b->V * b->ellp, cudaMemcpyHostToDevice, st));
+    } else {
+      std::vector<uint64_t> buf((size_t)b->V * b->ellp, 0);
+      for (uint32_t v = 0; v < b->V; ++v)
+        for (uint64_t k = offsets[v]; k < offsets[v + 1]; ++k)
+          buf[(size_t)v * b->ellp + (k - offsets[v])] = (uint64_t)tape[k] & b->wmask;
+      CK(cudaMemcpyAsync(d_tape, buf.data(), 8 * buf.size(), cudaMemcpyHostToDevice, st));
+      CK(cudaStreamSynchronize(st));
+    }
+  }
+  if (caps) {
+    CK(cudaMemcpyAsync(b->d_cap, caps, 8ull * b->V, cudaMemcpyHostToDevice, st));
+    // longest-cap-first order inside each bucket (largest work starts first)
+    bool uniform = true;
+    for (uint32_t v = 1; v < b->V && uniform; ++v) uniform = caps[v] == caps[0];
+    if (!uniform) {
+      for (const Bucket& k : b->buckets) {
+        if (k.count < 2) continue;
+        auto first = b->h_ids.begin() + k.first;
+        std::stable_sort(first, first + k.count, [&](uint32_t x, uint32_t y) { return caps[x] > caps[y]; });
+      }
+      CK(cudaMemcpyAsync(b->d_ids, b->h_ids.data(), 4ull * b->V, cudaMemcpyHostToDevice, st));
+      CK(cudaStreamSynchronize(st));
+    }
+  } else {
+    CK(cudaMemsetAsync(b->d_cap, 0xff, 8ull * b->V, st));
+  }
+  CK(cudaMemsetAsync(b->S.uhead, 0, 4ull * b->V, st));
+  b->inputs_loaded = true;
+  g_err.clear();
+  return RASP_OK;
+}
+
+int rasp_reset(rasp_batch* b) {
+  if (!b) return fail(RASP_EINVAL, "batch is NULL");
+  if (!b->programs_loaded || !b->inputs_loaded) return fail(RASP_ESTATE, "load programs and inputs first");
+  CK(cudaMemsetAsync(b->d_hist, 0, 8 * 10, b->stream));
+  CK(launch_pack(b->S, b->d_prog, b->d_progoff, b->shared_programs ? b->d_progvm : nullptr, b->V, b->wmask, b->sp,
+                 b->stream));
+  return RASP_OK;
+}
+
+int rasp_run(rasp_batch* b, uint64_t max_steps) {
+  if (!b) return fail(RASP_EINVAL, "batch is NULL");
+  if (!b->programs_loaded || !b->inputs_loaded) return fail(RASP_ESTATE, "load programs and inputs before rasp_run");
+  cudaStream_t st = b->stream;
+  const StepVariant var = variant_of(b);
+  Params P{};
+  P.wmask = b->wmask;
+  P.budget = max_steps;
+  P.ell = b->ell;
+  P.s = b->s;
+  P.ellp = b->ellp;
+  P.sp = b->sp;
+  P.err = b->d_err;
+  P.hist = b->d_hist;
+  CK(cudaMemsetAsync(b->d_heads, 0, 4 * kNumBuckets, st));
+  b->launches = 0;
+  for (size_t k = 0; k < b->buckets.size(); ++k) {
+    const Bucket& bk = b->buckets[k];
+    if (!bk.count) continue;
+    const uint32_t* ids = b->d_ids + bk.first;
+    if (bk.sched == RASP_SCHED_PLAIN) {
+      CK(launch_plain(var, b->S, P, ids, bk.count, st));
+    } else {
+      Queue Q{ids, bk.count, b->d_heads + k};
+      CK(launch_persist(var, b->S, P, Q, bk.shape, st));
+    }
+    b->launches++;
+  }
+  return RASP_OK;
+}
+
+int rasp_sync(rasp_batch* b) {
+  if (!b) return fail(RASP_EINVAL, "batch is NULL");
+  return check_device_error(b);
+}
+
+int rasp_read_state(rasp_batch* b, uint64_t first, uint64_t count, rasp_state_view* out) {
+  if (!b || !out) return fail(RASP_EINVAL, "batch or view is NULL");
+  if (first > b->V || count > b->V - first) return fail(RASP_EINVAL, "range [%llu, +%llu) outside the batch",
+                                                      (unsigned long long)first, (unsigned long long)count);
+  int rc = check_device_error(b);
+  if (rc) return rc;
+  if (!count) return RASP_OK;
+  cudaStream_t st = b->stream;
+  const DevState& S = b->S;
+  if (out->i) CK(cudaMemcpyAsync(out->i, S.i + first, 8 * count, cudaMemcpyDeviceToHost, st));
+  if (out->a) CK(cudaMemcpyAsync(out->a, S.a + first, 8 * count, cudaMemcpyDeviceToHost, st));
+  if (out->steps) CK(cudaMemcpyAsync(out->steps, S.steps + first, 8 * count, cudaMemcpyDeviceToHost, st));
+  if (out->status) CK(cudaMemcpyAsync(out->status, S.status + first, count, cudaMemcpyDeviceToHost, st));
+  if (out->uhead) CK(cudaMemcpyAsync(out->uhead, S.uhead + first, 4 * count, cudaMemcpyDeviceToHost, st));
+  if (out->ylen) CK(cudaMemcpyAsync(out->ylen, S.ylen + first, 4 * count, cudaMemcpyDeviceToHost, st));
+  std::vector<uint64_t> ybuf, mbuf;
+  if (out->y && b->s) {
+    if (b->sp == b->s) {
+      CK(cudaMemcpyAsync(out->y, S.y + first * b->sp, 8 * count * b->sp, cudaMemcpyDeviceToHost, st));
+    } else {
+      ybuf.resize(count * b->sp);
+      CK(cudaMemcpyAsync(ybuf.data(), S.y + first * b->sp, 8 * count * b->sp, cudaMemcpyDeviceToHost, st));
+    }
+  }
+  uint64_t need = 0;
+  if (out->mem) {
+    for (uint64_t v = first; v < first + count; ++v) need += b->h_n[v];
+    if (out->mem_words < need) return fail(RASP_EINVAL, "mem holds %llu words, the range needs %llu",
+                                           (unsigned long long)out->mem_words, (unsigned long long)need);
+    const uint64_t lo = b->h_memoff[first];
+    const uint64_t hi = b->h_memoff[first + count - 1] + even(b->h_n[first + count - 1]);
+    if (need == hi - lo) {
+      CK(cudaMemcpyAsync(out->mem, S.mem + lo, 8 * need, cudaMemcpyDeviceToHost, st));
+    } else {
+      mbuf.resize(hi - lo);
+      CK(cudaMemcpyAsync(mbuf.data(), S.mem + lo, 8 * (hi - lo), cudaMemcpyDeviceToHost, st));
+    }
+  }
+  CK(cudaStreamSynchronize(st));
+  if (!ybuf.empty())
+    for (uint64_t v = 0; v < count; ++v)
+      memcpy(out->y + v * b->s, ybuf.data() + v * b->sp, 8 * b->s);
+  if (!mbuf.empty()) {
+    const uint64_t lo = b->h_memoff[first];
+    uint64_t o = 0;
+    for (uint64_t v = first; v < first + count; ++v) {
+      memcpy(out->mem + o, mbuf.data() + (b->h_memoff[v] - lo), 8ull * b->h_n[v]);
+      o += b->h_n[v];
+    }
+  }
+  return RASP_OK;
+}
+
+int rasp_load_state(rasp_batch* b, uint64_t first, uint64_t count, const rasp_state_view* in) {
+  if (!b || !in) return fail(RASP_EINVAL, "batch or view is NULL");
+  if (first > b->V || count > b->V - first) return fail(RASP_EINVAL, "range outside the batch");
+  if (!count) return RASP_OK;
+  for (uint64_t v = 0; v < count; ++v) {
+    if (in->uhead && in->uhead[v] > b->ell) return fail(RASP_EINVAL, "u_0 of VM %llu exceeds l", (unsigned long long)(first + v));
+    if (in->ylen && in->ylen[v] > b->s) return fail(RASP_EINVAL, "y_0 of VM %llu exceeds s", (unsigned long long)(first + v));
+    if (in->status && in->status[v] > RASP_FAULT_ADDR) return fail(RASP_EINVAL, "bad status for VM %llu", (unsigned long long)(first + v));
+  }
+  uint64_t need = 0;
+  if (in->mem) {
+    for (uint64_t v = first; v < first + count; ++v) need += b->h_n[v];
+    if (in->mem_words < need) return fail(RASP_EINVAL, "mem holds %llu words, the range needs %llu",
+                                          (unsigned long long)in->mem_words, (unsigned long long)need);
+  }
+  cudaStream_t st = b->stream;
+  const DevState& S = b->S;
+  if (in->i) CK(cudaMemcpyAsync(S.i + first, in->i, 8 * count, cudaMemcpyHostToDevice, st));
+  if (in->a) CK(cudaMemcpyAsync(S.a + first, in->a, 8 * count, cudaMemcpyHostToDevice, st));
+  if (in->steps) CK(cudaMemcpyAsync(S.steps + first, in->steps, 8 * count, cudaMemcpyHostToDevice, st));
+  if (in->status) CK(cudaMemcpyAsync(S.status + first, in->status, count, cudaMemcpyHostToDevice, st));
+  if (in->uhead) CK(cudaMemcpyAsync(S.uhead + first, in->uhead, 4 * count, cudaMemcpyHostToDevice, st));
+  if (in->ylen) CK(cudaMemcpyAsync(S.ylen + first, in->ylen, 4 * count, cudaMemcpyHostToDevice, st));
+  std::vector<uint64_t> ybuf, mbuf;
+  if (in->y && b->s) {
+    ybuf.assign(count * b->sp, 0);
+    for (uint64_t v = 0; v < count; ++v)
+      for (uint32_t k = 0; k < b->s; ++k) ybuf[v * b->sp + k] = (uint64_t)in->y[v * b->s + k] & b->wmask;
+    CK(cudaMemcpyAsync(S.y + first * b->sp, ybuf.data(), 8 * ybuf.size(), cudaMemcpyHostToDevice, st));
+  }
+  if (in->mem) {
+    const uint64_t lo = b->h_memoff[first];
+    const uint64_t hi = b->h_memoff[first + count - 1] + even(b->h_n[first + count - 1]);
+    mbuf.assign(hi - lo, 0);
+    uint64_t o = 0;
+    for (uint64_t v = first; v < first + count; ++v) {
+      for (uint32_t k = 0; k < b->h_n[v]; ++k) mbuf[b->h_memoff[v] - lo + k] = (uint64_t)in->mem[o + k] & b->wmask;
+      o += b->h_n[v];
+    }
+    CK(cudaMemcpyAsync(S.mem + lo, mbuf.data(), 8 * mbuf.size(), cudaMemcpyHostToDevice, st));
+  }
+  CK(cudaStreamSynchronize(st));
+  return RASP_OK;
+}
+
+int rasp_read_stats(rasp_batch* b, rasp_stats* out) {
+  if (!b || !out) return fail(RASP_EINVAL, "batch or stats is NULL");
+  int rc = check_device_error(b);
+  if (rc) return rc;
+  unsigned long long agg[6] = {0, 0, 0, 0, 0, 0}, hist[10] = {0};
+  CK(launch_stats(b->S, b->V, b->d_stats, b->stream));
+  CK(cudaMemcpyAsync(agg, b->d_stats, sizeof(agg), cudaMemcpyDeviceToHost, b->stream));
+  CK(cudaMemcpyAsync(hist, b->d_hist, sizeof(hist), cudaMemcpyDeviceToHost, b->stream));
+  CK(cudaStreamSynchronize(b->stream));
+  memset(out, 0, sizeof(*out));
+  out->vm_steps = agg[0];
+  out->running = agg[1];
+  out->halted = agg[2];
+  out->timeout = agg[3];
+  out->fault_overflow = agg[4];
+  out->fault_addr = agg[5];
+  for (int k = 1; k <= 7; ++k) out->op_steps[k] = hist[k];
+  out->pri_full = hist[8];
+  out->bnz_taken = hist[9];
+  out->launches = b->launches;
+  return RASP_OK;
+}
+
+void rasp_batch_destroy(rasp_batch* b) {
+  if (!b) return;
+  cudaStreamSynchronize(b->stream);
+  if (b->owns && b->base) cudaFree(b->base);
+  delete b;
+}
+
+}  // extern "C"

@@ -1,0 +1,48 @@
+// internal.h -- host-side declarations shared by the C-ABI layer and the
+// kernel launchers (not part of the public ABI).
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "engine.cuh"
+
+namespace rasp {
+
+struct StepVariant {
+  bool masked;   // w < 64
+  bool checked;  // RASP_CHECKED semantics
+  bool hist;     // collect per-opcode counters
+  bool vote;     // warp opcode voting instead of guarded selects
+};
+
+// Persistent-kernel launch shape for one bucket of VMs.
+struct PersistShape {
+  bool staged;          // M, tape and y in shared memory (bulk-copied)
+  uint32_t ncap;        // slot capacity for M (words, even)
+  uint32_t slot_words;  // words per lane slot (M + tape + y, padded)
+  uint32_t warps;       // warps per CTA
+  uint32_t epoch;       // steps between warp scheduling points
+  uint32_t refill_min;  // idle lanes that trigger a refill
+  uint32_t grid;        // CTAs
+  size_t smem;          // dynamic shared memory per CTA
+};
+
+cudaError_t launch_pack(const DevState& S, const uint64_t* prog, const uint64_t* prog_off,
+                        const uint32_t* prog_of_vm, uint32_t num_vms, uint64_t wmask, uint32_t sp,
+                        cudaStream_t stream);
+
+cudaError_t launch_plain(const StepVariant& var, const DevState& S, const Params& P,
+                         const uint32_t* ids, uint32_t count, cudaStream_t stream);
+
+// Fills grid/smem of `shape` for the current device (occupancy-sized) and
+// returns the resident CTAs per SM (0 if the shape cannot launch).
+int persist_configure(const StepVariant& var, PersistShape& shape);
+
+cudaError_t launch_persist(const StepVariant& var, const DevState& S, const Params& P, const Queue& Q,
+                           const PersistShape& shape, cudaStream_t stream);
+
+// Aggregate: out[0] = sum steps, out[1..5] = count per status.
+cudaError_t launch_stats(const DevState& S, uint32_t num_vms, unsigned long long* out, cudaStream_t stream);
+
+}  // namespace rasp

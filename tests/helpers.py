@@ -47,3 +47,37 @@ def busy_beavers():
         name, tau = head.split()
         out.append((name, int(tau), body))
     return out
+
+
+# ------------------------------------------------------------------ parity plumbing
+def oracle_state(wl, budget=U64, checked=False, hist=False, threads=1):
+    """Run a workload through the CPU oracle (programs expanded per VM)."""
+    from oracle import oracle
+    progs, po = wl.expanded_programs()
+    return oracle.run_packed(progs, po, wl.mem_words, wl.tapes, wl.tape_off, wl.ell, wl.s,
+                             caps=wl.caps, budget=budget, w=wl.w, checked=checked, hist=hist,
+                             threads=threads)
+
+
+def assert_same_state(got, st, ell, s, ids=None, what=""):
+    """GPU state (library layout, optionally only VMs `ids`) == oracle state."""
+    V = st.count
+    sel = slice(None) if ids is None else ids
+    u64 = lambda x: np.asarray(x).view(np.uint64) if np.asarray(x).dtype == np.int64 else np.asarray(x)
+    for key, want in (("i", st.i), ("a", st.a), ("steps", st.steps), ("status", st.status),
+                      ("uhead", st.u[0::ell + 1][:V]), ("ylen", st.y[0::s + 1][:V])):
+        g = u64(got[key])[sel]
+        w = np.asarray(want)
+        if not np.array_equal(g.astype(np.uint64), w.astype(np.uint64)):
+            bad = np.nonzero(g.astype(np.uint64) != w.astype(np.uint64))[0]
+            raise AssertionError("%s: field %s differs at %d VMs, first %d: gpu %r oracle %r"
+                                 % (what, key, bad.size, bad[0], g[bad[0]], w[bad[0]]))
+    if s:
+        gy = u64(got["y"])[sel].reshape(V, s)
+        wy = st.y.reshape(V, s + 1)[:, 1:]
+        assert np.array_equal(gy, wy), "%s: outputs y differ" % what
+    if "mem" in got and ids is None:
+        gm = u64(got["mem"])
+        if not np.array_equal(gm, st.mem[:gm.shape[0]]):
+            bad = np.nonzero(gm != st.mem[:gm.shape[0]])[0]
+            raise AssertionError("%s: memory differs at %d words, first word %d" % (what, bad.size, bad[0]))

@@ -1,0 +1,277 @@
+"""CUDA path vs the CPU oracle, bit-exact, through the C ABI (needs a GPU)."""
+import os
+
+import numpy as np
+import pytest
+
+from paper_2604_12902_gb300 import dsl, workloads as W
+from tests.helpers import (ADD, BNZ, LOD, MUL, PRI, RD, STO, U64, asm, assert_same_state,
+                           batch, busy_beavers, oracle_state)
+
+pytestmark = pytest.mark.gpu
+
+SCHEDS = {"plain": 0x10, "persist": 0x20, "persist_gl": 0x30}
+DISPATCH = {"select": 0x000, "vote": 0x100}
+THREADS = os.cpu_count() or 1
+
+
+@pytest.fixture(scope="module")
+def rasp():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2604_12902_gb300 import rasp as R
+    R.lib()
+    return R
+
+
+def run_gpu(R, wl, flags=0, budget=U64, semantics=0, epoch=0, mem=True, steps_split=None):
+    with R.Batch(wl.mem_words, wl.ell, wl.s, word_bits=wl.w, semantics=semantics,
+                 flags=flags, epoch=epoch) as b:
+        b.load_workload(wl)
+        if steps_split:
+            for t in steps_split:
+                b.run(t)
+        b.run(budget)
+        got = b.read_state(mem=mem)
+        stats = b.stats()
+    return got, stats
+
+
+def wl_from(programs, tapes, n, caps, ell, s, w=64, name="hand"):
+    p, po, nn, t, to, cc = batch(programs, tapes, n, caps)
+    return W.Workload(name, p, po, nn.astype(np.uint32), t, to,
+                      cc if cc is not None else np.full(len(programs), U64, np.uint64), ell, s, w)
+
+
+@pytest.mark.parametrize("sched", list(SCHEDS))
+@pytest.mark.parametrize("disp", list(DISPATCH))
+def test_random_programs_all_schedules(rasp, sched, disp):
+    wl = W.random_programs(num_vms=1024, seed=1)
+    st, _ = oracle_state(wl)
+    got, stats = run_gpu(rasp, wl, SCHEDS[sched] | DISPATCH[disp])
+    assert_same_state(got, st, wl.ell, wl.s, what="random/%s/%s" % (sched, disp))
+    assert stats["vm_steps"] == int(st.steps.sum())
+
+
+@pytest.mark.parametrize("sched", list(SCHEDS))
+@pytest.mark.parametrize("disp", list(DISPATCH))
+def test_template_programs_all_schedules(rasp, sched, disp):
+    wl = W.template_programs(num_vms=20000, seed=2)
+    st, _ = oracle_state(wl, threads=THREADS)
+    got, _ = run_gpu(rasp, wl, SCHEDS[sched] | DISPATCH[disp])
+    assert_same_state(got, st, wl.ell, wl.s, what="templates/%s/%s" % (sched, disp))
+
+
+@pytest.mark.parametrize("epoch", [1, 7, 64])
+def test_persistent_epoch_independence(rasp, epoch):
+    wl = W.template_programs(num_vms=5000, seed=7)
+    st, _ = oracle_state(wl)
+    for sched in ("persist", "persist_gl"):
+        got, _ = run_gpu(rasp, wl, SCHEDS[sched], epoch=epoch)
+        assert_same_state(got, st, wl.ell, wl.s, what="epoch %d %s" % (epoch, sched))
+
+
+def test_template_full_size_auto_schedule(rasp):
+    """1,048,576 template programs, n = 256, cap 4096, the benchmark's launch
+    configuration: every VM compared with the oracle."""
+    wl = W.template_programs(num_vms=1 << 20, seed=2)
+    st, h = oracle_state(wl, threads=THREADS, hist=True)
+    got, stats = run_gpu(rasp, wl, 0)
+    assert_same_state(got, st, wl.ell, wl.s, what="templates full")
+    assert stats["halted"] == wl.num_vms
+
+
+def test_random_full_size_stats(rasp):
+    wl = W.random_programs(num_vms=1024, seed=1)
+    st, h = oracle_state(wl, hist=True)
+    for sched in SCHEDS.values():
+        got, stats = run_gpu(rasp, wl, sched | 0x1000)
+        assert stats["op_steps"][1:8] == [int(x) for x in h[1:8]]
+        assert stats["pri_full"] == int(h[8]) and stats["bnz_taken"] == int(h[0])
+        assert stats["halted"] == int((st.status == 1).sum())
+        assert stats["timeout"] == int((st.status == 2).sum())
+
+
+OPS = list(range(9))
+ARGS = [0, 1, 2, 5, 1 << 63, U64]
+
+
+@pytest.mark.parametrize("n,tape,w", [(6, [3, -2], 64), (8, [], 8), (6, [], 64), (8, [3, -2], 2)])
+def test_exhaustive_tiny_programs(rasp, n, tape, w):
+    instrs = [(o, a) for o in OPS for a in ARGS]
+    progs = [[]] + [asm(x) for x in instrs] + [asm(x, y) for x in instrs for y in instrs]
+    if n == 6 or w == 8:
+        progs += [asm(x, y, z) for x in instrs for y in instrs for z in instrs]
+    wl = wl_from(progs, [tape] * len(progs), n, 64, 2, 2, w=w, name="tiny")
+    st, _ = oracle_state(wl, threads=THREADS)
+    for sched in SCHEDS.values():
+        got, _ = run_gpu(rasp, wl, sched)
+        assert_same_state(got, st, 2, 2, what="tiny n=%d w=%d sched=%x" % (n, w, sched))
+
+
+@pytest.mark.parametrize("w", [29, 32, 64])
+def test_busy_beavers_on_gpu(rasp, w):
+    bbs = busy_beavers()
+    lows = [dsl.lower(src, ell=10, s=2) for _, _, src in bbs]
+    wl = wl_from([l.words for l in lows], [[]] * 3, 256, 10 ** 6, 10, 2, w=w, name="bb")
+    st, _ = oracle_state(wl)
+    for sched in SCHEDS.values():
+        got, _ = run_gpu(rasp, wl, sched)
+        assert_same_state(got, st, 10, 2, what="bb w=%d" % w)
+        if w == 29:
+            assert [int(x) for x in got["steps"]] == [tau for _, tau, _ in bbs]
+
+
+def _checked_workload(V=4096, seed=11):
+    """Random programs whose operands straddle [0, n) and whose data are large,
+    so that address and overflow faults both occur."""
+    ids = np.arange(V, dtype=np.uint64)
+    n = 48
+    ops = np.array([1, 2, 2, 2, 3, 3, 3, 4, 5, 7, 0, 8])[W.uniform_int(W.draws(seed, 1, ids, 20), 0, 11)]
+    arg = W.uniform_int(W.draws(seed, 2, ids, 20), 30, n + 3)
+    arg[:, ::5] -= 36                                           # some negative operands
+    ops[:, :4] = RD                                             # read the large inputs first
+    arg[:, :4] = np.arange(40, 44)
+    prog = np.empty((V, 40), np.int64)
+    prog[:, 0::2] = ops
+    prog[:, 1::2] = arg
+    big = W.uniform_int(W.draws(seed, 3, ids, 4), -(1 << 31), (1 << 31) - 1).astype(np.int64)
+    tape = big * np.int64(1 << 32)
+    return W.Workload("checked", prog.reshape(-1), np.arange(V + 1, dtype=np.uint64) * 40,
+                      np.full(V, n, np.uint32), tape.reshape(-1), np.arange(V + 1, dtype=np.uint64) * 4,
+                      np.full(V, 500, np.uint64), 4, 3)
+
+
+def test_checked_semantics_faults(rasp):
+    wl = _checked_workload()
+    st, _ = oracle_state(wl, checked=True)
+    counts = np.bincount(st.status, minlength=5)
+    assert counts[3] > 50 and counts[4] > 500, counts          # both fault kinds occur
+    for sched in SCHEDS.values():
+        for disp in DISPATCH.values():
+            got, stats = run_gpu(rasp, wl, sched | disp, semantics=1)
+            assert_same_state(got, st, wl.ell, wl.s, what="checked %x" % (sched | disp))
+            assert stats["fault_overflow"] == counts[3] and stats["fault_addr"] == counts[4]
+
+
+def test_wrap_semantics_never_faults(rasp):
+    wl = _checked_workload()
+    st, _ = oracle_state(wl)
+    got, stats = run_gpu(rasp, wl, 0)
+    assert_same_state(got, st, wl.ell, wl.s, what="wrap")
+    assert stats["fault_overflow"] == 0 and stats["fault_addr"] == 0
+
+
+@pytest.mark.parametrize("sched", list(SCHEDS))
+def test_budget_and_resume(rasp, sched):
+    wl = W.random_programs(num_vms=2048, seed=4, cap=300)
+    for t1 in (0, 1, 13, 100):
+        part, _ = oracle_state(wl, budget=t1)
+        got, _ = run_gpu(rasp, wl, SCHEDS[sched], budget=t1)
+        assert_same_state(got, part, wl.ell, wl.s, what="budget %d" % t1)
+    full, _ = oracle_state(wl)
+    got, _ = run_gpu(rasp, wl, SCHEDS[sched], steps_split=[5, 17, 17, 90])
+    assert_same_state(got, full, wl.ell, wl.s, what="resumed")
+
+
+def test_checkpoint_restore_roundtrip(rasp):
+    wl = W.template_programs(num_vms=3000, seed=9)
+    full, _ = oracle_state(wl)
+    with rasp.Batch(wl.mem_words, wl.ell, wl.s) as b:
+        b.load_workload(wl)
+        b.run(150)
+        snap = b.read_state()
+    with rasp.Batch(wl.mem_words, wl.ell, wl.s) as b2:
+        b2.load_workload(wl)                 # tapes and caps; state is then overwritten
+        b2.load_state(snap)
+        b2.run()
+        got = b2.read_state()
+    assert_same_state(got, full, wl.ell, wl.s, what="restored")
+
+
+def test_ragged_memory_sizes_and_odd_tapes(rasp):
+    """Mixed n across every bucket (odd n, n = 1, n >= 2048), odd l and s,
+    empty programs, cap 0."""
+    rng = np.random.default_rng(3)
+    ns = [1, 2, 3, 5, 7, 63, 64, 65, 127, 255, 256, 257, 511, 700, 1000, 1500, 3000, 4096]
+    progs, tapes, nn, caps = [], [], [], []
+    for v in range(1500):
+        n = ns[v % len(ns)]
+        m = int(rng.integers(0, n // 2 + 1))
+        ops = rng.integers(0, 9, size=m)
+        args = rng.integers(-2, n + 2, size=m)
+        progs.append([int(x) for pair in zip(ops, args) for x in pair])
+        tapes.append([int(x) for x in rng.integers(-50, 50, size=int(rng.integers(0, 4)))])
+        nn.append(n)
+        caps.append(int(rng.choice([0, 1, 50, 400])))
+    wl = wl_from(progs, tapes, nn, caps, 3, 5)
+    st, _ = oracle_state(wl)
+    for sched in SCHEDS.values():
+        for disp in DISPATCH.values():
+            got, _ = run_gpu(rasp, wl, sched | disp)
+            assert_same_state(got, st, 3, 5, what="ragged %x" % (sched | disp))
+
+
+def test_instruction_counter_wraps_at_word_boundary(rasp):
+    """Place i just below 2^w (via a restored state) so that i (+) 1 and i (+) 2 wrap."""
+    from oracle import oracle
+    for w, n in ((64, 250), (64, 256), (16, 250), (8, 7)):
+        wl = wl_from([asm((LOD, 3))] * 4, [[]] * 4, n, 40, 1, 1, w=w)
+        mask = (1 << w) - 1
+        st = oracle.pack(wl.programs, wl.prog_off, wl.mem_words, wl.tapes, wl.tape_off, 1, 1, w=w)
+        i0 = [mask, mask - 1, mask - 2, mask - 3]
+        rng = np.random.default_rng(w + n)
+        st.i[:] = np.array(i0, np.uint64)
+        st.mem[:] = rng.integers(0, 8, size=st.mem.shape[0]).astype(np.uint64)
+        with rasp.Batch(wl.mem_words, 1, 1, word_bits=w) as b:
+            b.load_workload(wl)
+            b.load_state(dict(i=st.i.view(np.int64), mem=st.mem.view(np.int64)))
+            b.run()
+            got = b.read_state()
+        oracle.run(st, caps=wl.caps)
+        assert_same_state(got, st, 1, 1, what="wrap w=%d n=%d" % (w, n))
+
+
+def test_shared_programs_match_expanded(rasp):
+    base = W.template_programs(num_vms=64, seed=5, instructions=48, mem_words=224, tape_len=8)
+    V = 64 * 50
+    prog_of_vm = np.repeat(np.arange(64, dtype=np.uint32), 50)
+    ids = np.arange(V, dtype=np.uint64)
+    tape = W.uniform_int(W.draws(5, 9, ids, 8), -50, 50).reshape(-1)
+    wl = W.Workload("shared", base.programs, base.prog_off, np.full(V, 224, np.uint32), tape,
+                    np.arange(V + 1, dtype=np.uint64) * 8, np.full(V, 2048, np.uint64), 8, 8,
+                    prog_of_vm=prog_of_vm)
+    st, _ = oracle_state(wl)
+    for sched in SCHEDS.values():
+        got, _ = run_gpu(rasp, wl, sched)
+        assert_same_state(got, st, 8, 8, what="shared %x" % sched)
+
+
+def test_argument_errors(rasp):
+    R = rasp
+    wl = W.random_programs(num_vms=8)
+    with pytest.raises(R.RaspError) as e:
+        R.Batch(wl.mem_words, 4, 8, word_bits=1)
+    assert e.value.code == R.RASP_EINVAL
+    with pytest.raises(R.RaspError):
+        R.Batch(wl.mem_words, 4, 8, word_bits=32, semantics=R.CHECKED)
+    with pytest.raises(R.RaspError):
+        R.Batch(np.array([64, 0], np.uint32), 4, 8)
+    with R.Batch(wl.mem_words, 4, 8) as b:
+        with pytest.raises(R.RaspError) as e:
+            b.run()
+        assert e.value.code == R.RASP_ESTATE
+        bad = wl.prog_off.copy()
+        bad[1] = 3
+        with pytest.raises(R.RaspError):
+            b.load_programs(wl.programs, bad)
+        with pytest.raises(R.RaspError):                          # program longer than n
+            b.load_programs(np.zeros(8 * 66, np.int64), np.arange(9, dtype=np.uint64) * 66)
+        b.load_programs(wl.programs, wl.prog_off)
+        with pytest.raises(R.RaspError):                          # |x| > l
+            b.load_inputs(np.zeros(40, np.int64), np.arange(9, dtype=np.uint64) * 5)
+        b.load_inputs(wl.tapes, wl.tape_off, wl.caps)
+        b.run()
+        with pytest.raises(R.RaspError):
+            b.read_state(first=5, count=10)

@@ -82,6 +82,9 @@ typedef struct rasp_config {
     uint32_t out_cap;    /* s: output capacity (y holds s+1 words)             */
     uint32_t flags;      /* RASP_SCHED_* | RASP_DISPATCH_* | RASP_COLLECT_STATS */
     uint32_t epoch;      /* steps between warp scheduling points; 0 = default  */
+    uint32_t warps_per_cta; /* persistent kernels: warps per CTA; 0 = default  */
+    uint32_t refill_min; /* persistent kernels: idle lanes that trigger a
+                            refill; 0 = default                               */
     void*    stream;     /* cudaStream_t for all work of the batch; NULL = the
                             legacy default stream                              */
     void*    arena;      /* optional caller-owned device memory for the batch;
@@ -176,6 +179,12 @@ int rasp_load_state(rasp_batch* b, uint64_t first, uint64_t count,
 
 /* Aggregate counters of the batch (synchronises the stream). */
 int rasp_read_stats(rasp_batch* b, rasp_stats* out);
+
+/* Describe the launch plan as JSON into buf (NUL-terminated): per memory
+ * bucket its size class, VM count, schedule, grid, warps per CTA, resident
+ * CTAs per SM, shared memory, epoch and refill threshold. EINVAL if buf is
+ * too small. Does not touch the GPU. */
+int rasp_describe(const rasp_batch* b, char* buf, uint64_t size);
 
 /* Free the batch (synchronises its stream first). NULL is a no-op. */
 void rasp_batch_destroy(rasp_batch* b);

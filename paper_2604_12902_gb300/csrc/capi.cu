@@ -187,7 +187,10 @@ void plan_buckets(rasp_batch* b) {
       sh.staged = false;
       sh.warps = 4;
       sh.refill_min = 1;
+      sh.epoch = b->cfg.epoch ? b->cfg.epoch : 16u;
     }
+    if (b->cfg.warps_per_cta) sh.warps = std::min<uint32_t>(b->cfg.warps_per_cta, 8u);
+    if (b->cfg.refill_min) sh.refill_min = std::min<uint32_t>(b->cfg.refill_min, 32u);
     if (sched != RASP_SCHED_PLAIN) {
       if (persist_configure(var, sh) == 0) {
         k.sched = RASP_SCHED_PLAIN;        // cannot be resident: fall back to the plain form
@@ -593,6 +596,28 @@ int rasp_read_stats(rasp_batch* b, rasp_stats* out) {
   out->pri_full = hist[8];
   out->bnz_taken = hist[9];
   out->launches = b->launches;
+  return RASP_OK;
+}
+
+int rasp_describe(const rasp_batch* b, char* buf, uint64_t size) {
+  if (!b || !buf || size == 0) return fail(RASP_EINVAL, "batch or buffer is NULL");
+  static const char* names[] = {"auto", "plain", "persist", "persist_gl"};
+  std::string s = "{\"vms\": " + std::to_string(b->V) + ", \"buckets\": [";
+  bool first = true;
+  for (const Bucket& k : b->buckets) {
+    if (!k.count) continue;
+    char tmp[512];
+    snprintf(tmp, sizeof(tmp),
+             "%s{\"n_max\": %u, \"vms\": %u, \"schedule\": \"%s\", \"grid\": %u, \"warps_per_cta\": %u, "
+             "\"ctas_per_sm\": %u, \"smem\": %zu, \"epoch\": %u, \"refill_min\": %u}",
+             first ? "" : ", ", k.ncap, k.count, names[(k.sched >> 4) & 3], k.shape.grid, k.shape.warps,
+             k.shape.ctas_per_sm, k.shape.smem, k.shape.epoch, k.shape.refill_min);
+    s += tmp;
+    first = false;
+  }
+  s += "]}";
+  if (s.size() + 1 > size) return fail(RASP_EINVAL, "buffer of %llu bytes is too small", (unsigned long long)size);
+  memcpy(buf, s.c_str(), s.size() + 1);
   return RASP_OK;
 }
 

@@ -2,12 +2,14 @@
 //
 // One call of `one_step` applies the Sec. 2.1 transition of "Towards a
 // Linear-Algebraic Hypervisor" to one machine held in registers (i, a, u_0,
-// y_0, steps) plus its memory M, tape u_1..u_l and output y_1..y_s (in shared
-// memory or HBM, whichever the schedule chose). The case equation is
-// evaluated in its guarded-sum form (Sec. 2.1, Phi_w(c) = sum_psi
-// eta_psi(c) Phi_psi(c), exactly one guard true): every candidate update is
-// formed and the guards select, so a warp whose lanes hold different opcodes
-// executes one instruction stream.
+// y_0, a step countdown) plus its memory M, tape u_1..u_l and output
+// y_1..y_s (in shared memory or HBM, whichever the schedule chose). The case
+// equation is evaluated in its guarded-sum form (Sec. 2.1, Phi_w(c) =
+// sum_psi eta_psi(c) Phi_psi(c), exactly one guard true): the candidate
+// updates of LOD/ADD/MUL/STO/BNZ are formed and the guards select, so a warp
+// whose lanes hold different opcodes runs one instruction stream. RD and PRI
+// (a few steps per program), fetches that straddle the end of memory,
+// operands outside [0, n) and the wrap of i at 2^w take short side paths.
 #pragma once
 
 #include <cstdint>
@@ -53,13 +55,26 @@ struct Queue {
   uint32_t* head;             // next unclaimed position (reset to 0 per launch)
 };
 
-// Registers of one machine while it runs.
+// Registers of one machine while it runs. The instruction counter is kept
+// as i = ibase + ip with ip = i mod n; ibase is 0 while i < n, which is
+// where programs spend their time, so the common step touches only the
+// 32-bit ip. Steps are counted down in 32 bits: the machine has taken
+// steps + (left0 - left) steps; the 64-bit stop/cap are consulted only when
+// the countdown reaches zero.
 struct Regs {
-  uint64_t i, a, steps, stop, cap;
+  uint64_t a;
+  uint64_t ibase;             // i - (i mod n)
+  uint64_t steps;             // steps at the start of the current countdown
+  uint64_t stop, cap;         // min(budget, cap) and cap
+  uint32_t left0, left;       // countdown start and remaining
   uint32_t ip;                // i mod n
   uint32_t n;
+  uint32_t ilim;              // min(n, 2^w): while ibase = 0, ip + 2 < ilim means i (+) 2 = ip + 2 < n
   uint32_t u0, y0;
 };
+
+__device__ __forceinline__ uint64_t i_of(const Regs& r) { return r.ibase + (uint64_t)r.ip; }
+__device__ __forceinline__ uint64_t steps_of(const Regs& r) { return r.steps + (uint64_t)(r.left0 - r.left); }
 
 struct Hist {
   uint32_t c[10];
@@ -69,103 +84,196 @@ struct Hist {
   }
 };
 
-__device__ __forceinline__ uint32_t mod_n(uint64_t x, uint32_t n) {
-  // x mod n on the unsigned value (words are bit vectors, Sec. 2.1).
-  if (x < n) return (uint32_t)x;
-  if ((n & (n - 1)) == 0) return (uint32_t)(x & (n - 1));
+static __device__ __noinline__ uint32_t mod_n_slow(uint64_t x, uint32_t n) {
+  if ((n & (n - 1u)) == 0u) return (uint32_t)(x & (uint64_t)(n - 1u));
   return (uint32_t)(x % n);
 }
 
-// One transition (or the decision that none applies).
-// Returns CONT after applying a step, otherwise the machine's final status
-// for this run: HALTED (fixed point), a CHECKED fault, or, when
-// steps >= stop, TIMEOUT (steps >= cap) / RUNNING (budget reached).
-template <bool MASKED, bool CHECKED, bool HIST>
-__device__ __forceinline__ uint32_t one_step(uint64_t* __restrict__ M,
-                                             const uint64_t* __restrict__ T,
-                                             uint64_t* __restrict__ Y,
-                                             const Params& P, Regs& r, Hist& h) {
+// x mod n on the unsigned value (words are bit vectors, Sec. 2.1).
+__device__ __forceinline__ uint32_t mod_n(uint64_t x, uint32_t n) {
+  return (x < (uint64_t)n) ? (uint32_t)x : mod_n_slow(x, n);
+}
+
+// Start a fresh 32-bit countdown toward stop; false if steps >= stop already.
+__device__ __forceinline__ bool arm_countdown(Regs& r) {
+  if (r.steps >= r.stop) {
+    r.left0 = r.left = 0;
+    return false;
+  }
+  const uint64_t rem = r.stop - r.steps;
+  r.left0 = r.left = rem > 0xFFFFFFFFull ? 0xFFFFFFFFu : (uint32_t)rem;
+  return true;
+}
+
+struct Countdown {
+  uint64_t steps;
+  uint32_t left;
+  uint32_t status;   // CONT: re-armed; else TIMEOUT / RUNNING at the stop
+};
+
+// The countdown reached zero (left == 0) and the machine is not a fixed
+// point: either the stop is reached or a new countdown starts.
+static __device__ __noinline__ Countdown countdown_next(uint64_t steps, uint32_t left0, uint64_t stop, uint64_t cap) {
+  Countdown c;
+  c.steps = steps + left0;
+  if (c.steps >= stop) {
+    c.left = 0;
+    c.status = c.steps >= cap ? ST_TIMEOUT : ST_RUNNING;
+    return c;
+  }
+  const uint64_t rem = stop - c.steps;
+  c.left = rem > 0xFFFFFFFFull ? 0xFFFFFFFFu : (uint32_t)rem;
+  c.status = CONT;
+  return c;
+}
+
+__device__ __forceinline__ uint32_t on_countdown_zero(Regs& r) {
+  const Countdown c = countdown_next(r.steps, r.left0, r.stop, r.cap);
+  r.steps = c.steps;
+  r.left0 = r.left = c.left;
+  return c.status;
+}
+
+// Result of fetching and decoding the next transition.
+struct Decoded {
+  uint64_t j;
+  uint32_t op;      // 1..7, 0 for an invalid opcode
+  uint32_t jm;      // j mod n
+  bool jin;         // j < n
+  bool taken;       // BNZ with a != 0
+};
+
+// <o, j> = <M[i mod n], M[(i (+) 1) mod n]> when the pair is not one aligned
+// 16-byte word (odd n or odd i mod n, or i = 2^w - 1 where i (+) 1 wraps to 0).
+template <class WordPtr>
+__device__ __noinline__ ulonglong2 fetch_slow(WordPtr M, uint32_t ip, uint32_t n, uint64_t i, uint64_t wm) {
+  if (!(ip & 1u) && ip + 1u < n && i != wm) return *reinterpret_cast<const ulonglong2*>(M + ip);
+  ulonglong2 oj;
+  oj.x = M[ip];
+  uint32_t k1 = (i == wm) ? 0u : ip + 1u;
+  if (k1 == n) k1 = 0u;
+  oj.y = M[k1];
+  return oj;
+}
+
+// Fetch, decode and evaluate the guards of the next transition. Returns CONT
+// if the transition applies (d filled), else the machine's final status for
+// this run: HALTED (fixed point), a CHECKED fault, or TIMEOUT / RUNNING at
+// the step stop.
+template <bool MASKED, bool CHECKED>
+__device__ __forceinline__ uint32_t decode(uint64_t* __restrict__ M, const Params& P, Regs& r, Decoded& d) {
   const uint64_t wm = MASKED ? P.wmask : ~0ull;
-  const uint64_t i = r.i, a = r.a;
   const uint32_t ip = r.ip, n = r.n;
-  if (CHECKED) {
+  const bool wide = r.ibase != 0ull;      // i >= n
+  if constexpr (CHECKED) {
     // without circular addressing the fetch needs i, i+1 in [0, n)
-    if (!(i < (uint64_t)n - 1)) {
-      if (r.steps >= r.stop) return r.steps >= r.cap ? ST_TIMEOUT : ST_RUNNING;
+    if (wide | (ip + 1u >= n)) {
+      if (r.left == 0u) {
+        const uint32_t s = on_countdown_zero(r);
+        if (s != CONT) return s;
+      }
       return ST_FAULT_ADDR;
     }
   }
-  // fetch <o, j> = <M[i mod n], M[(i (+) 1) mod n]>
-  uint64_t o, j;
-  if (!(ip & 1u) && ip + 1u < n && i != wm) {
-    const ulonglong2 oj = *reinterpret_cast<const ulonglong2*>(M + ip);
-    o = oj.x;
-    j = oj.y;
+  ulonglong2 oj;
+  if (((ip | n) & 1u) == 0u) {
+    // even n and even i mod n: i is even (ibase is a multiple of n), so
+    // i != 2^w - 1 and M[ip], M[ip+1] is one aligned 16-byte word
+    oj = *reinterpret_cast<const ulonglong2*>(M + ip);
   } else {
-    o = M[ip];
-    uint32_t k1 = (i == wm) ? 0u : ip + 1u;   // i (+) 1 wraps to 0 at i = 2^w - 1
-    if (k1 == n) k1 = 0u;
-    j = M[k1];
+    oj = fetch_slow(M, ip, n, i_of(r), wm);
   }
-  const uint32_t jm = mod_n(j, n);
-  const bool valid = (o - 1ull) < 7ull;
-  const uint32_t op = valid ? (uint32_t)o : 0u;
-  // guards of the "otherwise" case: c -> c
-  const bool fixed = !valid || (op == 6u && r.u0 >= P.ell) || (op == 5u && a != 0 && j == i);
-  if (fixed) return ST_HALTED;
-  if (r.steps >= r.stop) return r.steps >= r.cap ? ST_TIMEOUT : ST_RUNNING;
-  if (CHECKED) {
-    if (op != 1u && op != 5u && j >= (uint64_t)n) return ST_FAULT_ADDR;
+  const uint64_t o = oj.x, j = oj.y;
+  d.j = j;
+  d.jin = j < (uint64_t)n;
+  d.jm = d.jin ? (uint32_t)j : mod_n_slow(j, n);
+  d.op = ((o - 1ull) < 7ull) ? (uint32_t)o : 0u;
+  d.taken = (d.op == 5u) & (r.a != 0ull);
+  // guards of the "otherwise" case (c -> c): invalid opcode, RD at the end
+  // of the tape, BNZ to itself (j == i; while i < n that is j < n and
+  // j == i mod n)
+  bool fixed = (d.op == 0u) | ((d.op == 6u) & (r.u0 >= P.ell)) | (d.taken & d.jin & ((uint32_t)j == ip) & !wide);
+  if (wide && d.taken && j == i_of(r)) fixed = true;
+  if (fixed | (r.left == 0u)) {
+    if (fixed) return ST_HALTED;
+    const uint32_t s = on_countdown_zero(r);
+    if (s != CONT) return s;
   }
-  uint64_t v = 0;
-  if (op == 2u || op == 3u || op == 7u) v = M[jm];
-  const uint64_t sum = a + v;
-  const uint64_t prod = a * v;
-  if (CHECKED) {
-    if (op == 2u && (int64_t)((a ^ sum) & (v ^ sum)) < 0) return ST_FAULT_OVERFLOW;
-    if (op == 3u) {
-      const int64_t hi = __mul64hi((long long)a, (long long)v);
-      if (hi != ((int64_t)prod >> 63)) return ST_FAULT_OVERFLOW;
+  if constexpr (CHECKED) {
+    if ((d.op != 1u) & (d.op != 5u) & !d.jin) return ST_FAULT_ADDR;
+  }
+  return CONT;
+}
+
+// i <- j (taken BNZ) or i (+) 2, kept as ibase + ip.
+template <bool MASKED>
+__device__ __forceinline__ void advance(const Params& P, Regs& r, const Decoded& d) {
+  if (d.taken) {
+    r.ip = d.jm;
+    r.ibase = d.jin ? 0ull : d.j - d.jm;
+  } else {
+    uint32_t nip = r.ip + 2u;
+    if ((r.ibase != 0ull) | (nip >= r.ilim)) {
+      // end of memory, i >= n, or i (+) 2 wraps at 2^w
+      const uint64_t wm = MASKED ? P.wmask : ~0ull;
+      const uint64_t ni = (i_of(r) + 2ull) & wm;
+      nip = mod_n(ni, r.n);
+      r.ibase = ni - nip;
     }
-  }
-  uint64_t na = a;
-  na = (op == 1u) ? j : na;
-  na = (op == 2u) ? sum : na;
-  na = (op == 3u) ? prod : na;
-  if (MASKED) na &= wm;
-  // M_{j mod n} <- a (STO) or <- u-bullet (RD); u-triangle advances the head
-  if (op == 4u) M[jm] = a;
-  if (op == 6u) {
-    M[jm] = T[r.u0];
-    r.u0 += 1u;
-  }
-  // y :: M_{j mod n}
-  const bool put = (op == 7u) && (r.y0 < P.s);
-  if (put) {
-    Y[r.y0] = v;
-    r.y0 += 1u;
-  }
-  const bool taken = (op == 5u) && (a != 0);
-  if (taken) {
-    r.i = j;
-    r.ip = jm;
-  } else {
-    const uint64_t ni = (i + 2ull) & wm;
-    uint32_t nip = ip + 2u;
-    if (nip >= n) nip -= n;
-    if (nip >= n) nip -= n;
-    if (ni < i) nip = (ni < n) ? (uint32_t)ni : 0u;   // i (+) 2 wrapped past 2^w
-    r.i = ni;
     r.ip = nip;
   }
-  r.a = na;
-  r.steps += 1ull;
-  if (HIST) {
+  r.left -= 1u;
+}
+
+template <bool HIST>
+__device__ __forceinline__ void count_step(Hist& h, uint32_t op, bool taken) {
+  if constexpr (HIST) {
 #pragma unroll
     for (uint32_t k = 1; k <= 7; ++k) h.c[k] += (op == k) ? 1u : 0u;
-    h.c[8] += (op == 7u && !put) ? 1u : 0u;
     h.c[9] += taken ? 1u : 0u;
   }
+}
+
+// One transition in guarded-sum form. Returns CONT after applying it, else
+// the final status (see decode).
+template <bool MASKED, bool CHECKED, bool HIST>
+__device__ __forceinline__ uint32_t one_step(uint64_t* __restrict__ M, const uint64_t* __restrict__ T,
+                                             uint64_t* __restrict__ Y, const Params& P, Regs& r, Hist& h) {
+  Decoded d;
+  const uint32_t s = decode<MASKED, CHECKED>(M, P, r, d);
+  if (s != CONT) return s;
+  const uint32_t op = d.op, jm = d.jm;
+  const uint64_t a = r.a;
+  uint64_t v = 0;
+  if ((op == 2u) | (op == 3u)) v = M[jm];
+  const uint64_t sum = a + v;
+  const uint64_t prod = a * v;
+  if constexpr (CHECKED) {
+    if ((op == 2u) & ((int64_t)((a ^ sum) & (v ^ sum)) < 0)) return ST_FAULT_OVERFLOW;
+    if ((op == 3u) && __mul64hi((long long)a, (long long)v) != ((int64_t)prod >> 63)) return ST_FAULT_OVERFLOW;
+  }
+  uint64_t na = (op == 1u) ? d.j : a;
+  na = (op == 2u) ? sum : na;
+  na = (op == 3u) ? prod : na;
+  if (MASKED) na &= P.wmask;
+  if (op == 4u) M[jm] = a;                       // M_{j mod n} <- a
+  if (op >= 6u) {
+    if (op == 6u) {                              // M_{j mod n} <- u-bullet; u-triangle
+      M[jm] = T[r.u0];
+      r.u0 += 1u;
+    } else {                                     // y :: M_{j mod n}
+      const uint64_t pv = M[jm];
+      if (r.y0 < P.s) {
+        Y[r.y0] = pv;
+        r.y0 += 1u;
+      } else if (HIST) {
+        h.c[8] += 1u;
+      }
+    }
+  }
+  r.a = na;
+  advance<MASKED>(P, r, d);
+  count_step<HIST>(h, op, d.taken);
   return CONT;
 }
 
@@ -183,23 +291,32 @@ __device__ __forceinline__ void flush_hist(const Params& P, Hist& h) {
   }
 }
 
-// Load the registers of VM v from the state store.
+// Registers of VM v, read from the state store (i goes to ibase until
+// arm_regs splits it).
 __device__ __forceinline__ void load_regs(const DevState& S, const Params& P, uint32_t v, Regs& r) {
-  r.i = S.i[v];
+  r.ibase = S.i[v];
   r.a = S.a[v];
   r.steps = S.steps[v];
   r.cap = S.cap[v];
   r.n = S.n[v];
   r.u0 = S.uhead[v];
   r.y0 = S.ylen[v];
+}
+
+// Derived registers once the loads of load_regs have landed.
+__device__ __forceinline__ void arm_regs(const Params& P, Regs& r) {
+  const uint64_t i = r.ibase;
   r.stop = P.budget < r.cap ? P.budget : r.cap;
-  r.ip = mod_n(r.i, r.n);
+  r.ip = mod_n(i, r.n);
+  r.ibase = i - r.ip;
+  r.ilim = (P.wmask >= (uint64_t)r.n - 1u) ? r.n : (uint32_t)(P.wmask + 1ull);
+  arm_countdown(r);
 }
 
 __device__ __forceinline__ void store_regs(const DevState& S, uint32_t v, const Regs& r, uint32_t st) {
-  S.i[v] = r.i;
+  S.i[v] = i_of(r);
   S.a[v] = r.a;
-  S.steps[v] = r.steps;
+  S.steps[v] = steps_of(r);
   S.uhead[v] = r.u0;
   S.ylen[v] = r.y0;
   S.status[v] = (uint8_t)st;

@@ -25,6 +25,7 @@ struct PersistShape {
   uint32_t epoch;       // steps between warp scheduling points
   uint32_t refill_min;  // idle lanes that trigger a refill
   uint32_t grid;        // CTAs
+  uint32_t ctas_per_sm; // resident CTAs per SM (occupancy)
   size_t smem;          // dynamic shared memory per CTA
 };
 

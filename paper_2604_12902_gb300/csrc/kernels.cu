@@ -68,49 +68,27 @@ __global__ void __launch_bounds__(256) k_pack(DevState S, const uint64_t* __rest
 
 // ------------------------------------------------------------------ vote step
 // Warp-synchronous step: every lane of the warp calls it; `active` lanes
-// take part. Returns CONT or a final status like one_step.
+// take part. Lanes are grouped by opcode with __match_any_sync and each group
+// runs the handler of its case of the Sec. 2.1 equation. Returns CONT or a
+// final status like one_step.
 template <bool MASKED, bool CHECKED, bool HIST>
 __device__ __forceinline__ uint32_t vote_step(uint64_t* __restrict__ M, const uint64_t* __restrict__ T,
                                               uint64_t* __restrict__ Y, const Params& P, Regs& r, Hist& h,
                                               bool active) {
-  const uint64_t wm = MASKED ? P.wmask : ~0ull;
-  const uint64_t i = r.i, a = r.a;
-  const uint32_t ip = r.ip, n = r.n;
+  Decoded d;
+  d.j = 0;
+  d.op = 0;
+  d.jm = 0;
+  d.jin = false;
+  d.taken = false;
   uint32_t result = CONT;
-  uint32_t op = 0;
-  uint64_t j = 0;
-  uint32_t jm = 0;
-  if (active) {
-    bool fetch_fault = false;
-    if (CHECKED) fetch_fault = !(i < (uint64_t)n - 1);
-    if (fetch_fault) {
-      result = (r.steps >= r.stop) ? (r.steps >= r.cap ? ST_TIMEOUT : ST_RUNNING) : ST_FAULT_ADDR;
-    } else {
-      uint64_t o;
-      if (!(ip & 1u) && ip + 1u < n && i != wm) {
-        const ulonglong2 oj = *reinterpret_cast<const ulonglong2*>(M + ip);
-        o = oj.x;
-        j = oj.y;
-      } else {
-        o = M[ip];
-        uint32_t k1 = (i == wm) ? 0u : ip + 1u;
-        if (k1 == n) k1 = 0u;
-        j = M[k1];
-      }
-      jm = mod_n(j, n);
-      const bool valid = (o - 1ull) < 7ull;
-      op = valid ? (uint32_t)o : 0u;
-      const bool fixed = !valid || (op == 6u && r.u0 >= P.ell) || (op == 5u && a != 0 && j == i);
-      if (fixed) result = ST_HALTED;
-      else if (r.steps >= r.stop) result = r.steps >= r.cap ? ST_TIMEOUT : ST_RUNNING;
-      else if (CHECKED && op != 1u && op != 5u && j >= (uint64_t)n) result = ST_FAULT_ADDR;
-    }
-  }
-  const uint32_t exec_op = (active && result == CONT) ? op : 0u;
+  if (active) result = decode<MASKED, CHECKED>(M, P, r, d);
+  const uint32_t exec_op = (active && result == CONT) ? d.op : 0u;
   uint32_t pend = __ballot_sync(FULL, exec_op != 0u);
   const uint32_t peers = __match_any_sync(FULL, exec_op);
   const uint32_t lane = threadIdx.x & 31u;
-  bool taken = false;
+  const uint64_t a = r.a;
+  const uint64_t wm = MASKED ? P.wmask : ~0ull;
   while (pend) {
     const int leader = __ffs(pend) - 1;
     const uint32_t gop = __shfl_sync(FULL, exec_op, leader);
@@ -118,34 +96,33 @@ __device__ __forceinline__ uint32_t vote_step(uint64_t* __restrict__ M, const ui
     if (grp & (1u << lane)) {
       switch (gop) {   // uniform over the group
         case 1u:       // LOD
-          r.a = MASKED ? (j & wm) : j;
+          r.a = d.j & wm;
           break;
         case 2u: {     // ADD
-          const uint64_t v = M[jm];
+          const uint64_t v = M[d.jm];
           const uint64_t s = a + v;
           if (CHECKED && (int64_t)((a ^ s) & (v ^ s)) < 0) result = ST_FAULT_OVERFLOW;
-          else r.a = MASKED ? (s & wm) : s;
+          else r.a = s & wm;
           break;
         }
         case 3u: {     // MUL
-          const uint64_t v = M[jm];
+          const uint64_t v = M[d.jm];
           const uint64_t p = a * v;
           if (CHECKED && __mul64hi((long long)a, (long long)v) != ((int64_t)p >> 63)) result = ST_FAULT_OVERFLOW;
-          else r.a = MASKED ? (p & wm) : p;
+          else r.a = p & wm;
           break;
         }
         case 4u:       // STO
-          M[jm] = a;
+          M[d.jm] = a;
           break;
-        case 5u:       // BNZ
-          taken = (a != 0);
+        case 5u:       // BNZ: the jump itself is taken in advance()
           break;
         case 6u:       // RD
-          M[jm] = T[r.u0];
+          M[d.jm] = T[r.u0];
           r.u0 += 1u;
           break;
         default: {     // PRI
-          const uint64_t v = M[jm];
+          const uint64_t v = M[d.jm];
           if (r.y0 < P.s) {
             Y[r.y0] = v;
             r.y0 += 1u;
@@ -159,24 +136,8 @@ __device__ __forceinline__ uint32_t vote_step(uint64_t* __restrict__ M, const ui
     pend &= ~grp;
   }
   if (exec_op != 0u && result == CONT) {
-    if (taken) {
-      r.i = j;
-      r.ip = jm;
-    } else {
-      const uint64_t ni = (i + 2ull) & wm;
-      uint32_t nip = ip + 2u;
-      if (nip >= n) nip -= n;
-      if (nip >= n) nip -= n;
-      if (ni < i) nip = (ni < n) ? (uint32_t)ni : 0u;
-      r.i = ni;
-      r.ip = nip;
-    }
-    r.steps += 1ull;
-    if (HIST) {
-#pragma unroll
-      for (uint32_t k = 1; k <= 7; ++k) h.c[k] += (exec_op == k) ? 1u : 0u;
-      h.c[9] += taken ? 1u : 0u;
-    }
+    advance<MASKED>(P, r, d);
+    count_step<HIST>(h, exec_op, d.taken);
   }
   return result;
 }
@@ -190,7 +151,7 @@ __global__ void __launch_bounds__(256) k_plain(DevState S, Params P, const uint3
   h.zero();
   bool active = false;
   uint32_t v = 0;
-  Regs r;
+  Regs r{};
   uint64_t* M = nullptr;
   const uint64_t* T = nullptr;
   uint64_t* Y = nullptr;
@@ -198,6 +159,7 @@ __global__ void __launch_bounds__(256) k_plain(DevState S, Params P, const uint3
     v = ids ? ids[t] : t;
     if (S.status[v] == ST_RUNNING) {
       load_regs(S, P, v, r);
+      arm_regs(P, r);
       M = S.mem + S.mem_off[v];
       T = S.tape + (uint64_t)v * P.ellp;
       Y = S.y + (uint64_t)v * P.sp;
@@ -224,8 +186,33 @@ __global__ void __launch_bounds__(256) k_plain(DevState S, Params P, const uint3
   flush_hist<HIST>(P, h);
 }
 
-// ------------------------------------------------------------------ persistent
-template <bool MASKED, bool CHECKED, bool HIST, bool VOTE, bool STAGED>
+// Run `epoch` steps of every active lane (warp-uniform loop).
+template <bool MASKED, bool CHECKED, bool HIST, bool VOTE>
+__device__ __forceinline__ void run_epoch(uint64_t* M, const uint64_t* T, uint64_t* Y, const Params& P, Regs& r,
+                                          Hist& h, bool& active, uint32_t& final_st, uint32_t epoch) {
+  if (VOTE) {
+    for (uint32_t t = 0; t < epoch; ++t) {
+      const uint32_t s = vote_step<MASKED, CHECKED, HIST>(M, T, Y, P, r, h, active);
+      if (active && s != CONT) {
+        active = false;
+        final_st = s;
+      }
+    }
+  } else {
+    for (uint32_t t = 0; t < epoch; ++t) {
+      if (active) {
+        const uint32_t s = one_step<MASKED, CHECKED, HIST>(M, T, Y, P, r, h);
+        if (s != CONT) {
+          active = false;
+          final_st = s;
+        }
+      }
+    }
+  }
+}
+
+// ------------------------------------------------------------------ persistent, staged in SMEM
+template <bool MASKED, bool CHECKED, bool HIST, bool VOTE>
 __global__ void __launch_bounds__(256) k_persist(DevState S, Params P, Queue Q, uint32_t ncap,
                                                  uint32_t slot_words, uint32_t epoch, uint32_t refill_min) {
   extern __shared__ __align__(16) uint64_t smem[];
@@ -237,24 +224,21 @@ __global__ void __launch_bounds__(256) k_persist(DevState S, Params P, Queue Q, 
   const uint32_t bar = smem_addr(wbase + lane);
   const uint32_t slot_s = smem_addr(slot);
   uint32_t phase = 0;
-  if (STAGED) {
-    mbar_init(bar, 1);
-    fence_mbar_init();
-  }
+  mbar_init(bar, 1);
+  fence_mbar_init();
   __syncwarp();
 
   Hist h;
   h.zero();
-  Regs r;
-  r.i = r.a = r.steps = r.stop = r.cap = 0;
-  r.ip = 0; r.n = 1; r.u0 = r.y0 = 0;
+  Regs r{};
+  r.n = 1;
   int32_t vm = -1;
   bool active = false, exhausted = false, dead = false;
   uint32_t final_st = ST_RUNNING;
   uint64_t moff = 0;
   uint64_t* M = slot;
-  const uint64_t* T = slot;
-  uint64_t* Y = slot;
+  const uint64_t* T = slot + ncap;
+  uint64_t* Y = slot + ncap + P.ellp;
   const uint32_t tbytes = P.ellp * 8u, ybytes = P.sp * 8u;
 
   for (;;) {
@@ -282,28 +266,20 @@ __global__ void __launch_bounds__(256) k_persist(DevState S, Params P, Queue Q, 
         }
       }
       if (fresh) {
-        if (STAGED) {
-          const uint32_t mbytes = ((r.n + 1u) & ~1u) * 8u;
-          mbar_arrive_expect_tx(bar, mbytes + tbytes + ybytes);
-          bulk_g2s(slot_s, S.mem + moff, mbytes, bar);
-          if (tbytes) bulk_g2s(slot_s + ncap * 8u, S.tape + (uint64_t)vm * P.ellp, tbytes, bar);
-          if (ybytes) bulk_g2s(slot_s + (ncap + P.ellp) * 8u, S.y + (uint64_t)vm * P.sp, ybytes, bar);
-          M = slot;
-          T = slot + ncap;
-          Y = slot + ncap + P.ellp;
-          if (!mbar_wait_bounded(bar, phase, WAIT_LIMIT)) {
-            atomicExch(P.err, ERR_WAIT_TIMEOUT);
-            dead = true;          // copies may still land: never touch the slot again
-            exhausted = true;
-            vm = -1;
-            fresh = false;
-          }
-          phase ^= 1u;
-        } else {
-          M = S.mem + moff;
-          T = S.tape + (uint64_t)vm * P.ellp;
-          Y = S.y + (uint64_t)vm * P.sp;
+        arm_regs(P, r);
+        const uint32_t mbytes = ((r.n + 1u) & ~1u) * 8u;
+        mbar_arrive_expect_tx(bar, mbytes + tbytes + ybytes);
+        bulk_g2s(slot_s, S.mem + moff, mbytes, bar);
+        if (tbytes) bulk_g2s(slot_s + ncap * 8u, S.tape + (uint64_t)vm * P.ellp, tbytes, bar);
+        if (ybytes) bulk_g2s(slot_s + (ncap + P.ellp) * 8u, S.y + (uint64_t)vm * P.sp, ybytes, bar);
+        if (!mbar_wait_bounded(bar, phase, WAIT_LIMIT)) {
+          atomicExch(P.err, ERR_WAIT_TIMEOUT);
+          dead = true;          // copies may still land: never touch the slot again
+          exhausted = true;
+          vm = -1;
+          fresh = false;
         }
+        phase ^= 1u;
         active = fresh;
       }
     }
@@ -312,25 +288,7 @@ __global__ void __launch_bounds__(256) k_persist(DevState S, Params P, Queue Q, 
 
     // ---- run until enough lanes can be refilled (checked every `epoch` steps)
     for (;;) {
-      if (VOTE) {
-        for (uint32_t t = 0; t < epoch; ++t) {
-          const uint32_t s = vote_step<MASKED, CHECKED, HIST>(M, T, Y, P, r, h, active);
-          if (active && s != CONT) {
-            active = false;
-            final_st = s;
-          }
-        }
-      } else {
-        for (uint32_t t = 0; t < epoch; ++t) {
-          if (active) {
-            const uint32_t s = one_step<MASKED, CHECKED, HIST>(M, T, Y, P, r, h);
-            if (s != CONT) {
-              active = false;
-              final_st = s;
-            }
-          }
-        }
-      }
+      run_epoch<MASKED, CHECKED, HIST, VOTE>(M, T, Y, P, r, h, active, final_st, epoch);
       if (!__any_sync(FULL, active)) break;
       const uint32_t want = __ballot_sync(FULL, !active && !exhausted);
       if ((uint32_t)__popc(want) >= refill_min) break;
@@ -339,19 +297,118 @@ __global__ void __launch_bounds__(256) k_persist(DevState S, Params P, Queue Q, 
     // ---- write back lanes whose VM stopped
     if (vm >= 0 && !active) {
       store_regs(S, (uint32_t)vm, r, final_st);
-      if (STAGED) {
-        fence_proxy_async_smem();
-        bulk_s2g(S.mem + moff, slot_s, ((r.n + 1u) & ~1u) * 8u);
-        if (ybytes) bulk_s2g(S.y + (uint64_t)vm * P.sp, slot_s + (ncap + P.ellp) * 8u, ybytes);
-        bulk_commit();
-      }
+      fence_proxy_async_smem();
+      bulk_s2g(S.mem + moff, slot_s, ((r.n + 1u) & ~1u) * 8u);
+      if (ybytes) bulk_s2g(S.y + (uint64_t)vm * P.sp, slot_s + (ncap + P.ellp) * 8u, ybytes);
+      bulk_commit();
       vm = -1;
     }
-    if (STAGED) bulk_wait_read_all();   // slot reusable once the stores have read it
+    bulk_wait_read_all();   // slot reusable once the stores have read it
   }
-  if (STAGED) {
-    bulk_wait_all();
-    if (dead) mbar_wait_bounded(bar, phase ^ 1u, WAIT_LIMIT);   // let stray copies land
+  bulk_wait_all();
+  if (dead) mbar_wait_bounded(bar, phase ^ 1u, WAIT_LIMIT);   // let stray copies land
+  flush_hist<HIST>(P, h);
+}
+
+// ------------------------------------------------------------------ persistent, M in HBM
+// Each lane runs one VM at a time with M, tape and y in HBM (cached in L1).
+// The next VM of every lane is prefetched in three stages that overlap the
+// running VM -- queue position, VM id (ids[pos]), registers -- so a lane
+// whose VM stops swaps the next one in without waiting on memory. Queue
+// positions are claimed in warp chunks of 32, the next chunk's atomic issued
+// while the current one is still being used.
+enum : uint32_t { PF_EMPTY = 0, PF_ID = 1, PF_REGS = 2, PF_NONE = 3 };
+
+template <bool MASKED, bool CHECKED, bool HIST, bool VOTE>
+__global__ void __launch_bounds__(256) k_persist_gl(DevState S, Params P, Queue Q, uint32_t epoch) {
+  const uint32_t lane = threadIdx.x & 31u;
+  Hist h;
+  h.zero();
+  // warp chunk of queue positions
+  uint32_t tick = 0;
+  if (lane == 0) tick = atomicAdd(Q.head, 32u);
+  uint32_t cbase = __shfl_sync(FULL, tick, 0);
+  uint32_t cused = 0;
+  bool inflight = false;          // lane 0 holds the next chunk's ticket in `tick`
+
+  // running VM
+  Regs r{};
+  r.n = 1;
+  int32_t vm = -1;
+  bool active = false;
+  uint32_t final_st = ST_RUNNING;
+  uint64_t* M = S.mem;
+  const uint64_t* T = S.tape;
+  uint64_t* Y = S.y;
+  // prefetched VM
+  uint32_t pf = PF_EMPTY, pf_pos = 0, pf_vm = 0;
+  Regs nr{};
+  uint64_t nmoff = 0;
+  uint8_t nstatus = 0;
+
+  for (;;) {
+    // ---- boundary: retire stopped VMs
+    if (vm >= 0 && !active) {
+      store_regs(S, (uint32_t)vm, r, final_st);
+      vm = -1;
+    }
+    // swap in the prefetched VM (its loads were issued a boundary ago)
+    if (vm < 0 && pf == PF_REGS) {
+      if (nstatus == ST_RUNNING) {
+        r = nr;
+        arm_regs(P, r);
+        vm = (int32_t)pf_vm;
+        M = S.mem + nmoff;
+        T = S.tape + (uint64_t)pf_vm * P.ellp;
+        Y = S.y + (uint64_t)pf_vm * P.sp;
+        active = true;
+      }
+      pf = PF_EMPTY;
+    }
+    // advance the prefetch pipeline: id -> registers
+    if (pf == PF_ID) {         // pf_vm = ids[pf_pos] was issued a boundary ago
+      nstatus = S.status[pf_vm];
+      load_regs(S, P, pf_vm, nr);
+      nmoff = S.mem_off[pf_vm];
+      pf = PF_REGS;
+    }
+    // new positions for lanes whose prefetch slot is empty
+    const uint32_t needm = __ballot_sync(FULL, pf == PF_EMPTY);
+    if (needm) {
+      if (cused >= 32u) {
+        if (!inflight) {
+          if (lane == 0) tick = atomicAdd(Q.head, 32u);
+          inflight = true;
+        }
+        cbase = __shfl_sync(FULL, tick, 0);
+        cused = 0;
+        inflight = false;
+      }
+      const uint32_t rank = (uint32_t)__popc(needm & ((1u << lane) - 1u));
+      const uint32_t avail = 32u - cused;
+      if (pf == PF_EMPTY && rank < avail) {
+        const uint32_t pos = cbase + cused + rank;
+        if (pos < Q.count) {
+          pf_pos = pos;
+          pf = PF_ID;
+        } else {
+          pf = PF_NONE;          // queue exhausted for this lane
+        }
+      }
+      const uint32_t took = min((uint32_t)__popc(needm), avail);
+      cused += took;
+      // claim the next chunk early so its atomic is in flight while this one drains
+      if (!inflight && cused >= 16u && cbase + 32u < Q.count) {
+        if (lane == 0) tick = atomicAdd(Q.head, 32u);
+        inflight = true;
+      }
+    }
+    if (pf == PF_ID) pf_vm = Q.ids[pf_pos];     // issue the id load; consumed next boundary
+    // done when no lane runs a VM or has one coming
+    if (__all_sync(FULL, vm < 0 && pf == PF_NONE)) break;
+
+    // ---- run
+    run_epoch<MASKED, CHECKED, HIST, VOTE>(M, T, Y, P, r, h, active, final_st, epoch);
   }
   flush_hist<HIST>(P, h);
 }
@@ -394,7 +451,8 @@ int num_sms() {
 }
 
 using PlainFn = void (*)(DevState, Params, const uint32_t*, uint32_t);
-using PersistFn = void (*)(DevState, Params, Queue, uint32_t, uint32_t, uint32_t, uint32_t);
+using StagedFn = void (*)(DevState, Params, Queue, uint32_t, uint32_t, uint32_t, uint32_t);
+using GlobalFn = void (*)(DevState, Params, Queue, uint32_t);
 
 template <bool M_, bool C_, bool H_>
 PlainFn plain_fn(bool vote) {
@@ -408,17 +466,29 @@ PlainFn pick_plain(const StepVariant& v) {
 }
 
 template <bool M_, bool C_, bool H_>
-PersistFn persist_fn(bool vote, bool staged) {
-  if (vote) return staged ? k_persist<M_, C_, H_, true, true> : k_persist<M_, C_, H_, true, false>;
-  return staged ? k_persist<M_, C_, H_, false, true> : k_persist<M_, C_, H_, false, false>;
+StagedFn staged_fn(bool vote) {
+  return vote ? k_persist<M_, C_, H_, true> : k_persist<M_, C_, H_, false>;
 }
 
-PersistFn pick_persist(const StepVariant& v, bool staged) {
-  if (v.checked)
-    return v.hist ? persist_fn<false, true, true>(v.vote, staged) : persist_fn<false, true, false>(v.vote, staged);
-  if (v.masked)
-    return v.hist ? persist_fn<true, false, true>(v.vote, staged) : persist_fn<true, false, false>(v.vote, staged);
-  return v.hist ? persist_fn<false, false, true>(v.vote, staged) : persist_fn<false, false, false>(v.vote, staged);
+StagedFn pick_staged(const StepVariant& v) {
+  if (v.checked) return v.hist ? staged_fn<false, true, true>(v.vote) : staged_fn<false, true, false>(v.vote);
+  if (v.masked) return v.hist ? staged_fn<true, false, true>(v.vote) : staged_fn<true, false, false>(v.vote);
+  return v.hist ? staged_fn<false, false, true>(v.vote) : staged_fn<false, false, false>(v.vote);
+}
+
+template <bool M_, bool C_, bool H_>
+GlobalFn global_fn(bool vote) {
+  return vote ? k_persist_gl<M_, C_, H_, true> : k_persist_gl<M_, C_, H_, false>;
+}
+
+GlobalFn pick_global(const StepVariant& v) {
+  if (v.checked) return v.hist ? global_fn<false, true, true>(v.vote) : global_fn<false, true, false>(v.vote);
+  if (v.masked) return v.hist ? global_fn<true, false, true>(v.vote) : global_fn<true, false, false>(v.vote);
+  return v.hist ? global_fn<false, false, true>(v.vote) : global_fn<false, false, false>(v.vote);
+}
+
+const void* persist_symbol(const StepVariant& v, bool staged) {
+  return staged ? (const void*)pick_staged(v) : (const void*)pick_global(v);
 }
 
 }  // namespace
@@ -439,38 +509,48 @@ cudaError_t launch_plain(const StepVariant& var, const DevState& S, const Params
                          uint32_t count, cudaStream_t stream) {
   if (!count) return cudaSuccess;
   const uint32_t blocks = (count + 255u) / 256u;
-  pick_plain(var)<<<blocks, 256, 0, stream>>>(S, P, ids, count);
+  PlainFn fn = pick_plain(var);
+  cudaFuncSetAttribute(fn, cudaFuncAttributePreferredSharedMemoryCarveout, (int)cudaSharedmemCarveoutMaxL1);
+  cudaGetLastError();
+  fn<<<blocks, 256, 0, stream>>>(S, P, ids, count);
   return cudaGetLastError();
 }
 
 int persist_configure(const StepVariant& var, PersistShape& sh) {
-  PersistFn fn = pick_persist(var, sh.staged);
+  const void* fn = persist_symbol(var, sh.staged);
   const size_t per_warp = sh.staged ? (size_t)(32u + 32u * sh.slot_words) * 8u : 0u;
   sh.smem = per_warp * sh.warps;
-  if (sh.smem > 48u * 1024u) {
-    if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sh.smem) != cudaSuccess) {
-      cudaGetLastError();
-      return 0;
-    }
+  if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sh.smem) != cudaSuccess) {
+    cudaGetLastError();
+    return 0;
   }
+  // staged: all of the unified L1/shared array as shared memory; otherwise
+  // keep it as L1 for the M slabs in HBM
+  cudaFuncSetAttribute(fn, cudaFuncAttributePreferredSharedMemoryCarveout,
+                       sh.staged ? (int)cudaSharedmemCarveoutMaxShared : (int)cudaSharedmemCarveoutMaxL1);
+  cudaGetLastError();
   int per_sm = 0;
   if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, (int)(32u * sh.warps), sh.smem) != cudaSuccess) {
     cudaGetLastError();
     return 0;
   }
   sh.grid = (uint32_t)(per_sm * num_sms());
+  sh.ctas_per_sm = (uint32_t)per_sm;
   return per_sm;
 }
 
 cudaError_t launch_persist(const StepVariant& var, const DevState& S, const Params& P, const Queue& Q,
                            const PersistShape& sh, cudaStream_t stream) {
   if (!Q.count || !sh.grid) return cudaSuccess;
-  PersistFn fn = pick_persist(var, sh.staged);
   uint32_t grid = sh.grid;
-  const uint32_t lanes_needed = (Q.count + 31u) / 32u;   // warps worth of VMs
-  const uint32_t max_useful = (lanes_needed + sh.warps - 1u) / sh.warps;
+  const uint32_t warps_needed = (Q.count + 31u) / 32u;
+  const uint32_t max_useful = (warps_needed + sh.warps - 1u) / sh.warps;
   if (grid > max_useful) grid = max_useful;
-  fn<<<grid, 32u * sh.warps, sh.smem, stream>>>(S, P, Q, sh.ncap, sh.slot_words, sh.epoch, sh.refill_min);
+  if (sh.staged)
+    pick_staged(var)<<<grid, 32u * sh.warps, sh.smem, stream>>>(S, P, Q, sh.ncap, sh.slot_words, sh.epoch,
+                                                                 sh.refill_min);
+  else
+    pick_global(var)<<<grid, 32u * sh.warps, 0, stream>>>(S, P, Q, sh.epoch);
   return cudaGetLastError();
 }
 

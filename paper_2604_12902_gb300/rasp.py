@@ -31,6 +31,7 @@ class rasp_config(ctypes.Structure):
     _fields_ = [("word_bits", ctypes.c_uint32), ("semantics", ctypes.c_uint32),
                 ("in_cap", ctypes.c_uint32), ("out_cap", ctypes.c_uint32),
                 ("flags", ctypes.c_uint32), ("epoch", ctypes.c_uint32),
+                ("warps_per_cta", ctypes.c_uint32), ("refill_min", ctypes.c_uint32),
                 ("stream", ctypes.c_void_p), ("arena", ctypes.c_void_p),
                 ("arena_bytes", ctypes.c_uint64)]
 
@@ -58,7 +59,7 @@ class RaspError(RuntimeError):
 _lib = None
 EXPORTS = ["rasp_batch_bytes", "rasp_batch_create", "rasp_load_programs", "rasp_load_inputs",
            "rasp_reset", "rasp_run", "rasp_sync", "rasp_read_state", "rasp_load_state",
-           "rasp_read_stats", "rasp_batch_destroy", "rasp_last_error", "rasp_version"]
+           "rasp_read_stats", "rasp_describe", "rasp_batch_destroy", "rasp_last_error", "rasp_version"]
 
 
 def lib():
@@ -80,11 +81,12 @@ def lib():
         L.rasp_read_state.argtypes = [P, U64, U64, ctypes.POINTER(rasp_state_view)]
         L.rasp_load_state.argtypes = [P, U64, U64, ctypes.POINTER(rasp_state_view)]
         L.rasp_read_stats.argtypes = [P, ctypes.POINTER(rasp_stats)]
+        L.rasp_describe.argtypes = [P, ctypes.c_char_p, U64]
         L.rasp_batch_destroy.argtypes = [P]
         L.rasp_batch_destroy.restype = None
         L.rasp_last_error.restype = ctypes.c_char_p
         L.rasp_version.restype = ctypes.c_char_p
-        for name in EXPORTS[:10]:
+        for name in EXPORTS[:11]:
             getattr(L, name).restype = I
         _lib = L
     return _lib
@@ -159,6 +161,13 @@ def rasp_read_stats(h) -> rasp_stats:
     return st
 
 
+def rasp_describe(h) -> dict:
+    import json
+    buf = ctypes.create_string_buffer(1 << 14)
+    _check(lib().rasp_describe(h, buf, len(buf)))
+    return json.loads(buf.value.decode())
+
+
 def rasp_batch_destroy(h):
     lib().rasp_batch_destroy(h)
 
@@ -183,13 +192,13 @@ class Batch:
 
     def __init__(self, mem_words, in_cap: int, out_cap: int, word_bits: int = 64,
                  semantics: int = WRAP, flags: int = 0, epoch: int = 0, stream=None,
-                 torch_arena: bool = True):
+                 torch_arena: bool = True, warps_per_cta: int = 0, refill_min: int = 0):
         import torch
         self.mem_words = np.ascontiguousarray(mem_words, dtype=np.uint32)
         self.V = int(self.mem_words.shape[0])
         self.ell, self.s, self.w = int(in_cap), int(out_cap), int(word_bits)
-        self.cfg = rasp_config(word_bits, semantics, in_cap, out_cap, flags, epoch,
-                               stream if stream is not None else _torch_stream(), None, 0)
+        self.cfg = rasp_config(word_bits, semantics, in_cap, out_cap, flags, epoch, warps_per_cta,
+                               refill_min, stream if stream is not None else _torch_stream(), None, 0)
         self._arena = None
         if torch_arena:
             nbytes = rasp_batch_bytes(self.cfg, self.mem_words)
@@ -254,6 +263,9 @@ class Batch:
                     fault_overflow=st.fault_overflow, fault_addr=st.fault_addr,
                     op_steps=[st.op_steps[k] for k in range(8)], pri_full=st.pri_full,
                     bnz_taken=st.bnz_taken, launches=st.launches)
+
+    def describe(self) -> dict:
+        return rasp_describe(self.h)
 
     def close(self):
         if getattr(self, "h", None):

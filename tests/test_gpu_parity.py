@@ -234,7 +234,7 @@ def test_instruction_counter_wraps_at_word_boundary(rasp):
 
 
 def test_shared_programs_match_expanded(rasp):
-    base = W.template_programs(num_vms=64, seed=5, instructions=48, mem_words=224, tape_len=8)
+    base = W.template_programs(num_vms=64, seed=5, instructions=48, mem_words=224, tape_len=8, loops_hi=2)
     V = 64 * 50
     prog_of_vm = np.repeat(np.arange(64, dtype=np.uint32), 50)
     ids = np.arange(V, dtype=np.uint64)

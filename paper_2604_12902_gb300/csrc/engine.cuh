@@ -186,9 +186,12 @@ __device__ __forceinline__ uint32_t decode(uint64_t* __restrict__ M, const Param
   const uint64_t o = oj.x, j = oj.y;
   d.j = j;
   d.jin = j < (uint64_t)n;
-  d.jm = d.jin ? (uint32_t)j : mod_n_slow(j, n);
   d.op = ((o - 1ull) < 7ull) ? (uint32_t)o : 0u;
   d.taken = (d.op == 5u) & (r.a != 0ull);
+  // j mod n only where j is an address or a jump target (LOD's j is an
+  // immediate, an untaken BNZ ignores it)
+  const bool addr = ((d.op >= 2u) & (d.op != 5u)) | d.taken;
+  d.jm = (d.jin | !addr) ? (uint32_t)j : mod_n_slow(j, n);
   // guards of the "otherwise" case (c -> c): invalid opcode, RD at the end
   // of the tape, BNZ to itself (j == i; while i < n that is j < n and
   // j == i mod n)
@@ -234,11 +237,12 @@ __device__ __forceinline__ void count_step(Hist& h, uint32_t op, bool taken) {
   }
 }
 
-// One transition in guarded-sum form. Returns CONT after applying it, else
-// the final status (see decode).
+// One transition, general form: every case of the Sec. 2.1 equation,
+// every guard and every wrap. Returns CONT after applying it, else the final
+// status (see decode).
 template <bool MASKED, bool CHECKED, bool HIST>
-__device__ __forceinline__ uint32_t one_step(uint64_t* __restrict__ M, const uint64_t* __restrict__ T,
-                                             uint64_t* __restrict__ Y, const Params& P, Regs& r, Hist& h) {
+__device__ __forceinline__ uint32_t step_general(uint64_t* __restrict__ M, const uint64_t* __restrict__ T,
+                                                 uint64_t* __restrict__ Y, const Params& P, Regs& r, Hist& h) {
   Decoded d;
   const uint32_t s = decode<MASKED, CHECKED>(M, P, r, d);
   if (s != CONT) return s;
@@ -275,6 +279,62 @@ __device__ __forceinline__ uint32_t one_step(uint64_t* __restrict__ M, const uin
   advance<MASKED>(P, r, d);
   count_step<HIST>(h, op, d.taken);
   return CONT;
+}
+
+// One transition in guarded-sum form. The common case -- i < n with an
+// aligned instruction pair, a valid opcode whose operand j lies in [0, n),
+// no fixed point, no wrap, countdown not exhausted -- is evaluated without
+// branches: every candidate update is formed and the opcode guards select
+// (Phi_w(c) = sum_psi eta_psi(c) Phi_psi(c)), so lanes holding different
+// opcodes stay on one instruction stream. Anything else falls through to
+// step_general.
+template <bool MASKED, bool CHECKED, bool HIST>
+__device__ __forceinline__ uint32_t one_step(uint64_t* __restrict__ M, const uint64_t* __restrict__ T,
+                                             uint64_t* __restrict__ Y, const Params& P, Regs& r, Hist& h) {
+  const uint32_t ip = r.ip, n = r.n;
+  if ((((ip | n) & 1u) == 0u) & (r.ibase == 0ull)) {
+    const ulonglong2 oj = *reinterpret_cast<const ulonglong2*>(M + ip);
+    const uint64_t o = oj.x, j = oj.y, a = r.a;
+    const uint32_t op = (uint32_t)o, jm = (uint32_t)j;
+    const bool valid = (o - 1ull) < 7ull;
+    const bool jin = j < (uint64_t)n;
+    const bool taken = (op == 5u) & (a != 0ull);
+    const bool rd = op == 6u;
+    const bool pri = op == 7u;
+    uint64_t v = 0;
+    if (((op == 2u) | (op == 3u) | pri) & jin) v = M[jm];
+    const uint64_t sum = a + v;
+    const uint64_t prod = a * v;
+    // rare: invalid opcode, operand outside memory, countdown exhausted, RD at
+    // the end of the tape, BNZ to itself, i (+) 2 at the end of memory or 2^w
+    const bool addr = ((op >= 2u) & (op != 5u)) | taken;   // j used as an address or jump target
+    bool rare = !valid | (addr & !jin) | (r.left == 0u) | (rd & (r.u0 >= P.ell)) |
+                (taken ? (jm == ip) : (ip + 2u >= r.ilim));
+    if constexpr (CHECKED) {
+      rare |= (op == 2u) & ((int64_t)((a ^ sum) & (v ^ sum)) < 0);
+      rare |= (op == 3u) & (__mul64hi((long long)a, (long long)v) != ((int64_t)prod >> 63));
+    }
+    if (!rare) {
+      uint64_t na = (op == 1u) ? j : a;
+      na = (op == 2u) ? sum : na;
+      na = (op == 3u) ? prod : na;
+      if (MASKED) na &= P.wmask;
+      uint64_t w = a;                            // STO writes a, RD writes u-bullet
+      if (rd) w = T[r.u0];
+      if ((op == 4u) | rd) M[jm] = w;
+      const bool put = pri & (r.y0 < P.s);       // y :: M_{j mod n}
+      if (put) Y[r.y0] = v;
+      r.u0 += rd ? 1u : 0u;
+      r.y0 += put ? 1u : 0u;
+      r.a = na;
+      r.ip = taken ? jm : ip + 2u;
+      r.left -= 1u;
+      if constexpr (HIST) h.c[8] += (pri & !put) ? 1u : 0u;
+      count_step<HIST>(h, op, taken);
+      return CONT;
+    }
+  }
+  return step_general<MASKED, CHECKED, HIST>(M, T, Y, P, r, h);
 }
 
 template <bool HIST>

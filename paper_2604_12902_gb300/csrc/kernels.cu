@@ -198,14 +198,13 @@ __device__ __forceinline__ void run_epoch(uint64_t* M, const uint64_t* T, uint64
         final_st = s;
       }
     }
-  } else {
+  } else if (active) {
     for (uint32_t t = 0; t < epoch; ++t) {
-      if (active) {
-        const uint32_t s = one_step<MASKED, CHECKED, HIST>(M, T, Y, P, r, h);
-        if (s != CONT) {
-          active = false;
-          final_st = s;
-        }
+      const uint32_t s = one_step<MASKED, CHECKED, HIST>(M, T, Y, P, r, h);
+      if (s != CONT) {
+        active = false;
+        final_st = s;
+        break;
       }
     }
   }

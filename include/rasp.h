@@ -85,6 +85,10 @@ typedef struct rasp_config {
     uint32_t warps_per_cta; /* persistent kernels: warps per CTA; 0 = default  */
     uint32_t refill_min; /* persistent kernels: idle lanes that trigger a
                             refill; 0 = default                               */
+    uint32_t ctas_per_sm;/* persistent kernels: resident CTAs per SM (fewer
+                            resident VMs keep their memory in L1/L2);
+                            0 = as many as fit                                */
+    uint32_t reserved;   /* must be 0                                         */
     void*    stream;     /* cudaStream_t for all work of the batch; NULL = the
                             legacy default stream                              */
     void*    arena;      /* optional caller-owned device memory for the batch;

@@ -94,6 +94,7 @@ namespace {
 int validate_config(const rasp_config* cfg, uint64_t num_vms, const uint32_t* mem_words) {
   if (!cfg) return fail(RASP_EINVAL, "config is NULL");
   if (cfg->word_bits < 2 || cfg->word_bits > 64) return fail(RASP_EINVAL, "word_bits must be in 2..64");
+  if (cfg->reserved) return fail(RASP_EINVAL, "rasp_config.reserved must be 0");
   if (cfg->semantics != RASP_WRAP && cfg->semantics != RASP_CHECKED)
     return fail(RASP_EINVAL, "unknown semantics %u", cfg->semantics);
   if (cfg->semantics == RASP_CHECKED && cfg->word_bits != 64)
@@ -172,7 +173,9 @@ void plan_buckets(rasp_batch* b) {
       return w;
     }();
     const size_t staged_bytes = (size_t)(32u + 32u * slot) * 8u;
-    if (sched == RASP_SCHED_AUTO) sched = (staged_bytes <= 80u * 1024u) ? RASP_SCHED_PERSIST : RASP_SCHED_PERSIST_GL;
+    // default before autotuning: persistent workers over HBM-resident slabs
+    // (measured fastest on the 256-word template workload)
+    if (sched == RASP_SCHED_AUTO) sched = RASP_SCHED_PERSIST_GL;
     if (sched == RASP_SCHED_PERSIST && staged_bytes > 220u * 1024u) sched = RASP_SCHED_PERSIST_GL;
     k.sched = sched;
     PersistShape& sh = k.shape;
@@ -187,13 +190,16 @@ void plan_buckets(rasp_batch* b) {
       sh.staged = false;
       sh.warps = 4;
       sh.refill_min = 1;
-      sh.epoch = b->cfg.epoch ? b->cfg.epoch : 16u;
+      sh.epoch = b->cfg.epoch ? b->cfg.epoch : 64u;
     }
     if (b->cfg.warps_per_cta) sh.warps = std::min<uint32_t>(b->cfg.warps_per_cta, 8u);
     if (b->cfg.refill_min) sh.refill_min = std::min<uint32_t>(b->cfg.refill_min, 32u);
     if (sched != RASP_SCHED_PLAIN) {
       if (persist_configure(var, sh) == 0) {
         k.sched = RASP_SCHED_PLAIN;        // cannot be resident: fall back to the plain form
+      } else if (b->cfg.ctas_per_sm && b->cfg.ctas_per_sm < sh.ctas_per_sm) {
+        sh.grid = sh.grid / sh.ctas_per_sm * b->cfg.ctas_per_sm;
+        sh.ctas_per_sm = b->cfg.ctas_per_sm;
       }
     }
   }

@@ -59,18 +59,20 @@ struct Queue {
 // as i = ibase + ip with ip = i mod n; ibase is 0 while i < n, which is
 // where programs spend their time, so the common step touches only the
 // 32-bit ip. Steps are counted down in 32 bits: the machine has taken
-// steps + (left0 - left) steps; the 64-bit stop/cap are consulted only when
-// the countdown reaches zero.
+// steps + (left0 - left) steps; the 64-bit budget and cap are consulted only
+// when the countdown reaches zero.
 struct Regs {
   uint64_t a;
   uint64_t ibase;             // i - (i mod n)
   uint64_t steps;             // steps at the start of the current countdown
-  uint64_t stop, cap;         // min(budget, cap) and cap
+  uint64_t cap;               // step cap; the run stops at min(budget, cap)
   uint32_t left0, left;       // countdown start and remaining
   uint32_t ip;                // i mod n
   uint32_t n;
   uint32_t ilim;              // min(n, 2^w): while ibase = 0, ip + 2 < ilim means i (+) 2 = ip + 2 < n
   uint32_t u0, y0;
+  ulonglong2 cur;             // <M[ip], M[ip+1]> when `have`: the next instruction, already loaded
+  bool have;
 };
 
 __device__ __forceinline__ uint64_t i_of(const Regs& r) { return r.ibase + (uint64_t)r.ip; }
@@ -94,13 +96,18 @@ __device__ __forceinline__ uint32_t mod_n(uint64_t x, uint32_t n) {
   return (x < (uint64_t)n) ? (uint32_t)x : mod_n_slow(x, n);
 }
 
-// Start a fresh 32-bit countdown toward stop; false if steps >= stop already.
-__device__ __forceinline__ bool arm_countdown(Regs& r) {
-  if (r.steps >= r.stop) {
+__device__ __forceinline__ uint64_t stop_of(const Params& P, const Regs& r) {
+  return P.budget < r.cap ? P.budget : r.cap;
+}
+
+// Start a fresh 32-bit countdown toward the stop; false if already there.
+__device__ __forceinline__ bool arm_countdown(const Params& P, Regs& r) {
+  const uint64_t stop = stop_of(P, r);
+  if (r.steps >= stop) {
     r.left0 = r.left = 0;
     return false;
   }
-  const uint64_t rem = r.stop - r.steps;
+  const uint64_t rem = stop - r.steps;
   r.left0 = r.left = rem > 0xFFFFFFFFull ? 0xFFFFFFFFu : (uint32_t)rem;
   return true;
 }
@@ -127,8 +134,8 @@ static __device__ __noinline__ Countdown countdown_next(uint64_t steps, uint32_t
   return c;
 }
 
-__device__ __forceinline__ uint32_t on_countdown_zero(Regs& r) {
-  const Countdown c = countdown_next(r.steps, r.left0, r.stop, r.cap);
+__device__ __forceinline__ uint32_t on_countdown_zero(const Params& P, Regs& r) {
+  const Countdown c = countdown_next(r.steps, r.left0, stop_of(P, r), r.cap);
   r.steps = c.steps;
   r.left0 = r.left = c.left;
   return c.status;
@@ -169,7 +176,7 @@ __device__ __forceinline__ uint32_t decode(uint64_t* __restrict__ M, const Param
     // without circular addressing the fetch needs i, i+1 in [0, n)
     if (wide | (ip + 1u >= n)) {
       if (r.left == 0u) {
-        const uint32_t s = on_countdown_zero(r);
+        const uint32_t s = on_countdown_zero(P, r);
         if (s != CONT) return s;
       }
       return ST_FAULT_ADDR;
@@ -199,7 +206,7 @@ __device__ __forceinline__ uint32_t decode(uint64_t* __restrict__ M, const Param
   if (wide && d.taken && j == i_of(r)) fixed = true;
   if (fixed | (r.left == 0u)) {
     if (fixed) return ST_HALTED;
-    const uint32_t s = on_countdown_zero(r);
+    const uint32_t s = on_countdown_zero(P, r);
     if (s != CONT) return s;
   }
   if constexpr (CHECKED) {
@@ -288,12 +295,28 @@ __device__ __forceinline__ uint32_t step_general(uint64_t* __restrict__ M, const
 // (Phi_w(c) = sum_psi eta_psi(c) Phi_psi(c)), so lanes holding different
 // opcodes stay on one instruction stream. Anything else falls through to
 // step_general.
-template <bool MASKED, bool CHECKED, bool HIST>
+//
+// With PIPE the fast path is software-pipelined: the instruction pair
+// <o, j> of the current step was loaded by the previous step (r.cur), and at
+// the start of this step two independent 16-byte loads go out together --
+// the sequential next pair M[ip+2..ip+3] and the aligned pair holding
+// M[j mod n], which is both the operand of ADD/MUL/PRI and the first
+// instruction of a taken BNZ. A step then waits on one memory latency
+// instead of two in a row, at the price of more registers and loads. A
+// STO/RD that writes the prefetched pair invalidates it.
+template <bool MASKED, bool CHECKED, bool HIST, bool PIPE>
 __device__ __forceinline__ uint32_t one_step(uint64_t* __restrict__ M, const uint64_t* __restrict__ T,
                                              uint64_t* __restrict__ Y, const Params& P, Regs& r, Hist& h) {
   const uint32_t ip = r.ip, n = r.n;
-  if ((((ip | n) & 1u) == 0u) & (r.ibase == 0ull)) {
-    const ulonglong2 oj = *reinterpret_cast<const ulonglong2*>(M + ip);
+  const uint32_t ilim = MASKED ? r.ilim : n;
+  const bool aligned = (((ip | n) & 1u) == 0u) & (r.ibase == 0ull);
+  if (PIPE && aligned && !r.have) {
+    // even n and even i = ip < n: i != 2^w - 1 and M[ip], M[ip+1] is one 16-byte word
+    r.cur = *reinterpret_cast<const ulonglong2*>(M + ip);
+    r.have = true;
+  }
+  if (aligned) {
+    const ulonglong2 oj = PIPE ? r.cur : *reinterpret_cast<const ulonglong2*>(M + ip);
     const uint64_t o = oj.x, j = oj.y, a = r.a;
     const uint32_t op = (uint32_t)o, jm = (uint32_t)j;
     const bool valid = (o - 1ull) < 7ull;
@@ -301,15 +324,24 @@ __device__ __forceinline__ uint32_t one_step(uint64_t* __restrict__ M, const uin
     const bool taken = (op == 5u) & (a != 0ull);
     const bool rd = op == 6u;
     const bool pri = op == 7u;
+    const bool seq_ok = ip + 3u < n;
+    ulonglong2 seq = make_ulonglong2(0ull, 0ull);
+    ulonglong2 pr = make_ulonglong2(0ull, 0ull);
     uint64_t v = 0;
-    if (((op == 2u) | (op == 3u) | pri) & jin) v = M[jm];
+    if (PIPE) {
+      if (seq_ok) seq = *reinterpret_cast<const ulonglong2*>(M + ip + 2u);
+      if (((op == 2u) | (op == 3u) | pri | taken) & jin) pr = *reinterpret_cast<const ulonglong2*>(M + (jm & ~1u));
+      v = (jm & 1u) ? pr.y : pr.x;
+    } else {
+      if (((op == 2u) | (op == 3u) | pri) & jin) v = M[jm];
+    }
     const uint64_t sum = a + v;
     const uint64_t prod = a * v;
+    const bool addr = ((op >= 2u) & (op != 5u)) | taken;   // j used as an address or jump target
     // rare: invalid opcode, operand outside memory, countdown exhausted, RD at
     // the end of the tape, BNZ to itself, i (+) 2 at the end of memory or 2^w
-    const bool addr = ((op >= 2u) & (op != 5u)) | taken;   // j used as an address or jump target
     bool rare = !valid | (addr & !jin) | (r.left == 0u) | (rd & (r.u0 >= P.ell)) |
-                (taken ? (jm == ip) : (ip + 2u >= r.ilim));
+                (taken ? (jm == ip) : (ip + 2u >= ilim));
     if constexpr (CHECKED) {
       rare |= (op == 2u) & ((int64_t)((a ^ sum) & (v ^ sum)) < 0);
       rare |= (op == 3u) & (__mul64hi((long long)a, (long long)v) != ((int64_t)prod >> 63));
@@ -319,21 +351,30 @@ __device__ __forceinline__ uint32_t one_step(uint64_t* __restrict__ M, const uin
       na = (op == 2u) ? sum : na;
       na = (op == 3u) ? prod : na;
       if (MASKED) na &= P.wmask;
+      const bool wr = (op == 4u) | rd;
       uint64_t w = a;                            // STO writes a, RD writes u-bullet
       if (rd) w = T[r.u0];
-      if ((op == 4u) | rd) M[jm] = w;
+      if (wr) M[jm] = w;
       const bool put = pri & (r.y0 < P.s);       // y :: M_{j mod n}
       if (put) Y[r.y0] = v;
       r.u0 += rd ? 1u : 0u;
       r.y0 += put ? 1u : 0u;
       r.a = na;
-      r.ip = taken ? jm : ip + 2u;
+      const uint32_t nip = taken ? jm : ip + 2u;
+      r.ip = nip;
+      if (PIPE) {
+        // the next pair: the jump target's (if aligned) or the sequential one,
+        // unless this step's store overwrote it
+        r.cur = taken ? pr : seq;
+        r.have = taken ? ((jm & 1u) == 0u) : (seq_ok & !(wr & ((jm | 1u) == (nip | 1u))));
+      }
       r.left -= 1u;
       if constexpr (HIST) h.c[8] += (pri & !put) ? 1u : 0u;
       count_step<HIST>(h, op, taken);
       return CONT;
     }
   }
+  if (PIPE) r.have = false;
   return step_general<MASKED, CHECKED, HIST>(M, T, Y, P, r, h);
 }
 
@@ -366,11 +407,11 @@ __device__ __forceinline__ void load_regs(const DevState& S, const Params& P, ui
 // Derived registers once the loads of load_regs have landed.
 __device__ __forceinline__ void arm_regs(const Params& P, Regs& r) {
   const uint64_t i = r.ibase;
-  r.stop = P.budget < r.cap ? P.budget : r.cap;
   r.ip = mod_n(i, r.n);
   r.ibase = i - r.ip;
   r.ilim = (P.wmask >= (uint64_t)r.n - 1u) ? r.n : (uint32_t)(P.wmask + 1ull);
-  arm_countdown(r);
+  r.have = false;
+  arm_countdown(P, r);
 }
 
 __device__ __forceinline__ void store_regs(const DevState& S, uint32_t v, const Regs& r, uint32_t st) {

@@ -179,7 +179,7 @@ __global__ void __launch_bounds__(256) k_plain(DevState S, Params P, const uint3
     if (had) store_regs(S, v, r, st);
   } else if (active) {
     do {
-      st = one_step<MASKED, CHECKED, HIST>(M, T, Y, P, r, h);
+      st = one_step<MASKED, CHECKED, HIST, false>(M, T, Y, P, r, h);
     } while (st == CONT);
     store_regs(S, v, r, st);
   }
@@ -187,7 +187,7 @@ __global__ void __launch_bounds__(256) k_plain(DevState S, Params P, const uint3
 }
 
 // Run `epoch` steps of every active lane (warp-uniform loop).
-template <bool MASKED, bool CHECKED, bool HIST, bool VOTE>
+template <bool MASKED, bool CHECKED, bool HIST, bool VOTE, bool PIPE>
 __device__ __forceinline__ void run_epoch(uint64_t* M, const uint64_t* T, uint64_t* Y, const Params& P, Regs& r,
                                           Hist& h, bool& active, uint32_t& final_st, uint32_t epoch) {
   if (VOTE) {
@@ -200,7 +200,7 @@ __device__ __forceinline__ void run_epoch(uint64_t* M, const uint64_t* T, uint64
     }
   } else if (active) {
     for (uint32_t t = 0; t < epoch; ++t) {
-      const uint32_t s = one_step<MASKED, CHECKED, HIST>(M, T, Y, P, r, h);
+      const uint32_t s = one_step<MASKED, CHECKED, HIST, PIPE>(M, T, Y, P, r, h);
       if (s != CONT) {
         active = false;
         final_st = s;
@@ -287,7 +287,7 @@ __global__ void __launch_bounds__(256) k_persist(DevState S, Params P, Queue Q, 
 
     // ---- run until enough lanes can be refilled (checked every `epoch` steps)
     for (;;) {
-      run_epoch<MASKED, CHECKED, HIST, VOTE>(M, T, Y, P, r, h, active, final_st, epoch);
+      run_epoch<MASKED, CHECKED, HIST, VOTE, false>(M, T, Y, P, r, h, active, final_st, epoch);
       if (!__any_sync(FULL, active)) break;
       const uint32_t want = __ballot_sync(FULL, !active && !exhausted);
       if ((uint32_t)__popc(want) >= refill_min) break;
@@ -407,7 +407,7 @@ __global__ void __launch_bounds__(256) k_persist_gl(DevState S, Params P, Queue 
     if (__all_sync(FULL, vm < 0 && pf == PF_NONE)) break;
 
     // ---- run
-    run_epoch<MASKED, CHECKED, HIST, VOTE>(M, T, Y, P, r, h, active, final_st, epoch);
+    run_epoch<MASKED, CHECKED, HIST, VOTE, true>(M, T, Y, P, r, h, active, final_st, epoch);
   }
   flush_hist<HIST>(P, h);
 }

@@ -32,6 +32,7 @@ class rasp_config(ctypes.Structure):
                 ("in_cap", ctypes.c_uint32), ("out_cap", ctypes.c_uint32),
                 ("flags", ctypes.c_uint32), ("epoch", ctypes.c_uint32),
                 ("warps_per_cta", ctypes.c_uint32), ("refill_min", ctypes.c_uint32),
+                ("ctas_per_sm", ctypes.c_uint32), ("reserved", ctypes.c_uint32),
                 ("stream", ctypes.c_void_p), ("arena", ctypes.c_void_p),
                 ("arena_bytes", ctypes.c_uint64)]
 
@@ -192,13 +193,15 @@ class Batch:
 
     def __init__(self, mem_words, in_cap: int, out_cap: int, word_bits: int = 64,
                  semantics: int = WRAP, flags: int = 0, epoch: int = 0, stream=None,
-                 torch_arena: bool = True, warps_per_cta: int = 0, refill_min: int = 0):
+                 torch_arena: bool = True, warps_per_cta: int = 0, refill_min: int = 0,
+                 ctas_per_sm: int = 0):
         import torch
         self.mem_words = np.ascontiguousarray(mem_words, dtype=np.uint32)
         self.V = int(self.mem_words.shape[0])
         self.ell, self.s, self.w = int(in_cap), int(out_cap), int(word_bits)
         self.cfg = rasp_config(word_bits, semantics, in_cap, out_cap, flags, epoch, warps_per_cta,
-                               refill_min, stream if stream is not None else _torch_stream(), None, 0)
+                               refill_min, ctas_per_sm, 0,
+                               stream if stream is not None else _torch_stream(), None, 0)
         self._arena = None
         if torch_arena:
             nbytes = rasp_batch_bytes(self.cfg, self.mem_words)

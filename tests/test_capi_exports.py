@@ -28,7 +28,7 @@ def test_library_exports_every_declared_function():
 def test_batch_bytes_validates_without_gpu():
     from paper_2604_12902_gb300 import rasp
     import numpy as np
-    cfg = rasp.rasp_config(64, 0, 4, 8, 0, 0, 0, 0, None, None, 0)
+    cfg = rasp.rasp_config(64, 0, 4, 8, 0, 0, 0, 0, 0, 0, None, None, 0)
     nbytes = rasp.rasp_batch_bytes(cfg, np.full(1024, 64, np.uint32))
     assert nbytes > 1024 * 64 * 8 * 2
     cfg.word_bits = 1

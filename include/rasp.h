@@ -190,6 +190,64 @@ int rasp_read_stats(rasp_batch* b, rasp_stats* out);
  * too small. Does not touch the GPU. */
 int rasp_describe(const rasp_batch* b, char* buf, uint64_t size);
 
+/* ---- running a caller-owned state store without allocating ---------------
+ * The paper has no counterpart to this call: it exists for callers that
+ * cannot allocate when they run machines -- code recording a CUDA graph
+ * (stream capture forbids cudaMalloc), engines whose device memory belongs
+ * to another framework's allocator, real-time loops that must not allocate.
+ * rasp_run_static advances VMs [0, num_vms) of a state store that the caller
+ * owns, in place, exactly as rasp_run does (same statuses, same cumulative
+ * step budget), and calls no cudaMalloc, cudaFree or other allocator.
+ *
+ * Its only extra memory is a fixed scratch area inside the library (a queue
+ * of up to RASP_STATIC_MAX_VMS VM ids and a few counters, about 4 MiB) that
+ * every GPU loading the library keeps until the process exits. The first
+ * call on each device looks up that area's device address (a one-time
+ * set-up with that device current); make that first call before any stream
+ * capture. Every call on a device shares the area and resets its counters,
+ * so calls whose work overlaps on the GPU (e.g. on two streams at once)
+ * race: order them on one stream or serialise them.
+ *
+ * Layout of the caller's device buffers (all device pointers, the caller
+ * owns them): i, a, steps, cap, status, uhead, ylen, n, mem_off are arrays
+ * of num_vms entries as in rasp_state_view (cap = per-VM step cap). VM v's
+ * memory is mem[mem_off[v] .. mem_off[v] + n[v]); mem_off[v] must be even
+ * and mem 16-byte aligned. The tape of VM v (u_1..u_l, zero padded) is
+ * tape[v*lp .. v*lp + l) and its output y_1..y_s is y[v*sp .. v*sp + s),
+ * with lp, sp = in_cap, out_cap rounded up to even; tape and y 16-byte
+ * aligned. Words must already be reduced to w bits.
+ * Returns RASP_EINVAL for num_vms > RASP_STATIC_MAX_VMS, bad w/semantics,
+ * NULL or misaligned buffers, RASP_ECUDA if a CUDA call fails; the message
+ * goes to err_buf (if given). Asynchronous on `stream`. */
+#define RASP_STATIC_MAX_VMS (1u << 20)
+
+typedef struct rasp_static_run {
+    int64_t*        i;
+    int64_t*        a;
+    uint64_t*       steps;
+    const uint64_t* cap;
+    uint8_t*        status;
+    uint32_t*       uhead;
+    uint32_t*       ylen;
+    const uint32_t* n;
+    const uint64_t* mem_off;
+    int64_t*        mem;
+    const int64_t*  tape;
+    int64_t*        y;
+    uint64_t        num_vms;
+    uint32_t        word_bits;   /* w, 2..64 */
+    uint32_t        semantics;   /* RASP_WRAP or RASP_CHECKED */
+    uint32_t        in_cap;      /* l */
+    uint32_t        out_cap;     /* s */
+    uint64_t        max_steps;   /* cumulative budget, as for rasp_run */
+    void*           stream;      /* cudaStream_t */
+    char*           err_buf;     /* optional: receives an error message */
+    uint32_t        err_buf_size;
+    uint32_t        reserved;
+} rasp_static_run;
+
+int rasp_run_static(const rasp_static_run* run);
+
 /* Free the batch (synchronises its stream first). NULL is a no-op. */
 void rasp_batch_destroy(rasp_batch* b);
 

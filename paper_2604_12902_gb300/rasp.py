@@ -287,3 +287,29 @@ class Batch:
             self.close()
         except Exception:
             pass
+
+
+# ---- rasp_run_static: a caller-owned state store, no allocation ----------
+class rasp_static_run(ctypes.Structure):
+    _fields_ = [("i", ctypes.c_void_p), ("a", ctypes.c_void_p), ("steps", ctypes.c_void_p),
+                ("cap", ctypes.c_void_p), ("status", ctypes.c_void_p), ("uhead", ctypes.c_void_p),
+                ("ylen", ctypes.c_void_p), ("n", ctypes.c_void_p), ("mem_off", ctypes.c_void_p),
+                ("mem", ctypes.c_void_p), ("tape", ctypes.c_void_p), ("y", ctypes.c_void_p),
+                ("num_vms", ctypes.c_uint64), ("word_bits", ctypes.c_uint32),
+                ("semantics", ctypes.c_uint32), ("in_cap", ctypes.c_uint32), ("out_cap", ctypes.c_uint32),
+                ("max_steps", ctypes.c_uint64), ("stream", ctypes.c_void_p), ("err_buf", ctypes.c_char_p),
+                ("err_buf_size", ctypes.c_uint32), ("reserved", ctypes.c_uint32)]
+
+
+RASP_STATIC_MAX_VMS = 1 << 20
+
+
+def rasp_run_static(run: rasp_static_run) -> int:
+    """Call rasp_run_static; returns its status code (0 = OK). The error
+    message, if any, is written to run.err_buf."""
+    L = lib()
+    if not getattr(L.rasp_run_static, "_typed", False):
+        L.rasp_run_static.argtypes = [ctypes.POINTER(rasp_static_run)]
+        L.rasp_run_static.restype = ctypes.c_int
+        L.rasp_run_static._typed = True
+    return L.rasp_run_static(ctypes.byref(run))

@@ -111,11 +111,11 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
-def make_workload(name: str, rank: int):
+def make_workload(name: str, rank: int, vms: int = 1 << 20):
     from paper_2604_12902_gb300 import workloads as W
     if name == "templates":
-        return W.template_programs(num_vms=1 << 20, seed=2, first_vm=rank << 20), \
-            "1,048,576 template programs (64 instr, 1-3 loops, trips U[1,64]), n=256, l=16, s=8, cap 4096"
+        return W.template_programs(num_vms=vms, seed=2, first_vm=rank * vms), \
+            "%s template programs (64 instr, 1-3 loops, trips U[1,64]), n=256, l=16, s=8, cap 4096" % format(vms, ",")
     if name == "random":
         return W.random_programs(num_vms=1024, seed=1, first_vm=rank * 1024), \
             "1,024 random programs (32 instr, opcodes U{1..7}, operands U[0,63]), n=64, l=4, s=8, cap 256"
@@ -190,6 +190,7 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-plain", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    ap.add_argument("--vms", type=int, default=1 << 20, help="template programs per GPU (profiling cases)")
     args = ap.parse_args()
     ws, rank, local = dist_env()
     if args.impl == "reference":
@@ -205,7 +206,7 @@ def main():
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
     from paper_2604_12902_gb300 import rasp as R
 
-    wl, desc = make_workload(args.workload, rank)
+    wl, desc = make_workload(args.workload, rank, args.vms)
     stream = torch.cuda.current_stream()
     b = R.Batch(wl.mem_words, wl.ell, wl.s, flags=args.flags, epoch=args.epoch)
     b.load_workload(wl)

@@ -140,7 +140,7 @@ Layout make_layout(uint64_t V, uint64_t mem_words, uint32_t ellp, uint32_t sp) {
   L.off_tape = take(8 * V * (uint64_t)ellp);
   L.off_y = take(8 * V * (uint64_t)sp);
   L.off_ids = take(4 * V);
-  L.off_heads = take(4 * kNumBuckets);
+  L.off_heads = take(8 * kNumBuckets);
   L.off_err = take(16);
   L.off_hist = take(8 * 10);
   L.off_stats = take(8 * 6);
@@ -462,7 +462,7 @@ int rasp_run(rasp_batch* b, uint64_t max_steps) {
   P.sp = b->sp;
   P.err = b->d_err;
   P.hist = b->d_hist;
-  CK(cudaMemsetAsync(b->d_heads, 0, 4 * kNumBuckets, st));
+  CK(cudaMemsetAsync(b->d_heads, 0, 8 * kNumBuckets, st));
   b->launches = 0;
   for (size_t k = 0; k < b->buckets.size(); ++k) {
     const Bucket& bk = b->buckets[k];
@@ -471,7 +471,7 @@ int rasp_run(rasp_batch* b, uint64_t max_steps) {
     if (bk.sched == RASP_SCHED_PLAIN) {
       CK(launch_plain(var, b->S, P, ids, bk.count, st));
     } else {
-      Queue Q{ids, bk.count, b->d_heads + k};
+      Queue Q{ids, bk.count, b->d_heads + k, b->d_heads + kNumBuckets + k, 0};
       CK(launch_persist(var, b->S, P, Q, bk.shape, st));
     }
     b->launches++;

@@ -53,6 +53,8 @@ struct Queue {
   const uint32_t* ids;        // VM ids in schedule order
   uint32_t count;
   uint32_t* head;             // next unclaimed position (reset to 0 per launch)
+  uint32_t* tail_head;        // next unclaimed tail position (reset to 0 per launch)
+  uint32_t soft_end;          // positions >= soft_end are handed out one by one to idle lanes
 };
 
 // Registers of one machine while it runs. The instruction counter is kept

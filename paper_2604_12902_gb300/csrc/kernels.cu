@@ -311,24 +311,29 @@ __global__ void __launch_bounds__(256) k_persist(DevState S, Params P, Queue Q, 
 
 // ------------------------------------------------------------------ persistent, M in HBM
 // Each lane runs one VM at a time with M, tape and y in HBM (cached in L1).
-// The next VM of every lane is prefetched in three stages that overlap the
+// The next VM of every lane is prefetched in stages that overlap the
 // running VM -- queue position, VM id (ids[pos]), registers -- so a lane
 // whose VM stops swaps the next one in without waiting on memory. Queue
-// positions are claimed in warp chunks of 32, the next chunk's atomic issued
-// while the current one is still being used.
+// positions below Q.soft_end are claimed in warp chunks of 32, the next
+// chunk's atomic issued while the current one is still being used. The
+// last positions (as many as there are resident lanes) form the tail: they
+// are claimed one at a time, only by lanes that are idle, so that near the
+// end no VM waits in a busy lane's prefetch slot while other lanes idle.
 enum : uint32_t { PF_EMPTY = 0, PF_ID = 1, PF_REGS = 2, PF_NONE = 3 };
 
 template <bool MASKED, bool CHECKED, bool HIST, bool VOTE>
-__global__ void __launch_bounds__(256) k_persist_gl(DevState S, Params P, Queue Q, uint32_t epoch) {
+__global__ void __launch_bounds__(128, 7) k_persist_gl(DevState S, Params P, Queue Q, uint32_t epoch) {
   const uint32_t lane = threadIdx.x & 31u;
+  const uint32_t lt = (1u << lane) - 1u;
   Hist h;
   h.zero();
-  // warp chunk of queue positions
+  // warp chunk [cpos, cend) of main-phase queue positions
   uint32_t tick = 0;
   if (lane == 0) tick = atomicAdd(Q.head, 32u);
-  uint32_t cbase = __shfl_sync(FULL, tick, 0);
-  uint32_t cused = 0;
-  bool inflight = false;          // lane 0 holds the next chunk's ticket in `tick`
+  uint32_t cpos = __shfl_sync(FULL, tick, 0);
+  uint32_t cend = cpos < Q.soft_end ? min(cpos + 32u, Q.soft_end) : cpos;
+  bool tail = cpos >= Q.soft_end;  // warp-uniform: main positions used up
+  bool inflight = false;           // lane 0 holds the next chunk's ticket in `tick`
 
   // running VM
   Regs r{};
@@ -371,35 +376,53 @@ __global__ void __launch_bounds__(256) k_persist_gl(DevState S, Params P, Queue 
       nmoff = S.mem_off[pf_vm];
       pf = PF_REGS;
     }
-    // new positions for lanes whose prefetch slot is empty
-    const uint32_t needm = __ballot_sync(FULL, pf == PF_EMPTY);
-    if (needm) {
-      if (cused >= 32u) {
-        if (!inflight) {
-          if (lane == 0) tick = atomicAdd(Q.head, 32u);
-          inflight = true;
-        }
-        cbase = __shfl_sync(FULL, tick, 0);
-        cused = 0;
-        inflight = false;
-      }
-      const uint32_t rank = (uint32_t)__popc(needm & ((1u << lane) - 1u));
-      const uint32_t avail = 32u - cused;
-      if (pf == PF_EMPTY && rank < avail) {
-        const uint32_t pos = cbase + cused + rank;
-        if (pos < Q.count) {
-          pf_pos = pos;
+    // ---- new queue positions
+    if (!tail) {
+      uint32_t needm = __ballot_sync(FULL, pf == PF_EMPTY);
+      while (needm && !tail) {
+        const uint32_t avail = cend - cpos;
+        const uint32_t rank = (uint32_t)__popc(needm & lt);
+        if (((needm >> lane) & 1u) && rank < avail) {
+          pf_pos = cpos + rank;
           pf = PF_ID;
-        } else {
-          pf = PF_NONE;          // queue exhausted for this lane
+        }
+        const uint32_t took = min((uint32_t)__popc(needm), avail);
+        cpos += took;
+        needm = __ballot_sync(FULL, pf == PF_EMPTY);
+        if (cpos >= cend) {      // chunk used up: take the next one
+          if (!inflight && lane == 0) tick = atomicAdd(Q.head, 32u);
+          inflight = false;
+          cpos = __shfl_sync(FULL, tick, 0);
+          if (cpos >= Q.soft_end) {
+            tail = true;
+            cend = cpos;
+          } else {
+            cend = min(cpos + 32u, Q.soft_end);
+          }
         }
       }
-      const uint32_t took = min((uint32_t)__popc(needm), avail);
-      cused += took;
       // claim the next chunk early so its atomic is in flight while this one drains
-      if (!inflight && cused >= 16u && cbase + 32u < Q.count) {
+      if (!tail && !inflight && cend - cpos <= 16u && cend < Q.soft_end) {
         if (lane == 0) tick = atomicAdd(Q.head, 32u);
         inflight = true;
+      }
+    }
+    if (tail) {
+      const uint32_t needm = __ballot_sync(FULL, pf == PF_EMPTY && vm < 0);
+      if (needm) {
+        const int leader = __ffs(needm) - 1;
+        uint32_t base = 0;
+        if ((int)lane == leader) base = atomicAdd(Q.tail_head, (uint32_t)__popc(needm));
+        base = __shfl_sync(FULL, base, leader);
+        if ((needm >> lane) & 1u) {
+          const uint32_t pos = Q.soft_end + base + (uint32_t)__popc(needm & lt);
+          if (pos < Q.count) {
+            pf_pos = pos;
+            pf = PF_ID;
+          } else {
+            pf = PF_NONE;        // queue exhausted for this lane
+          }
+        }
       }
     }
     if (pf == PF_ID) pf_vm = Q.ids[pf_pos];     // issue the id load; consumed next boundary
@@ -545,11 +568,16 @@ cudaError_t launch_persist(const StepVariant& var, const DevState& S, const Para
   const uint32_t warps_needed = (Q.count + 31u) / 32u;
   const uint32_t max_useful = (warps_needed + sh.warps - 1u) / sh.warps;
   if (grid > max_useful) grid = max_useful;
+  // the last (resident lanes) positions are the tail: served one VM at a
+  // time to idle lanes so that no lane queues a second VM behind a running one
+  Queue q = Q;
+  const uint64_t lanes = (uint64_t)grid * sh.warps * 32u;
+  q.soft_end = Q.count > lanes ? (uint32_t)(Q.count - lanes) : 0u;
   if (sh.staged)
-    pick_staged(var)<<<grid, 32u * sh.warps, sh.smem, stream>>>(S, P, Q, sh.ncap, sh.slot_words, sh.epoch,
+    pick_staged(var)<<<grid, 32u * sh.warps, sh.smem, stream>>>(S, P, q, sh.ncap, sh.slot_words, sh.epoch,
                                                                  sh.refill_min);
   else
-    pick_global(var)<<<grid, 32u * sh.warps, 0, stream>>>(S, P, Q, sh.epoch);
+    pick_global(var)<<<grid, 32u * sh.warps, 0, stream>>>(S, P, q, sh.epoch);
   return cudaGetLastError();
 }
 

@@ -190,7 +190,7 @@ void plan_buckets(rasp_batch* b) {
       sh.staged = false;
       sh.warps = 4;
       sh.refill_min = 1;
-      sh.epoch = b->cfg.epoch ? b->cfg.epoch : 64u;
+      sh.epoch = b->cfg.epoch ? b->cfg.epoch : 128u;
     }
     if (b->cfg.warps_per_cta) sh.warps = std::min<uint32_t>(b->cfg.warps_per_cta, 8u);
     if (b->cfg.refill_min) sh.refill_min = std::min<uint32_t>(b->cfg.refill_min, 32u);

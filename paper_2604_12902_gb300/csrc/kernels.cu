@@ -426,6 +426,23 @@ __global__ void __launch_bounds__(128, 7) k_persist_gl(DevState S, Params P, Que
       }
     }
     if (pf == PF_ID) pf_vm = Q.ids[pf_pos];     // issue the id load; consumed next boundary
+    if (tail && vm < 0 && pf == PF_ID) {
+      // an idle lane in the tail starts its VM at once (waiting on the loads
+      // here) instead of two boundaries later
+      nstatus = S.status[pf_vm];
+      load_regs(S, P, pf_vm, nr);
+      nmoff = S.mem_off[pf_vm];
+      pf = PF_EMPTY;
+      if (nstatus == ST_RUNNING) {
+        r = nr;
+        arm_regs(P, r);
+        vm = (int32_t)pf_vm;
+        M = S.mem + nmoff;
+        T = S.tape + (uint64_t)pf_vm * P.ellp;
+        Y = S.y + (uint64_t)pf_vm * P.sp;
+        active = true;
+      }
+    }
     // done when no lane runs a VM or has one coming
     if (__all_sync(FULL, vm < 0 && pf == PF_NONE)) break;
 

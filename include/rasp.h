@@ -74,6 +74,8 @@ enum rasp_semantics {
 #define RASP_DISPATCH_VOTE     0x100u /* warp opcode voting, one handler/group */
 #define RASP_COLLECT_STATS     0x1000u /* count executed steps per opcode      */
 #define RASP_SHARED_PROGRAM    0x2000u /* programs indexed by prog_of_vm       */
+#define RASP_CUDA_GRAPH        0x4000u /* rasp_run replays a CUDA graph captured
+                                          once per budget (cached, up to 8)   */
 
 typedef struct rasp_config {
     uint32_t word_bits;  /* w, 2..64 (64 for RASP_CHECKED)                     */

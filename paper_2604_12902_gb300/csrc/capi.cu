@@ -51,6 +51,15 @@ struct Bucket {
   PersistShape shape{};
 };
 
+// One launch: adjacent buckets on the HBM-slab persistent schedule share one
+// queue (that schedule does not depend on n); others launch per bucket.
+struct Group {
+  uint32_t first = 0;
+  uint32_t count = 0;
+  uint32_t sched = 0;
+  PersistShape shape{};
+};
+
 struct Layout {
   size_t off_i, off_a, off_steps, off_cap, off_status, off_uhead, off_ylen, off_n, off_memoff;
   size_t off_mem, off_prog, off_progoff, off_progvm, off_tape, off_y, off_ids, off_heads, off_err,
@@ -86,7 +95,11 @@ struct rasp_batch {
   bool programs_loaded = false, inputs_loaded = false;
   std::vector<uint32_t> h_ids;  // bucket-ordered VM ids
   std::vector<Bucket> buckets;
+  std::vector<Group> groups;
   uint64_t launches = 0;
+  // CUDA graphs of rasp_run, one per budget (RASP_CUDA_GRAPH)
+  cudaStream_t cap_stream = nullptr;
+  std::vector<std::pair<uint64_t, cudaGraphExec_t>> graphs;
 };
 
 namespace {
@@ -194,14 +207,34 @@ void plan_buckets(rasp_batch* b) {
     }
     if (b->cfg.warps_per_cta) sh.warps = std::min<uint32_t>(b->cfg.warps_per_cta, 8u);
     if (b->cfg.refill_min) sh.refill_min = std::min<uint32_t>(b->cfg.refill_min, 32u);
+    if (sched == RASP_SCHED_PLAIN) plain_configure(var);
     if (sched != RASP_SCHED_PLAIN) {
       if (persist_configure(var, sh) == 0) {
+        plain_configure(var);
         k.sched = RASP_SCHED_PLAIN;        // cannot be resident: fall back to the plain form
       } else if (b->cfg.ctas_per_sm && b->cfg.ctas_per_sm < sh.ctas_per_sm) {
         sh.grid = sh.grid / sh.ctas_per_sm * b->cfg.ctas_per_sm;
         sh.ctas_per_sm = b->cfg.ctas_per_sm;
       }
     }
+  }
+}
+
+void build_groups(rasp_batch* b) {
+  b->groups.clear();
+  for (const Bucket& k : b->buckets) {
+    if (!k.count) continue;
+    if (!b->groups.empty() && k.sched == RASP_SCHED_PERSIST_GL && b->groups.back().sched == RASP_SCHED_PERSIST_GL &&
+        b->groups.back().first + b->groups.back().count == k.first) {
+      b->groups.back().count += k.count;
+      continue;
+    }
+    Group g;
+    g.first = k.first;
+    g.count = k.count;
+    g.sched = k.sched;
+    g.shape = k.shape;
+    b->groups.push_back(g);
   }
 }
 
@@ -326,6 +359,15 @@ int rasp_batch_create(const rasp_config* cfg, uint64_t num_vms, const uint32_t* 
     b->h_ids[b->buckets[k].first + fill[k]++] = (uint32_t)v;
   }
   plan_buckets(b);
+  build_groups(b);
+  if (cfg->flags & RASP_CUDA_GRAPH) {
+    if (cudaStreamCreateWithFlags(&b->cap_stream, cudaStreamNonBlocking) != cudaSuccess) {
+      cudaGetLastError();
+      if (b->owns) cudaFree(b->base);
+      delete b;
+      return fail(RASP_ECUDA, "cannot create the capture stream");
+    }
+  }
 
   cudaStream_t st = b->stream;
   auto cleanup_fail = [&](int code) {
@@ -422,7 +464,7 @@ int rasp_load_inputs(rasp_batch* b, const int64_t* tape, const uint64_t* offsets
     bool uniform = true;
     for (uint32_t v = 1; v < b->V && uniform; ++v) uniform = caps[v] == caps[0];
     if (!uniform) {
-      for (const Bucket& k : b->buckets) {
+      for (const Group& k : b->groups) {
         if (k.count < 2) continue;
         auto first = b->h_ids.begin() + k.first;
         std::stable_sort(first, first + k.count, [&](uint32_t x, uint32_t y) { return caps[x] > caps[y]; });
@@ -448,10 +490,12 @@ int rasp_reset(rasp_batch* b) {
   return RASP_OK;
 }
 
-int rasp_run(rasp_batch* b, uint64_t max_steps) {
-  if (!b) return fail(RASP_EINVAL, "batch is NULL");
-  if (!b->programs_loaded || !b->inputs_loaded) return fail(RASP_ESTATE, "load programs and inputs before rasp_run");
-  cudaStream_t st = b->stream;
+}  // extern "C"
+
+namespace {
+
+// Enqueue one rasp_run on `st`: reset the queue counters, one launch per group.
+int enqueue_run(rasp_batch* b, cudaStream_t st, uint64_t max_steps) {
   const StepVariant var = variant_of(b);
   Params P{};
   P.wmask = b->wmask;
@@ -463,19 +507,54 @@ int rasp_run(rasp_batch* b, uint64_t max_steps) {
   P.err = b->d_err;
   P.hist = b->d_hist;
   CK(cudaMemsetAsync(b->d_heads, 0, 8 * kNumBuckets, st));
-  b->launches = 0;
-  for (size_t k = 0; k < b->buckets.size(); ++k) {
-    const Bucket& bk = b->buckets[k];
-    if (!bk.count) continue;
-    const uint32_t* ids = b->d_ids + bk.first;
-    if (bk.sched == RASP_SCHED_PLAIN) {
-      CK(launch_plain(var, b->S, P, ids, bk.count, st));
+  uint64_t launches = 0;
+  for (size_t k = 0; k < b->groups.size(); ++k) {
+    const Group& g = b->groups[k];
+    const uint32_t* ids = b->d_ids + g.first;
+    if (g.sched == RASP_SCHED_PLAIN) {
+      CK(launch_plain(var, b->S, P, ids, g.count, st));
     } else {
-      Queue Q{ids, bk.count, b->d_heads + k, b->d_heads + kNumBuckets + k, 0};
-      CK(launch_persist(var, b->S, P, Q, bk.shape, st));
+      Queue Q{ids, g.count, b->d_heads + k, b->d_heads + kNumBuckets + k, 0};
+      CK(launch_persist(var, b->S, P, Q, g.shape, st));
     }
-    b->launches++;
+    launches++;
   }
+  b->launches = launches;
+  return RASP_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int rasp_run(rasp_batch* b, uint64_t max_steps) {
+  if (!b) return fail(RASP_EINVAL, "batch is NULL");
+  if (!b->programs_loaded || !b->inputs_loaded) return fail(RASP_ESTATE, "load programs and inputs before rasp_run");
+  if (!b->cap_stream) return enqueue_run(b, b->stream, max_steps);
+  // CUDA graph: capture the run once per budget on a private stream, replay it on the batch stream
+  cudaGraphExec_t exec = nullptr;
+  for (auto& e : b->graphs)
+    if (e.first == max_steps) exec = e.second;
+  if (!exec) {
+    CK(cudaStreamBeginCapture(b->cap_stream, cudaStreamCaptureModeThreadLocal));
+    const int rc = enqueue_run(b, b->cap_stream, max_steps);
+    cudaGraph_t graph = nullptr;
+    const cudaError_t e = cudaStreamEndCapture(b->cap_stream, &graph);
+    if (rc != RASP_OK) {
+      if (graph) cudaGraphDestroy(graph);
+      return rc;
+    }
+    if (e != cudaSuccess) return fail(RASP_ECUDA, "cudaStreamEndCapture: %s", cudaGetErrorString(e));
+    const cudaError_t ei = cudaGraphInstantiate(&exec, graph, 0);
+    cudaGraphDestroy(graph);
+    if (ei != cudaSuccess) return fail(RASP_ECUDA, "cudaGraphInstantiate: %s", cudaGetErrorString(ei));
+    if (b->graphs.size() >= 8) {
+      cudaGraphExecDestroy(b->graphs.front().second);
+      b->graphs.erase(b->graphs.begin());
+    }
+    b->graphs.emplace_back(max_steps, exec);
+  }
+  CK(cudaGraphLaunch(exec, b->stream));
   return RASP_OK;
 }
 
@@ -621,7 +700,17 @@ int rasp_describe(const rasp_batch* b, char* buf, uint64_t size) {
     s += tmp;
     first = false;
   }
-  s += "]}";
+  s += "], \"launches\": [";
+  first = true;
+  for (const Group& g : b->groups) {
+    char tmp[256];
+    snprintf(tmp, sizeof(tmp), "%s{\"vms\": %u, \"schedule\": \"%s\", \"grid\": %u}", first ? "" : ", ",
+             g.count, names[(g.sched >> 4) & 3], g.shape.grid);
+    s += tmp;
+    first = false;
+  }
+  s += "], \"cuda_graph\": ";
+  s += b->cap_stream ? "true}" : "false}";
   if (s.size() + 1 > size) return fail(RASP_EINVAL, "buffer of %llu bytes is too small", (unsigned long long)size);
   memcpy(buf, s.c_str(), s.size() + 1);
   return RASP_OK;
@@ -630,6 +719,8 @@ int rasp_describe(const rasp_batch* b, char* buf, uint64_t size) {
 void rasp_batch_destroy(rasp_batch* b) {
   if (!b) return;
   cudaStreamSynchronize(b->stream);
+  for (auto& e : b->graphs) cudaGraphExecDestroy(e.second);
+  if (b->cap_stream) cudaStreamDestroy(b->cap_stream);
   if (b->owns && b->base) cudaFree(b->base);
   delete b;
 }

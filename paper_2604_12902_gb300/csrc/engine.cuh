@@ -311,9 +311,10 @@ __device__ __forceinline__ uint32_t one_step(uint64_t* __restrict__ M, const uin
                                              uint64_t* __restrict__ Y, const Params& P, Regs& r, Hist& h) {
   const uint32_t ip = r.ip, n = r.n;
   const uint32_t ilim = MASKED ? r.ilim : n;
-  const bool aligned = (((ip | n) & 1u) == 0u) & (r.ibase == 0ull);
+  // i = ip < n even with ip + 1 < n: i != 2^w - 1 and M[ip], M[ip+1] is one
+  // aligned 16-byte word (slabs start 16-byte aligned)
+  const bool aligned = ((ip & 1u) == 0u) & (ip + 1u < n) & (r.ibase == 0ull);
   if (PIPE && aligned && !r.have) {
-    // even n and even i = ip < n: i != 2^w - 1 and M[ip], M[ip+1] is one 16-byte word
     r.cur = *reinterpret_cast<const ulonglong2*>(M + ip);
     r.have = true;
   }
@@ -368,7 +369,7 @@ __device__ __forceinline__ uint32_t one_step(uint64_t* __restrict__ M, const uin
         // the next pair: the jump target's (if aligned) or the sequential one,
         // unless this step's store overwrote it
         r.cur = taken ? pr : seq;
-        r.have = taken ? ((jm & 1u) == 0u) : (seq_ok & !(wr & ((jm | 1u) == (nip | 1u))));
+        r.have = taken ? (((jm & 1u) == 0u) & (jm + 1u < n)) : (seq_ok & !(wr & ((jm | 1u) == (nip | 1u))));
       }
       r.left -= 1u;
       if constexpr (HIST) h.c[8] += (pri & !put) ? 1u : 0u;

@@ -33,6 +33,9 @@ cudaError_t launch_pack(const DevState& S, const uint64_t* prog, const uint64_t*
                         const uint32_t* prog_of_vm, uint32_t num_vms, uint64_t wmask, uint32_t sp,
                         cudaStream_t stream);
 
+// One-time function attributes of the plain kernel (carveout).
+void plain_configure(const StepVariant& var);
+
 cudaError_t launch_plain(const StepVariant& var, const DevState& S, const Params& P,
                          const uint32_t* ids, uint32_t count, cudaStream_t stream);
 

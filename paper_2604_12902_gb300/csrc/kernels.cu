@@ -544,14 +544,17 @@ cudaError_t launch_pack(const DevState& S, const uint64_t* prog, const uint64_t*
   return cudaGetLastError();
 }
 
+void plain_configure(const StepVariant& var) {
+  cudaFuncSetAttribute(pick_plain(var), cudaFuncAttributePreferredSharedMemoryCarveout,
+                       (int)cudaSharedmemCarveoutMaxL1);
+  cudaGetLastError();
+}
+
 cudaError_t launch_plain(const StepVariant& var, const DevState& S, const Params& P, const uint32_t* ids,
                          uint32_t count, cudaStream_t stream) {
   if (!count) return cudaSuccess;
   const uint32_t blocks = (count + 255u) / 256u;
-  PlainFn fn = pick_plain(var);
-  cudaFuncSetAttribute(fn, cudaFuncAttributePreferredSharedMemoryCarveout, (int)cudaSharedmemCarveoutMaxL1);
-  cudaGetLastError();
-  fn<<<blocks, 256, 0, stream>>>(S, P, ids, count);
+  pick_plain(var)<<<blocks, 256, 0, stream>>>(S, P, ids, count);
   return cudaGetLastError();
 }
 

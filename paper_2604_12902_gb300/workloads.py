@@ -303,3 +303,169 @@ def _template_chunk(ids, seed, I, n, T, trip_lo, trip_hi, loops_lo, loops_hi,
     out[:, 1::2] = arg
     return out
 
+
+
+def draws_ragged(seed: int, tag: int, vm_ids: np.ndarray, counts: np.ndarray) -> np.ndarray:
+    """Flat uint32 draws: the first counts[v] entries of draws(seed, tag,
+    [vm_ids[v]], .) for every v, concatenated (same values as `draws`)."""
+    vm = np.asarray(vm_ids, dtype=np.uint64)
+    counts = np.asarray(counts, dtype=np.int64)
+    nblk = (counts + 3) // 4
+    bvm = np.repeat(np.arange(vm.shape[0]), nblk)
+    bstart = np.concatenate([[0], np.cumsum(nblk)[:-1]])
+    bidx = (np.arange(bvm.shape[0]) - bstart[bvm]).astype(np.uint32)
+    v64 = vm[bvm]
+    out = philox4x32(bidx, (v64 & _MASK32).astype(np.uint32), (v64 >> np.uint64(32)).astype(np.uint32),
+                     np.uint32(tag & 0xFFFFFFFF), np.uint32(seed & 0xFFFFFFFF),
+                     np.uint32((seed >> 32) & 0xFFFFFFFF))
+    blocks = np.stack(out, axis=-1).reshape(-1)                 # 4 words per block, in block order
+    svm = np.repeat(np.arange(vm.shape[0]), counts)
+    sstart = np.concatenate([[0], np.cumsum(counts)[:-1]])
+    t = np.arange(svm.shape[0]) - sstart[svm]
+    return blocks[4 * bstart[svm] + t]
+
+
+def _uniform_rows(u32: np.ndarray, lo, hi) -> np.ndarray:
+    """uniform_int with per-element bounds."""
+    span = (np.asarray(hi, np.int64) - np.asarray(lo, np.int64) + 1).astype(np.uint64)
+    return ((u32.astype(np.uint64) * span) >> np.uint64(32)).astype(np.int64) + lo
+
+
+# ---------------------------------------------------------------------------
+# Uneven batch: program length log-uniform in [8, 512] instructions, memory
+# log-uniform in [16, 4096] words (raised to fit the program and its data,
+# never rounded), step cap log-uniform in [64, 65536]. Programs follow the
+# template structure scaled to their length: R = min(l, (I-3)//4) RD
+# instructions, up to three counter-bounded loops (as many as fit), straight-
+# line blocks, PRI PRI HLT. With probability p_nonhalting the loop decrement
+# is LOD 0 instead of LOD -1, so a program with a loop never halts.
+# ---------------------------------------------------------------------------
+def uneven_programs(num_vms: int = 1 << 22, seed: int = 3, len_lo: int = 8, len_hi: int = 512,
+                    n_lo: int = 16, n_hi: int = 4096, cap_lo: int = 64, cap_hi: int = 65536,
+                    p_nonhalting: float = 0.15, tape_len: int = 16, s: int = 8, first_vm: int = 0,
+                    chunk: int = 1 << 16, workers: int = 0) -> Workload:
+    """``workers`` > 1 generates chunks in a spawn-context process pool (safe
+    after CUDA has been initialised in the calling process); the result does
+    not depend on it."""
+    args = [(first_vm + c0, min(chunk, num_vms - c0), seed, len_lo, len_hi, n_lo, n_hi, cap_lo, cap_hi,
+             p_nonhalting, tape_len) for c0 in range(0, num_vms, chunk)]
+    if workers > 1 and len(args) > 1:
+        import multiprocessing as mp
+        from concurrent.futures import ProcessPoolExecutor
+        with ProcessPoolExecutor(min(workers, len(args)), mp_context=mp.get_context("spawn")) as ex:
+            parts = list(ex.map(_uneven_job, args))
+    else:
+        parts = [_uneven_job(a) for a in args]
+    progs, offs, mems, tapes, caps = [], [], [], [], []
+    total = 0
+    for words, I, n, cap, tape in parts:
+        progs.append(words)
+        offs.append(total + np.concatenate([[0], np.cumsum(2 * I)[:-1]]))
+        total += int(2 * I.sum())
+        mems.append(n)
+        caps.append(cap)
+        tapes.append(tape)
+    prog_off = np.zeros(num_vms + 1, np.uint64)
+    prog_off[:-1] = np.concatenate(offs).astype(np.uint64)
+    prog_off[-1] = total
+    return Workload("uneven", np.concatenate(progs), prog_off, np.concatenate(mems).astype(np.uint32),
+                    np.concatenate(tapes).reshape(-1), _regular_offsets(num_vms, tape_len),
+                    np.concatenate(caps).astype(np.uint64), ell=tape_len, s=s,
+                    meta=dict(seed=seed, p_nonhalting=p_nonhalting))
+
+
+def _uneven_job(a):
+    first, cnt, seed, len_lo, len_hi, n_lo, n_hi, cap_lo, cap_hi, p_nonhalting, tape_len = a
+    ids = np.arange(first, first + cnt, dtype=np.uint64)
+    words, I, n, cap = _uneven_chunk(ids, seed, len_lo, len_hi, n_lo, n_hi, cap_lo, cap_hi,
+                                     p_nonhalting, tape_len)
+    tape = uniform_int(draws(seed, 4, ids, tape_len), -1000, 1000)
+    return words, I, n, cap, tape
+
+
+def _uneven_chunk(ids, seed, len_lo, len_hi, n_lo, n_hi, cap_lo, cap_hi, p_nonhalting, tape_len):
+    V = ids.shape[0]
+    st = draws(seed, 1, ids, 16)
+    I = log_uniform_int(st[:, 0], len_lo, len_hi)
+    R = np.minimum(tape_len, np.maximum(0, (I - 3) // 4))
+    D = 2 * I
+    n = np.maximum(log_uniform_int(st[:, 1], n_lo, n_hi), D + R + 3 + 8)
+    cap = log_uniform_int(st[:, 2], cap_lo, cap_hi)
+    nonhalt = (st[:, 3].astype(np.float64) / 4294967296.0) < p_nonhalting
+    lmax = np.clip((I - R - 3) // 13, 0, 3)
+    L = np.where(lmax > 0, _uniform_rows(st[:, 4], np.minimum(1, lmax), lmax), 0)
+    trips = np.stack([uniform_int(st[:, 5 + k], 1, 64) for k in range(3)], axis=1)
+    extra = np.maximum(0, I - R - 3 - 13 * L) // np.maximum(L, 1)
+    body = np.stack([1 + np.minimum(uniform_int(st[:, 8 + k], 0, 2), extra) for k in range(3)], axis=1)
+    present = np.arange(3)[None, :] < L[:, None]
+    loop_len = np.where(present, 12 + body, 0)
+    fill_total = I - R - 3 - loop_len.sum(axis=1)
+    assert np.all(fill_total >= 0)
+    fills = np.zeros((V, 4), np.int64)
+    rest = fill_total.copy()
+    for g in range(3):
+        take = uniform_int(st[:, 11 + g], 0, 1 << 20) % (rest // 2 + 1)
+        take = np.where(g < L, take, 0)
+        fills[:, g] = take
+        rest = rest - take
+    fills[np.arange(V), L] += rest
+    seg_len = np.stack([R, fills[:, 0], loop_len[:, 0], fills[:, 1], loop_len[:, 1],
+                        fills[:, 2], loop_len[:, 2], fills[:, 3], np.full(V, 3)], axis=1)
+    seg_kind = np.array([_SEG_PROLOGUE, _SEG_FILL, _SEG_LOOP, _SEG_FILL, _SEG_LOOP,
+                         _SEG_FILL, _SEG_LOOP, _SEG_FILL, _SEG_EPI])
+    seg_loop = np.array([-1, -1, 0, -1, 1, -1, 2, -1, -1])
+    seg_end = np.cumsum(seg_len, axis=1)
+    assert np.all(seg_end[:, -1] == I)
+    # flat per-instruction arrays
+    vm = np.repeat(np.arange(V), I)
+    start = np.concatenate([[0], np.cumsum(I)[:-1]])
+    t = np.arange(vm.shape[0]) - start[vm]
+    bounds = (start[:, None] + seg_end).reshape(-1)
+    g = np.searchsorted(bounds, np.arange(vm.shape[0]), side="right")
+    k = g % 9
+    seg_start = (seg_end - seg_len)[vm, k]
+    r = t - seg_start
+    kind = seg_kind[k]
+    li = np.clip(seg_loop[k], 0, 2)
+    b = body[vm, li]
+    Tk = trips[vm, li]
+    Dv, Rv, nv = D[vm], R[vm], n[vm]
+    c_k = Dv + Rv + li
+    scratch_lo = Dv + Rv + 3
+    cls = uniform_int(draws_ragged(seed, 2, ids, I), 0, 3)
+    oper = draws_ragged(seed, 3, ids, I)
+    rnd_op = np.array([LOD, ADD, MUL, STO])[cls]
+    rnd_arg = np.where(cls == 0, uniform_int(oper, -8, 8),
+                       np.where(cls == 3, _uniform_rows(oper, scratch_lo, nv - 1),
+                                _uniform_rows(oper, Dv, nv - 1)))
+    op = np.zeros(vm.shape[0], np.int64)
+    arg = np.zeros(vm.shape[0], np.int64)
+    m = kind == _SEG_PROLOGUE
+    op[m] = RD
+    arg[m] = (Dv + r)[m]
+    m = kind == _SEG_FILL
+    op[m] = rnd_op[m]
+    arg[m] = rnd_arg[m]
+    m = (kind == _SEG_EPI) & (r < 2)
+    op[m] = PRI
+    arg[m] = _uniform_rows(oper, Dv, nv - 1)[m]
+    drop = nonhalt[vm]
+    lp = kind == _SEG_LOOP
+    st0 = start[vm] * 0 + seg_start
+    table = [
+        (r == 0, LOD, Tk), (r == 1, STO, c_k), (r == 2, LOD, 0), (r == 3, ADD, c_k),
+        (r == 4, BNZ, 2 * (st0 + 7)), (r == 5, LOD, 1), (r == 6, BNZ, 2 * (st0 + 12 + b)),
+        (r == 7 + b, LOD, np.where(drop, 0, -1)), (r == 8 + b, ADD, c_k), (r == 9 + b, STO, c_k),
+        (r == 10 + b, LOD, 1), (r == 11 + b, BNZ, 2 * (st0 + 2)),
+    ]
+    for cond, o, a in table:
+        mm = lp & cond
+        op[mm] = o
+        arg[mm] = np.broadcast_to(a, vm.shape)[mm]
+    mb = lp & (r >= 7) & (r < 7 + b)
+    op[mb] = rnd_op[mb]
+    arg[mb] = rnd_arg[mb]
+    words = np.empty(2 * vm.shape[0], np.int64)
+    words[0::2] = op
+    words[1::2] = arg
+    return words, I, n, cap

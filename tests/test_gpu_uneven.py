@@ -1,0 +1,98 @@
+"""Uneven batches: mixed program lengths, memory sizes (odd n, non powers of
+two, 16..4096 words) and step caps, about 30% non-halting; bucketing, merged
+launches, longest-cap-first order and CUDA-graph replay (needs a GPU)."""
+import os
+
+import numpy as np
+import pytest
+
+from paper_2604_12902_gb300 import workloads as W
+from tests.helpers import U64, assert_same_state, oracle_state
+
+pytestmark = pytest.mark.gpu
+THREADS = os.cpu_count() or 1
+
+
+@pytest.fixture(scope="module")
+def rasp():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2604_12902_gb300 import rasp as R
+    R.lib()
+    return R
+
+
+@pytest.fixture(scope="module")
+def uneven64k():
+    wl = W.uneven_programs(num_vms=1 << 16, seed=3)
+    st, _ = oracle_state(wl, threads=THREADS)
+    return wl, st
+
+
+@pytest.mark.parametrize("flags", [0x00, 0x10, 0x20, 0x30, 0x4000, 0x4030, 0x130])
+def test_uneven_batch_every_vm(rasp, uneven64k, flags):
+    wl, st = uneven64k
+    with rasp.Batch(wl.mem_words, wl.ell, wl.s, flags=flags) as b:
+        b.load_workload(wl)
+        b.run()
+        got = b.read_state()
+        if flags & 0x4000:                       # replay the captured graph on a fresh c_0
+            b.reset()
+            b.run()
+            again = b.read_state()
+            for k in got:
+                assert np.array_equal(got[k], again[k]), k
+    assert_same_state(got, st, wl.ell, wl.s, what="uneven flags=%#x" % flags)
+    counts = np.bincount(st.status, minlength=5)
+    assert 0.2 < counts[2] / wl.num_vms < 0.45           # about 30% time out
+
+
+def test_graph_replay_with_budgets(rasp, uneven64k):
+    wl, full = uneven64k
+    part, _ = oracle_state(wl, budget=300, threads=THREADS)
+    with rasp.Batch(wl.mem_words, wl.ell, wl.s, flags=0x4000) as b:
+        b.load_workload(wl)
+        b.run(300)
+        got = b.read_state()
+        assert_same_state(got, part, wl.ell, wl.s, what="graph budget 300")
+        b.run()
+        got = b.read_state()
+        assert_same_state(got, full, wl.ell, wl.s, what="graph resumed")
+        assert b.describe()["cuda_graph"] is True
+
+
+def test_auto_schedule_merges_buckets_into_one_launch(rasp, uneven64k):
+    wl, _ = uneven64k
+    with rasp.Batch(wl.mem_words, wl.ell, wl.s) as b:
+        d = b.describe()
+        assert len(d["buckets"]) >= 5
+        assert len(d["launches"]) == 1 and d["launches"][0]["vms"] == wl.num_vms
+        b.load_workload(wl)
+        b.run()
+        assert b.stats()["launches"] == 1
+
+
+def test_uneven_full_size_sampled(rasp):
+    """4,194,304 programs (about 28 GiB of M): every VM checked for the
+    invariants, 3,000 sampled VMs compared with the oracle field by field."""
+    wl = W.uneven_programs(num_vms=1 << 22, seed=3, workers=THREADS)
+    with rasp.Batch(wl.mem_words, wl.ell, wl.s, flags=0x4000) as b:
+        b.load_workload(wl)
+        b.run()
+        got = b.read_state(mem=False)
+        stats = b.stats()
+        rng = np.random.default_rng(33)
+        ids = np.sort(rng.choice(wl.num_vms, size=3000, replace=False))
+        mems = [b.read_state(first=int(v), count=1)["mem"] for v in ids]
+    assert np.all(got["steps"] <= wl.caps)
+    assert set(np.unique(got["status"])) <= {1, 2}
+    to = got["status"] == 2
+    assert np.all(got["steps"][to] == wl.caps[to])
+    assert 0.2 < to.mean() < 0.45
+    assert stats["vm_steps"] == int(got["steps"].sum())
+    sub = wl.subset(ids)
+    st, _ = oracle_state(sub, threads=THREADS)
+    sel = {k: got[k][ids] for k in ("i", "a", "steps", "status", "uhead", "ylen", "y")}
+    sel["mem"] = np.concatenate(mems)
+    assert_same_state(sel, st, wl.ell, wl.s, what="uneven full-size sample")

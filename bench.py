@@ -116,6 +116,11 @@ def make_workload(name: str, rank: int, vms: int = 1 << 20):
     if name == "templates":
         return W.template_programs(num_vms=vms, seed=2, first_vm=rank * vms), \
             "%s template programs (64 instr, 1-3 loops, trips U[1,64]), n=256, l=16, s=8, cap 4096" % format(vms, ",")
+    if name == "uneven":
+        wl = W.uneven_programs(num_vms=vms if vms != 1 << 20 else 1 << 22, seed=3,
+                               first_vm=rank * (1 << 22), workers=os.cpu_count() or 1)
+        return wl, ("%s uneven programs (length log-U[8,512], n log-U[16,4096], cap log-U[64,65536], "
+                    "~30%% non-halting), l=16, s=8" % format(wl.num_vms, ","))
     if name == "random":
         return W.random_programs(num_vms=1024, seed=1, first_vm=rank * 1024), \
             "1,024 random programs (32 instr, opcodes U{1..7}, operands U[0,63]), n=64, l=4, s=8, cap 256"
@@ -183,12 +188,13 @@ def main():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
-    ap.add_argument("--workload", default="templates", choices=["templates", "random"])
+    ap.add_argument("--workload", default="templates", choices=["templates", "uneven", "random"])
     ap.add_argument("--flags", type=lambda x: int(x, 0), default=0, help="rasp_config.flags (schedule)")
     ap.add_argument("--epoch", type=int, default=0)
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU-oracle baseline")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-plain", action="store_true")
+    ap.add_argument("--no-tune", action="store_true", help="skip the (untimed) schedule autotuning")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--vms", type=int, default=1 << 20, help="template programs per GPU (profiling cases)")
     args = ap.parse_args()
@@ -210,6 +216,9 @@ def main():
     stream = torch.cuda.current_stream()
     b = R.Batch(wl.mem_words, wl.ell, wl.s, flags=args.flags, epoch=args.epoch)
     b.load_workload(wl)
+    tuned = None
+    if (args.flags & R.SCHED_PERSIST_GL) == 0 and not args.epoch and not args.no_tune:
+        tuned = b.autotune(reps=2)      # untimed: measured schedule choice, state unchanged
 
     # opcode mix (and total steps) from an untimed counting run
     with R.Batch(wl.mem_words, wl.ell, wl.s, flags=args.flags | R.COLLECT_STATS, epoch=args.epoch) as bs:
@@ -254,6 +263,8 @@ def main():
     pack_ms = [e[0].elapsed_time(e[1]) for e in evs]
     b.sync()
     st = b.stats()
+    run_launches = int(st["launches"])
+    m_bytes = float(wl.mem_words.astype(np.uint64).sum()) * 8.0
     assert st["vm_steps"] == total_steps, "timed runs disagree with the counting run"
 
     ms_total = torch.tensor([elapsed_ms], device="cuda")
@@ -341,11 +352,12 @@ def main():
                 "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True,
                 "scaling": "weak", "vs_baseline": None, "dtype": "int64", "data": "synthetic",
                 "config": {"workload": desc, "vms_per_gpu": wl.num_vms, "vm_steps_per_gpu": total_steps,
-                           "l2": "inputs larger than L2 (M = %.1f GiB)" % (wl.num_vms * 256 * 8 / 2 ** 30
-                                                                          if args.workload == "templates" else 0.0),
-                           "schedule_flags": args.flags, "parallelism": "vm shards x%d" % ws},
+                           "l2": "inputs larger than L2 (M = %.2f GiB)" % (m_bytes / 2 ** 30)
+                                 if m_bytes > 129e6 else "M below L2 size (%.1f MB); no flush" % (m_bytes / 1e6),
+                           "schedule_flags": args.flags, "parallelism": "vm shards x%d" % ws,
+                           "schedule": tuned["chosen"] if tuned else "flags %#x" % args.flags},
                 "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "plain": plain,
-                "gpu_launches": 2 * args.steps, "clocks": clocks}
+                "gpu_launches": (1 + run_launches) * args.steps, "clocks": clocks}
         print(json.dumps(line), flush=True)
     if dist:
         dist.destroy_process_group()

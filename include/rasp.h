@@ -69,6 +69,9 @@ enum rasp_semantics {
 #define RASP_SCHED_PLAIN       0x10u  /* one thread per VM, state in HBM      */
 #define RASP_SCHED_PERSIST     0x20u  /* persistent workers, M staged in SMEM */
 #define RASP_SCHED_PERSIST_GL  0x30u  /* persistent workers, M in HBM via L1  */
+#define RASP_SCHED_SHARED      0x40u  /* one CTA per program, program words in
+                                         SMEM (fetched while the VM has not
+                                         written into them); needs prog_of_vm */
 #define RASP_SCHED_MASK        0xF0u
 #define RASP_DISPATCH_SELECT   0x000u /* branch-free guarded-sum step         */
 #define RASP_DISPATCH_VOTE     0x100u /* warp opcode voting, one handler/group */
@@ -84,7 +87,8 @@ typedef struct rasp_config {
     uint32_t out_cap;    /* s: output capacity (y holds s+1 words)             */
     uint32_t flags;      /* RASP_SCHED_* | RASP_DISPATCH_* | RASP_COLLECT_STATS */
     uint32_t epoch;      /* steps between warp scheduling points; 0 = default  */
-    uint32_t warps_per_cta; /* persistent kernels: warps per CTA; 0 = default  */
+    uint32_t warps_per_cta; /* persistent kernels: warps per CTA (SMEM-staged
+                            up to 8, HBM-slab up to 4); 0 = default           */
     uint32_t refill_min; /* persistent kernels: idle lanes that trigger a
                             refill; 0 = default                               */
     uint32_t ctas_per_sm;/* persistent kernels: resident CTAs per SM (fewer
@@ -185,6 +189,16 @@ int rasp_load_state(rasp_batch* b, uint64_t first, uint64_t count,
 
 /* Aggregate counters of the batch (synchronises the stream). */
 int rasp_read_stats(rasp_batch* b, rasp_stats* out);
+
+/* Measured schedule choice (SURVEY's autotuner): times candidate schedules
+ * (persistent over HBM slabs with several epochs and CTA shapes, plain, and
+ * SMEM-staged where it fits) on this batch from its current state with the
+ * given step budget, `reps` times each, restoring the state after every
+ * trial, then adopts the fastest for later rasp_run calls (replacing any
+ * schedule flag of the config). The machine state is left unchanged.
+ * Allocates a temporary snapshot of the state (ENOMEM if it does not fit).
+ * Synchronises the stream. The trial times appear in rasp_describe. */
+int rasp_autotune(rasp_batch* b, uint64_t max_steps, uint32_t reps);
 
 /* Describe the launch plan as JSON into buf (NUL-terminated): per memory
  * bucket its size class, VM count, schedule, grid, warps per CTA, resident

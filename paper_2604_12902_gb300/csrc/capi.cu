@@ -63,7 +63,7 @@ struct Group {
 struct Layout {
   size_t off_i, off_a, off_steps, off_cap, off_status, off_uhead, off_ylen, off_n, off_memoff;
   size_t off_mem, off_prog, off_progoff, off_progvm, off_tape, off_y, off_ids, off_heads, off_err,
-      off_hist, off_stats;
+      off_hist, off_stats, off_dirty, off_pvoff, off_pvids;
   size_t total;
 };
 
@@ -93,13 +93,22 @@ struct rasp_batch {
   uint64_t* d_cap = nullptr;
   bool shared_programs = false;
   bool programs_loaded = false, inputs_loaded = false;
-  std::vector<uint32_t> h_ids;  // bucket-ordered VM ids
+  std::vector<uint32_t> h_ids;       // queue order: bucket-contiguous, sorted within each launch group
+  std::vector<uint32_t> h_ids_base;  // bucket-contiguous, VM id order within a bucket
+  std::vector<uint64_t> h_caps;      // per-VM caps (empty: all uncapped)
   std::vector<Bucket> buckets;
   std::vector<Group> groups;
   uint64_t launches = 0;
   // CUDA graphs of rasp_run, one per budget (RASP_CUDA_GRAPH)
   cudaStream_t cap_stream = nullptr;
   std::vector<std::pair<uint64_t, cudaGraphExec_t>> graphs;
+  std::string tuned;           // JSON report of the last rasp_autotune
+  // shared programs: VMs grouped by program (CSR) and the longest program
+  uint32_t* d_pvoff = nullptr;
+  uint32_t* d_pvids = nullptr;
+  uint32_t num_programs = 0;
+  uint32_t max_plen = 0;
+  bool dirty_valid = false;    // codedirty is up to date (only the shared kernel tracks it)
 };
 
 namespace {
@@ -116,7 +125,7 @@ int validate_config(const rasp_config* cfg, uint64_t num_vms, const uint32_t* me
   if (!mem_words) return fail(RASP_EINVAL, "mem_words is NULL");
   const uint32_t sched = cfg->flags & RASP_SCHED_MASK;
   if (sched != RASP_SCHED_AUTO && sched != RASP_SCHED_PLAIN && sched != RASP_SCHED_PERSIST &&
-      sched != RASP_SCHED_PERSIST_GL)
+      sched != RASP_SCHED_PERSIST_GL && sched != RASP_SCHED_SHARED)
     return fail(RASP_EINVAL, "unknown schedule flag 0x%x", sched);
   if (cfg->word_bits < 64) {
     const uint64_t lim = 1ull << cfg->word_bits;
@@ -157,6 +166,9 @@ Layout make_layout(uint64_t V, uint64_t mem_words, uint32_t ellp, uint32_t sp) {
   L.off_err = take(16);
   L.off_hist = take(8 * 10);
   L.off_stats = take(8 * 6);
+  L.off_dirty = take(V);
+  L.off_pvoff = take(4 * (V + 1));
+  L.off_pvids = take(4 * V);
   L.total = o;
   return L;
 }
@@ -179,6 +191,10 @@ void plan_buckets(rasp_batch* b) {
   for (Bucket& k : b->buckets) {
     if (!k.count) continue;
     uint32_t sched = forced;
+    if (sched == RASP_SCHED_SHARED) {
+      k.sched = sched;                     // one launch over programs, see build_groups
+      continue;
+    }
     const uint32_t slot = [&] {
       uint32_t w = k.ncap + b->ellp + b->sp;
       w = even(w);
@@ -206,6 +222,7 @@ void plan_buckets(rasp_batch* b) {
       sh.epoch = b->cfg.epoch ? b->cfg.epoch : 128u;
     }
     if (b->cfg.warps_per_cta) sh.warps = std::min<uint32_t>(b->cfg.warps_per_cta, 8u);
+    if (!sh.staged) sh.warps = std::min<uint32_t>(sh.warps, 4u);   // k_persist_gl: at most 128 threads
     if (b->cfg.refill_min) sh.refill_min = std::min<uint32_t>(b->cfg.refill_min, 32u);
     if (sched == RASP_SCHED_PLAIN) plain_configure(var);
     if (sched != RASP_SCHED_PLAIN) {
@@ -220,8 +237,34 @@ void plan_buckets(rasp_batch* b) {
   }
 }
 
+// Queue order for the current launch groups: every group's range holds
+// exactly the VMs of its buckets; inside a group, longest cap first (the
+// largest work starts first). Uploads the order.
+int order_ids(rasp_batch* b) {
+  b->h_ids = b->h_ids_base;
+  if (!b->h_caps.empty()) {
+    const std::vector<uint64_t>& caps = b->h_caps;
+    for (const Group& k : b->groups) {
+      if (k.count < 2) continue;
+      auto first = b->h_ids.begin() + k.first;
+      std::stable_sort(first, first + k.count, [&](uint32_t x, uint32_t y) { return caps[x] > caps[y]; });
+    }
+  }
+  CK(cudaMemcpyAsync(b->d_ids, b->h_ids.data(), 4ull * b->V, cudaMemcpyHostToDevice, b->stream));
+  CK(cudaStreamSynchronize(b->stream));
+  return RASP_OK;
+}
+
 void build_groups(rasp_batch* b) {
   b->groups.clear();
+  if ((b->cfg.flags & RASP_SCHED_MASK) == RASP_SCHED_SHARED) {
+    Group g;
+    g.first = 0;
+    g.count = b->V;
+    g.sched = RASP_SCHED_SHARED;
+    b->groups.push_back(g);
+    return;
+  }
   for (const Bucket& k : b->buckets) {
     if (!k.count) continue;
     if (!b->groups.empty() && k.sched == RASP_SCHED_PERSIST_GL && b->groups.back().sched == RASP_SCHED_PERSIST_GL &&
@@ -242,7 +285,8 @@ int check_device_error(rasp_batch* b) {
   int err = 0;
   CK(cudaMemcpyAsync(&err, b->d_err, sizeof(int), cudaMemcpyDeviceToHost, b->stream));
   CK(cudaStreamSynchronize(b->stream));
-  if (err) return fail(RASP_EDEVICE, "a kernel reported internal error %d (bounded wait expired)", err);
+  if (err) return fail(RASP_EDEVICE, "a kernel reported internal error %d (%s)", err,
+                       err == ERR_SLOT ? "VM larger than its bucket's slot" : "bounded wait expired");
   return RASP_OK;
 }
 
@@ -333,6 +377,9 @@ int rasp_batch_create(const rasp_config* cfg, uint64_t num_vms, const uint32_t* 
   b->d_err = (int*)(B + L.off_err);
   b->d_hist = (unsigned long long*)(B + L.off_hist);
   b->d_stats = (unsigned long long*)(B + L.off_stats);
+  S.codedirty = (uint8_t*)(B + L.off_dirty);
+  b->d_pvoff = (uint32_t*)(B + L.off_pvoff);
+  b->d_pvids = (uint32_t*)(B + L.off_pvids);
 
   // buckets by memory size (stable: VM id order within a bucket)
   std::vector<uint32_t> cls(num_vms);
@@ -358,6 +405,7 @@ int rasp_batch_create(const rasp_config* cfg, uint64_t num_vms, const uint32_t* 
     const uint32_t k = cls[v];
     b->h_ids[b->buckets[k].first + fill[k]++] = (uint32_t)v;
   }
+  b->h_ids_base = b->h_ids;
   plan_buckets(b);
   build_groups(b);
   if (cfg->flags & RASP_CUDA_GRAPH) {
@@ -423,10 +471,29 @@ int rasp_load_programs(rasp_batch* b, const int64_t* words, const uint64_t* offs
   if (total) CK(cudaMemcpyAsync(b->d_prog, words, 8 * total, cudaMemcpyHostToDevice, st));
   CK(cudaMemcpyAsync(b->d_progoff, offsets, 8 * (num_programs + 1), cudaMemcpyHostToDevice, st));
   b->shared_programs = prog_of_vm != nullptr;
+  {
+    // VMs grouped by program (counting sort), for the shared-program schedule
+    std::vector<uint32_t> pvoff(num_programs + 1, 0), pvids(b->V);
+    for (uint32_t v = 0; v < b->V; ++v) pvoff[(prog_of_vm ? prog_of_vm[v] : v) + 1]++;
+    for (uint64_t p = 0; p < num_programs; ++p) pvoff[p + 1] += pvoff[p];
+    std::vector<uint32_t> fillp(pvoff.begin(), pvoff.end() - 1);
+    for (uint32_t v = 0; v < b->V; ++v) pvids[fillp[prog_of_vm ? prog_of_vm[v] : v]++] = v;
+    b->max_plen = 0;
+    for (uint64_t p = 0; p < num_programs; ++p)
+      b->max_plen = std::max<uint32_t>(b->max_plen, (uint32_t)(offsets[p + 1] - offsets[p]));
+    if (b->max_plen * 8ull > 200ull * 1024ull && (b->cfg.flags & RASP_SCHED_MASK) == RASP_SCHED_SHARED)
+      return fail(RASP_EINVAL, "shared-program schedule: a program of %u words does not fit in shared memory",
+                  b->max_plen);
+    b->num_programs = (uint32_t)num_programs;
+    CK(cudaMemcpyAsync(b->d_pvoff, pvoff.data(), 4 * pvoff.size(), cudaMemcpyHostToDevice, st));
+    CK(cudaMemcpyAsync(b->d_pvids, pvids.data(), 4ull * b->V, cudaMemcpyHostToDevice, st));
+    CK(cudaStreamSynchronize(st));
+  }
   if (prog_of_vm) CK(cudaMemcpyAsync(b->d_progvm, prog_of_vm, 4ull * b->V, cudaMemcpyHostToDevice, st));
   CK(cudaMemsetAsync(b->d_hist, 0, 8 * 10, st));
   CK(launch_pack(b->S, b->d_prog, b->d_progoff, b->shared_programs ? b->d_progvm : nullptr, b->V, b->wmask, b->sp, st));
   b->programs_loaded = true;
+  b->dirty_valid = true;
   g_err.clear();
   return RASP_OK;
 }
@@ -460,20 +527,17 @@ int rasp_load_inputs(rasp_batch* b, const int64_t* tape, const uint64_t* offsets
   }
   if (caps) {
     CK(cudaMemcpyAsync(b->d_cap, caps, 8ull * b->V, cudaMemcpyHostToDevice, st));
-    // longest-cap-first order inside each bucket (largest work starts first)
     bool uniform = true;
     for (uint32_t v = 1; v < b->V && uniform; ++v) uniform = caps[v] == caps[0];
-    if (!uniform) {
-      for (const Group& k : b->groups) {
-        if (k.count < 2) continue;
-        auto first = b->h_ids.begin() + k.first;
-        std::stable_sort(first, first + k.count, [&](uint32_t x, uint32_t y) { return caps[x] > caps[y]; });
-      }
-      CK(cudaMemcpyAsync(b->d_ids, b->h_ids.data(), 4ull * b->V, cudaMemcpyHostToDevice, st));
-      CK(cudaStreamSynchronize(st));
-    }
+    if (uniform) b->h_caps.clear();
+    else b->h_caps.assign(caps, caps + b->V);
   } else {
     CK(cudaMemsetAsync(b->d_cap, 0xff, 8ull * b->V, st));
+    b->h_caps.clear();
+  }
+  {
+    const int rc = order_ids(b);
+    if (rc) return rc;
   }
   CK(cudaMemsetAsync(b->S.uhead, 0, 4ull * b->V, st));
   b->inputs_loaded = true;
@@ -487,6 +551,7 @@ int rasp_reset(rasp_batch* b) {
   CK(cudaMemsetAsync(b->d_hist, 0, 8 * 10, b->stream));
   CK(launch_pack(b->S, b->d_prog, b->d_progoff, b->shared_programs ? b->d_progvm : nullptr, b->V, b->wmask, b->sp,
                  b->stream));
+  b->dirty_valid = true;
   return RASP_OK;
 }
 
@@ -511,9 +576,20 @@ int enqueue_run(rasp_batch* b, cudaStream_t st, uint64_t max_steps) {
   for (size_t k = 0; k < b->groups.size(); ++k) {
     const Group& g = b->groups[k];
     const uint32_t* ids = b->d_ids + g.first;
-    if (g.sched == RASP_SCHED_PLAIN) {
+    if (g.sched == RASP_SCHED_SHARED) {
+      if (!b->dirty_valid) {
+        // another schedule ran since c_0 and did not track code writes: every
+        // VM fetches from its own slab until the next reset
+        CK(cudaMemsetAsync(b->S.codedirty, 1, b->V, st));
+        b->dirty_valid = true;
+      }
+      CK(launch_shared(var, b->S, P, b->d_prog, b->d_progoff, b->d_pvoff, b->d_pvids, b->num_programs,
+                       b->max_plen, st));
+    } else if (g.sched == RASP_SCHED_PLAIN) {
+      b->dirty_valid = false;
       CK(launch_plain(var, b->S, P, ids, g.count, st));
     } else {
+      b->dirty_valid = false;
       Queue Q{ids, g.count, b->d_heads + k, b->d_heads + kNumBuckets + k, 0};
       CK(launch_persist(var, b->S, P, Q, g.shape, st));
     }
@@ -656,6 +732,7 @@ int rasp_load_state(rasp_batch* b, uint64_t first, uint64_t count, const rasp_st
       o += b->h_n[v];
     }
     CK(cudaMemcpyAsync(S.mem + lo, mbuf.data(), 8 * mbuf.size(), cudaMemcpyHostToDevice, st));
+    CK(cudaMemsetAsync(b->S.codedirty + first, 1, count, st));   // restored M may differ from the program
   }
   CK(cudaStreamSynchronize(st));
   return RASP_OK;
@@ -684,9 +761,129 @@ int rasp_read_stats(rasp_batch* b, rasp_stats* out) {
   return RASP_OK;
 }
 
+}  // extern "C"
+
+namespace {
+
+void drop_graphs(rasp_batch* b) {
+  for (auto& e : b->graphs) cudaGraphExecDestroy(e.second);
+  b->graphs.clear();
+}
+
+int replan(rasp_batch* b) {
+  plan_buckets(b);
+  build_groups(b);
+  drop_graphs(b);
+  return b->inputs_loaded ? order_ids(b) : RASP_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int rasp_autotune(rasp_batch* b, uint64_t max_steps, uint32_t reps) {
+  if (!b) return fail(RASP_EINVAL, "batch is NULL");
+  if (!b->programs_loaded || !b->inputs_loaded) return fail(RASP_ESTATE, "load programs and inputs before tuning");
+  if (reps == 0) reps = 1;
+  int rc = check_device_error(b);
+  if (rc) return rc;
+  cudaStream_t st = b->stream;
+  const Layout& L = b->L;
+  // mutable state: i, a, steps | status, uhead, ylen | M | y | counters
+  const size_t spans[][2] = {{L.off_i, L.off_cap}, {L.off_status, L.off_n}, {L.off_mem, L.off_prog},
+                             {L.off_y, L.off_ids}, {L.off_hist, L.off_stats}, {L.off_dirty, L.off_dirty + b->V}};
+  const bool dirty_valid0 = b->dirty_valid;
+  size_t total = 0;
+  for (auto& sp : spans) total += sp[1] - sp[0];
+  char* snap = nullptr;
+  if (cudaMalloc(&snap, total) != cudaSuccess) {
+    cudaGetLastError();
+    return fail(RASP_ENOMEM, "autotune needs %llu bytes for a snapshot of the state", (unsigned long long)total);
+  }
+  auto copy_state = [&](bool save) -> cudaError_t {
+    size_t o = 0;
+    for (auto& sp : spans) {
+      const size_t len = sp[1] - sp[0];
+      cudaError_t e = save ? cudaMemcpyAsync(snap + o, b->base + sp[0], len, cudaMemcpyDeviceToDevice, st)
+                           : cudaMemcpyAsync(b->base + sp[0], snap + o, len, cudaMemcpyDeviceToDevice, st);
+      if (e != cudaSuccess) return e;
+      o += len;
+    }
+    return cudaSuccess;
+  };
+  struct Cand { const char* name; uint32_t sched, epoch, warps; };
+  static const Cand cands[] = {
+      {"persist_gl e128 w4", RASP_SCHED_PERSIST_GL, 128, 4}, {"persist_gl e64 w4", RASP_SCHED_PERSIST_GL, 64, 4},
+      {"persist_gl e256 w4", RASP_SCHED_PERSIST_GL, 256, 4}, {"persist_gl e128 w2", RASP_SCHED_PERSIST_GL, 128, 2},
+      {"plain", RASP_SCHED_PLAIN, 0, 0},                     {"persist_smem e32 w1", RASP_SCHED_PERSIST, 32, 1},
+      {"shared", RASP_SCHED_SHARED, 0, 0}};
+  // the shared-program schedule is a candidate only when programs are shared
+  const int ncand = (int)(sizeof(cands) / sizeof(cands[0])) - (b->shared_programs ? 0 : 1);
+  const rasp_config saved = b->cfg;
+  cudaEvent_t e0, e1;
+  cudaEventCreate(&e0);
+  cudaEventCreate(&e1);
+  float best = 1e30f;
+  int best_k = -1;
+  std::string rep = "{\"budget\": " + std::to_string(max_steps) + ", \"trials\": [";
+  cudaError_t ce = copy_state(true);
+  for (int k = 0; ce == cudaSuccess && k < ncand; ++k) {
+    b->cfg.flags = (saved.flags & ~RASP_SCHED_MASK) | cands[k].sched;
+    b->cfg.epoch = cands[k].epoch;
+    b->cfg.warps_per_cta = cands[k].warps;
+    rc = replan(b);
+    if (rc) break;
+    float tmin = 1e30f;
+    for (uint32_t r = 0; r < reps && ce == cudaSuccess; ++r) {
+      ce = copy_state(false);
+      b->dirty_valid = dirty_valid0;
+      if (ce != cudaSuccess) break;
+      cudaEventRecord(e0, st);
+      rc = enqueue_run(b, st, max_steps);
+      if (rc) break;
+      cudaEventRecord(e1, st);
+      ce = cudaEventSynchronize(e1);
+      float ms = 0;
+      cudaEventElapsedTime(&ms, e0, e1);
+      tmin = std::min(tmin, ms);
+    }
+    if (rc || ce != cudaSuccess) break;
+    char tmp[128];
+    snprintf(tmp, sizeof(tmp), "%s{\"schedule\": \"%s\", \"ms\": %.4f}", k ? ", " : "", cands[k].name, tmin);
+    rep += tmp;
+    if (tmin < best) {
+      best = tmin;
+      best_k = k;
+    }
+  }
+  // leave the state as it was and adopt the fastest plan
+  const cudaError_t ce2 = copy_state(false);
+  b->dirty_valid = dirty_valid0;
+  cudaStreamSynchronize(st);
+  cudaFree(snap);
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  b->cfg = saved;
+  if (best_k >= 0) {
+    b->cfg.flags = (saved.flags & ~RASP_SCHED_MASK) | cands[best_k].sched;
+    b->cfg.epoch = cands[best_k].epoch;
+    b->cfg.warps_per_cta = cands[best_k].warps;
+  }
+  const int rc2 = replan(b);
+  if (rc) return rc;
+  if (rc2) return rc2;
+  if (ce != cudaSuccess || ce2 != cudaSuccess)
+    return fail(RASP_ECUDA, "autotune: %s", cudaGetErrorString(ce != cudaSuccess ? ce : ce2));
+  rep += "], \"chosen\": \"";
+  rep += best_k >= 0 ? cands[best_k].name : "none";
+  rep += "\"}";
+  b->tuned = rep;
+  return check_device_error(b);
+}
+
 int rasp_describe(const rasp_batch* b, char* buf, uint64_t size) {
   if (!b || !buf || size == 0) return fail(RASP_EINVAL, "batch or buffer is NULL");
-  static const char* names[] = {"auto", "plain", "persist", "persist_gl"};
+  static const char* names[] = {"auto", "plain", "persist", "persist_gl", "shared"};
   std::string s = "{\"vms\": " + std::to_string(b->V) + ", \"buckets\": [";
   bool first = true;
   for (const Bucket& k : b->buckets) {
@@ -695,7 +892,7 @@ int rasp_describe(const rasp_batch* b, char* buf, uint64_t size) {
     snprintf(tmp, sizeof(tmp),
              "%s{\"n_max\": %u, \"vms\": %u, \"schedule\": \"%s\", \"grid\": %u, \"warps_per_cta\": %u, "
              "\"ctas_per_sm\": %u, \"smem\": %zu, \"epoch\": %u, \"refill_min\": %u}",
-             first ? "" : ", ", k.ncap, k.count, names[(k.sched >> 4) & 3], k.shape.grid, k.shape.warps,
+             first ? "" : ", ", k.ncap, k.count, names[std::min<uint32_t>(k.sched >> 4, 4u)], k.shape.grid, k.shape.warps,
              k.shape.ctas_per_sm, k.shape.smem, k.shape.epoch, k.shape.refill_min);
     s += tmp;
     first = false;
@@ -705,12 +902,15 @@ int rasp_describe(const rasp_batch* b, char* buf, uint64_t size) {
   for (const Group& g : b->groups) {
     char tmp[256];
     snprintf(tmp, sizeof(tmp), "%s{\"vms\": %u, \"schedule\": \"%s\", \"grid\": %u}", first ? "" : ", ",
-             g.count, names[(g.sched >> 4) & 3], g.shape.grid);
+             g.count, names[std::min<uint32_t>(g.sched >> 4, 4u)], g.shape.grid);
     s += tmp;
     first = false;
   }
   s += "], \"cuda_graph\": ";
-  s += b->cap_stream ? "true}" : "false}";
+  s += b->cap_stream ? "true" : "false";
+  s += ", \"autotune\": ";
+  s += b->tuned.empty() ? "null" : b->tuned;
+  s += "}";
   if (s.size() + 1 > size) return fail(RASP_EINVAL, "buffer of %llu bytes is too small", (unsigned long long)size);
   memcpy(buf, s.c_str(), s.size() + 1);
   return RASP_OK;

@@ -22,7 +22,7 @@ enum : uint32_t {
   CONT = 0xFFu  // step applied, machine continues
 };
 
-enum : int { ERR_NONE = 0, ERR_WAIT_TIMEOUT = 1 };
+enum : int { ERR_NONE = 0, ERR_WAIT_TIMEOUT = 1, ERR_SLOT = 2 };
 
 // Structure-of-arrays state store in HBM (one entry per VM).
 struct DevState {
@@ -38,6 +38,7 @@ struct DevState {
   uint64_t* mem;              // M slabs
   const uint64_t* tape;       // u_1..u_l, stride ellp words per VM
   uint64_t* y;                // y_1..y_s, stride sp words per VM
+  uint8_t* codedirty;         // 1 if the VM may have written into its program words (NULL: untracked)
 };
 
 struct Params {
@@ -75,6 +76,7 @@ struct Regs {
   uint32_t u0, y0;
   ulonglong2 cur;             // <M[ip], M[ip+1]> when `have`: the next instruction, already loaded
   bool have;
+  bool clean;                 // shared-program mode: no write has touched M[0, plen) yet
 };
 
 __device__ __forceinline__ uint64_t i_of(const Regs& r) { return r.ibase + (uint64_t)r.ip; }
@@ -249,9 +251,10 @@ __device__ __forceinline__ void count_step(Hist& h, uint32_t op, bool taken) {
 // One transition, general form: every case of the Sec. 2.1 equation,
 // every guard and every wrap. Returns CONT after applying it, else the final
 // status (see decode).
-template <bool MASKED, bool CHECKED, bool HIST>
+template <bool MASKED, bool CHECKED, bool HIST, bool SHARED = false>
 __device__ __forceinline__ uint32_t step_general(uint64_t* __restrict__ M, const uint64_t* __restrict__ T,
-                                                 uint64_t* __restrict__ Y, const Params& P, Regs& r, Hist& h) {
+                                                 uint64_t* __restrict__ Y, const Params& P, Regs& r, Hist& h,
+                                                 uint32_t plen = 0) {
   Decoded d;
   const uint32_t s = decode<MASKED, CHECKED>(M, P, r, d);
   if (s != CONT) return s;
@@ -270,6 +273,7 @@ __device__ __forceinline__ uint32_t step_general(uint64_t* __restrict__ M, const
   na = (op == 3u) ? prod : na;
   if (MASKED) na &= P.wmask;
   if (op == 4u) M[jm] = a;                       // M_{j mod n} <- a
+  if (SHARED && ((op == 4u) | (op == 6u)) && jm < plen) r.clean = false;
   if (op >= 6u) {
     if (op == 6u) {                              // M_{j mod n} <- u-bullet; u-triangle
       M[jm] = T[r.u0];
@@ -306,9 +310,10 @@ __device__ __forceinline__ uint32_t step_general(uint64_t* __restrict__ M, const
 // instruction of a taken BNZ. A step then waits on one memory latency
 // instead of two in a row, at the price of more registers and loads. A
 // STO/RD that writes the prefetched pair invalidates it.
-template <bool MASKED, bool CHECKED, bool HIST, bool PIPE>
+template <bool MASKED, bool CHECKED, bool HIST, bool PIPE, bool SHARED = false>
 __device__ __forceinline__ uint32_t one_step(uint64_t* __restrict__ M, const uint64_t* __restrict__ T,
-                                             uint64_t* __restrict__ Y, const Params& P, Regs& r, Hist& h) {
+                                             uint64_t* __restrict__ Y, const Params& P, Regs& r, Hist& h,
+                                             const uint64_t* Pg = nullptr, uint32_t plen = 0) {
   const uint32_t ip = r.ip, n = r.n;
   const uint32_t ilim = MASKED ? r.ilim : n;
   // i = ip < n even with ip + 1 < n: i != 2^w - 1 and M[ip], M[ip+1] is one
@@ -319,7 +324,11 @@ __device__ __forceinline__ uint32_t one_step(uint64_t* __restrict__ M, const uin
     r.have = true;
   }
   if (aligned) {
-    const ulonglong2 oj = PIPE ? r.cur : *reinterpret_cast<const ulonglong2*>(M + ip);
+    // shared-program mode: while the VM has not written into M[0, plen), its
+    // code words equal the program, so they are fetched from the one copy
+    // of the program in shared memory
+    const uint64_t* F = (SHARED && r.clean && ip + 1u < plen) ? Pg : M;
+    const ulonglong2 oj = PIPE ? r.cur : *reinterpret_cast<const ulonglong2*>(F + ip);
     const uint64_t o = oj.x, j = oj.y, a = r.a;
     const uint32_t op = (uint32_t)o, jm = (uint32_t)j;
     const bool valid = (o - 1ull) < 7ull;
@@ -358,6 +367,7 @@ __device__ __forceinline__ uint32_t one_step(uint64_t* __restrict__ M, const uin
       uint64_t w = a;                            // STO writes a, RD writes u-bullet
       if (rd) w = T[r.u0];
       if (wr) M[jm] = w;
+      if (SHARED) r.clean = r.clean & !(wr & (jm < plen));
       const bool put = pri & (r.y0 < P.s);       // y :: M_{j mod n}
       if (put) Y[r.y0] = v;
       r.u0 += rd ? 1u : 0u;
@@ -378,7 +388,7 @@ __device__ __forceinline__ uint32_t one_step(uint64_t* __restrict__ M, const uin
     }
   }
   if (PIPE) r.have = false;
-  return step_general<MASKED, CHECKED, HIST>(M, T, Y, P, r, h);
+  return step_general<MASKED, CHECKED, HIST, SHARED>(M, T, Y, P, r, h, plen);
 }
 
 template <bool HIST>

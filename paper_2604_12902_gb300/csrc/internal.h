@@ -33,6 +33,12 @@ cudaError_t launch_pack(const DevState& S, const uint64_t* prog, const uint64_t*
                         const uint32_t* prog_of_vm, uint32_t num_vms, uint64_t wmask, uint32_t sp,
                         cudaStream_t stream);
 
+// Shared-program schedule: one CTA per program (program in shared memory),
+// lanes run the program's VMs pv_ids[pv_off[p] .. pv_off[p+1]).
+cudaError_t launch_shared(const StepVariant& var, const DevState& S, const Params& P, const uint64_t* prog,
+                          const uint64_t* prog_off, const uint32_t* pv_off, const uint32_t* pv_ids,
+                          uint32_t num_programs, uint32_t max_plen, cudaStream_t stream);
+
 // One-time function attributes of the plain kernel (carveout).
 void plain_configure(const StepVariant& var);
 

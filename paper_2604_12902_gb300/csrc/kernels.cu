@@ -62,6 +62,7 @@ __global__ void __launch_bounds__(256) k_pack(DevState S, const uint64_t* __rest
       S.status[v] = ST_RUNNING;
       S.uhead[v] = 0;
       S.ylen[v] = 0;
+      if (S.codedirty) S.codedirty[v] = 0;
     }
   }
 }
@@ -264,6 +265,12 @@ __global__ void __launch_bounds__(256) k_persist(DevState S, Params P, Queue Q, 
           exhausted = true;
         }
       }
+      if (fresh && ((r.n + 1u) & ~1u) > ncap) {
+        // the VM does not fit this bucket's slot: refuse it (flag, not a copy past the slot)
+        atomicExch(P.err, ERR_SLOT);
+        vm = -1;
+        fresh = false;
+      }
       if (fresh) {
         arm_regs(P, r);
         const uint32_t mbytes = ((r.n + 1u) & ~1u) * 8u;
@@ -452,6 +459,70 @@ __global__ void __launch_bounds__(128, 7) k_persist_gl(DevState S, Params P, Que
   flush_hist<HIST>(P, h);
 }
 
+// ------------------------------------------------------------------ shared programs
+// One CTA per program (grid-stride over programs): the program's words sit
+// once in shared memory and the CTA's lanes run that program's VMs, each
+// lane taking the next VM from a shared-memory counter when its VM stops.
+// Instructions are fetched from the shared copy while the VM has not written
+// into its program words (Regs::clean); data lives in the VM's own slab.
+template <bool MASKED, bool CHECKED, bool HIST>
+__global__ void __launch_bounds__(128) k_shared(DevState S, Params P, const uint64_t* __restrict__ prog,
+                                                const uint64_t* __restrict__ prog_off,
+                                                const uint32_t* __restrict__ pv_off,
+                                                const uint32_t* __restrict__ pv_ids, uint32_t num_programs) {
+  extern __shared__ __align__(16) uint64_t ps[];
+  __shared__ uint32_t next;
+  Hist h;
+  h.zero();
+  for (uint32_t p = blockIdx.x; p < num_programs; p += gridDim.x) {
+    const uint64_t po = prog_off[p];
+    const uint32_t plen = (uint32_t)(prog_off[p + 1] - po);
+    for (uint32_t k = threadIdx.x; k < plen; k += blockDim.x) ps[k] = prog[po + k] & P.wmask;
+    if (threadIdx.x == 0) next = 0;
+    __syncthreads();
+    const uint32_t first = pv_off[p], count = pv_off[p + 1] - first;
+    Regs r{};
+    r.n = 1;
+    int32_t vm = -1;
+    uint32_t st = CONT;
+    uint64_t* M = S.mem;
+    const uint64_t* T = S.tape;
+    uint64_t* Y = S.y;
+    bool more = true;
+    for (;;) {
+      if (vm < 0 && more) {
+        const uint32_t idx = atomicAdd(&next, 1u);
+        if (idx < count) {
+          const uint32_t v = pv_ids[first + idx];
+          if (S.status[v] == ST_RUNNING) {
+            load_regs(S, P, v, r);
+            arm_regs(P, r);
+            r.clean = S.codedirty[v] == 0;
+            M = S.mem + S.mem_off[v];
+            T = S.tape + (uint64_t)v * P.ellp;
+            Y = S.y + (uint64_t)v * P.sp;
+            vm = (int32_t)v;
+          }
+        } else {
+          more = false;
+        }
+      }
+      if (vm < 0) {
+        if (!more) break;
+        continue;
+      }
+      st = one_step<MASKED, CHECKED, HIST, false, true>(M, T, Y, P, r, h, ps, plen);
+      if (st != CONT) {
+        store_regs(S, (uint32_t)vm, r, st);
+        if (!r.clean) S.codedirty[vm] = 1;
+        vm = -1;
+      }
+    }
+    __syncthreads();   // every lane done with this program's copy
+  }
+  flush_hist<HIST>(P, h);
+}
+
 // ------------------------------------------------------------------ stats
 __global__ void __launch_bounds__(256) k_stats(DevState S, uint32_t num_vms, unsigned long long* out) {
   unsigned long long steps = 0, c[5] = {0, 0, 0, 0, 0};
@@ -541,6 +612,32 @@ cudaError_t launch_pack(const DevState& S, const uint64_t* prog, const uint64_t*
   const uint32_t cap = (uint32_t)num_sms() * 16u;
   if (blocks > cap) blocks = cap;
   k_pack<<<blocks, 256, 0, stream>>>(S, prog, prog_off, prog_of_vm, num_vms, wmask, sp);
+  return cudaGetLastError();
+}
+
+using SharedFn = void (*)(DevState, Params, const uint64_t*, const uint64_t*, const uint32_t*, const uint32_t*,
+                         uint32_t);
+
+SharedFn pick_shared(const StepVariant& v) {
+  if (v.checked) return v.hist ? k_shared<false, true, true> : k_shared<false, true, false>;
+  if (v.masked) return v.hist ? k_shared<true, false, true> : k_shared<true, false, false>;
+  return v.hist ? k_shared<false, false, true> : k_shared<false, false, false>;
+}
+
+cudaError_t launch_shared(const StepVariant& var, const DevState& S, const Params& P, const uint64_t* prog,
+                          const uint64_t* prog_off, const uint32_t* pv_off, const uint32_t* pv_ids,
+                          uint32_t num_programs, uint32_t max_plen, cudaStream_t stream) {
+  if (!num_programs) return cudaSuccess;
+  const size_t smem = (size_t)((max_plen + 1u) & ~1u) * 8u;
+  SharedFn fn = pick_shared(var);
+  if (smem > 48u * 1024u) {
+    if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
+      return cudaGetLastError();
+  }
+  uint32_t grid = num_programs;
+  const uint32_t cap = (uint32_t)num_sms() * 64u;
+  if (grid > cap) grid = cap;
+  fn<<<grid, 128, smem, stream>>>(S, P, prog, prog_off, pv_off, pv_ids, num_programs);
   return cudaGetLastError();
 }
 

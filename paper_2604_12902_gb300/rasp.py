@@ -61,7 +61,8 @@ class RaspError(RuntimeError):
 _lib = None
 EXPORTS = ["rasp_batch_bytes", "rasp_batch_create", "rasp_load_programs", "rasp_load_inputs",
            "rasp_reset", "rasp_run", "rasp_sync", "rasp_read_state", "rasp_load_state",
-           "rasp_read_stats", "rasp_describe", "rasp_batch_destroy", "rasp_last_error", "rasp_version"]
+           "rasp_read_stats", "rasp_describe", "rasp_autotune", "rasp_batch_destroy", "rasp_last_error",
+           "rasp_version"]
 
 
 def lib():
@@ -84,11 +85,12 @@ def lib():
         L.rasp_load_state.argtypes = [P, U64, U64, ctypes.POINTER(rasp_state_view)]
         L.rasp_read_stats.argtypes = [P, ctypes.POINTER(rasp_stats)]
         L.rasp_describe.argtypes = [P, ctypes.c_char_p, U64]
+        L.rasp_autotune.argtypes = [P, U64, U32]
         L.rasp_batch_destroy.argtypes = [P]
         L.rasp_batch_destroy.restype = None
         L.rasp_last_error.restype = ctypes.c_char_p
         L.rasp_version.restype = ctypes.c_char_p
-        for name in EXPORTS[:11]:
+        for name in EXPORTS[:12]:
             getattr(L, name).restype = I
         _lib = L
     return _lib
@@ -168,6 +170,10 @@ def rasp_describe(h) -> dict:
     buf = ctypes.create_string_buffer(1 << 14)
     _check(lib().rasp_describe(h, buf, len(buf)))
     return json.loads(buf.value.decode())
+
+
+def rasp_autotune(h, max_steps: int = U64_MAX, reps: int = 2):
+    _check(lib().rasp_autotune(h, int(max_steps) & U64_MAX, reps))
 
 
 def rasp_batch_destroy(h):
@@ -270,6 +276,12 @@ class Batch:
 
     def describe(self) -> dict:
         return rasp_describe(self.h)
+
+    def autotune(self, max_steps: int = U64_MAX, reps: int = 2) -> dict:
+        """Time the candidate schedules on this batch (state unchanged) and
+        keep the fastest; returns the trial report."""
+        rasp_autotune(self.h, max_steps, reps)
+        return self.describe()["autotune"]
 
     def close(self):
         if getattr(self, "h", None):

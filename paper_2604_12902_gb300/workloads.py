@@ -469,3 +469,24 @@ def _uneven_chunk(ids, seed, len_lo, len_hi, n_lo, n_hi, cap_lo, cap_hi, p_nonha
     words[0::2] = op
     words[1::2] = arg
     return words, I, n, cap
+
+
+# ---------------------------------------------------------------------------
+# Shared-program rollout: P candidate programs (length 48, the loop templates
+# above with at most two loops) each run on R input tapes of 8 ints uniform
+# in [-50, 50]; memory = 96 program words + 128 private data words (n = 224);
+# step cap 2048. VM v runs program v // R.
+# ---------------------------------------------------------------------------
+def shared_programs(num_programs: int = 16384, vms_per_program: int = 256, seed: int = 4,
+                    instructions: int = 48, data_words: int = 128, tape_len: int = 8,
+                    tape_lo: int = -50, tape_hi: int = 50, cap: int = 2048, s: int = 8) -> Workload:
+    n = 2 * instructions + data_words
+    base = template_programs(num_vms=num_programs, seed=seed, instructions=instructions, mem_words=n,
+                             tape_len=tape_len, loops_hi=2)
+    V = num_programs * vms_per_program
+    ids = np.arange(V, dtype=np.uint64)
+    tape = uniform_int(draws(seed, 9, ids, tape_len), tape_lo, tape_hi)
+    return Workload("shared", base.programs, base.prog_off, np.full(V, n, np.uint32), tape.reshape(-1),
+                    _regular_offsets(V, tape_len), np.full(V, cap, np.uint64), ell=tape_len, s=s,
+                    prog_of_vm=np.repeat(np.arange(num_programs, dtype=np.uint32), vms_per_program),
+                    meta=dict(seed=seed, programs=num_programs, vms_per_program=vms_per_program))

@@ -1,0 +1,108 @@
+"""Shared-program schedule: one program in shared memory per CTA, many VMs
+(inputs) per program, copy-on-write when a VM writes into its program words
+(needs a GPU)."""
+import os
+
+import numpy as np
+import pytest
+
+from paper_2604_12902_gb300 import workloads as W
+from tests.helpers import assert_same_state, oracle_state
+
+pytestmark = pytest.mark.gpu
+THREADS = os.cpu_count() or 1
+SHARED = 0x40
+
+
+@pytest.fixture(scope="module")
+def rasp():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2604_12902_gb300 import rasp as R
+    R.lib()
+    return R
+
+
+def run(R, wl, flags, budgets=(None,)):
+    with R.Batch(wl.mem_words, wl.ell, wl.s, word_bits=wl.w, flags=flags) as b:
+        b.load_workload(wl)
+        for t in budgets:
+            b.run() if t is None else b.run(t)
+        return b.read_state(), b.stats()
+
+
+def self_modifying_shared(P=300, R=40, seed=8):
+    """Random 32-instruction programs filling a 64-word memory (STO and RD
+    land on code often), shared by R VMs each."""
+    base = W.random_programs(num_vms=P, seed=seed)
+    V = P * R
+    ids = np.arange(V, dtype=np.uint64)
+    tape = W.uniform_int(W.draws(seed, 9, ids, 4), -100, 100).reshape(-1)
+    return W.Workload("selfmod-shared", base.programs, base.prog_off, np.full(V, 64, np.uint32), tape,
+                      np.arange(V + 1, dtype=np.uint64) * 4, np.full(V, 256, np.uint64), 4, 8,
+                      prog_of_vm=np.repeat(np.arange(P, dtype=np.uint32), R))
+
+
+def test_shared_templates_every_vm(rasp):
+    wl = W.shared_programs(num_programs=512, vms_per_program=64)
+    st, _ = oracle_state(wl, threads=THREADS)
+    got, stats = run(rasp, wl, SHARED)
+    assert_same_state(got, st, wl.ell, wl.s, what="shared templates")
+    assert stats["halted"] == wl.num_vms
+
+
+def test_shared_self_modifying_code(rasp):
+    wl = self_modifying_shared()
+    st, _ = oracle_state(wl, threads=THREADS)
+    got, _ = run(rasp, wl, SHARED)
+    assert_same_state(got, st, wl.ell, wl.s, what="shared self-modifying")
+    part, _ = oracle_state(wl, budget=37, threads=THREADS)
+    got, _ = run(rasp, wl, SHARED, budgets=(37,))
+    assert_same_state(got, part, wl.ell, wl.s, what="shared self-modifying, budget 37")
+    got, _ = run(rasp, wl, SHARED, budgets=(5, 37, 90, None))
+    assert_same_state(got, st, wl.ell, wl.s, what="shared self-modifying, resumed")
+
+
+def test_shared_after_other_schedule_and_autotune(rasp):
+    wl = self_modifying_shared(P=100, R=20, seed=9)
+    st, _ = oracle_state(wl, threads=THREADS)
+    with rasp.Batch(wl.mem_words, wl.ell, wl.s, flags=0x30) as b:       # persistent, then shared
+        b.load_workload(wl)
+        b.run(20)
+        before = b.read_state()
+        rep = b.autotune(reps=1)
+        assert "shared" in [t["schedule"] for t in rep["trials"]]
+        after = b.read_state()
+        for k in before:
+            assert np.array_equal(before[k], after[k]), k
+        b.run()
+        got = b.read_state()
+    assert_same_state(got, st, wl.ell, wl.s, what="after autotune (%s)" % rep["chosen"])
+
+
+def test_shared_masked_word_size(rasp):
+    wl = W.shared_programs(num_programs=64, vms_per_program=32, seed=6)
+    wl.w = 16
+    st, _ = oracle_state(wl)
+    got, _ = run(rasp, wl, SHARED)
+    assert_same_state(got, st, wl.ell, wl.s, what="shared w=16")
+
+
+def test_shared_full_size_sampled(rasp):
+    """16,384 programs x 256 tapes = 4,194,304 VMs; every VM halts; 2,000
+    sampled VMs compared with the oracle."""
+    wl = W.shared_programs()
+    with rasp.Batch(wl.mem_words, wl.ell, wl.s, flags=SHARED) as b:
+        b.load_workload(wl)
+        b.run()
+        got = b.read_state(mem=False)
+        stats = b.stats()
+        ids = np.sort(np.random.default_rng(44).choice(wl.num_vms, size=2000, replace=False))
+        mems = [b.read_state(first=int(v), count=1)["mem"] for v in ids]
+    assert stats["halted"] == wl.num_vms
+    sub = wl.subset(ids)
+    st, _ = oracle_state(sub, threads=THREADS)
+    sel = {k: got[k][ids] for k in ("i", "a", "steps", "status", "uhead", "ylen", "y")}
+    sel["mem"] = np.concatenate(mems)
+    assert_same_state(sel, st, wl.ell, wl.s, what="shared full-size sample")

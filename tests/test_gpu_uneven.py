@@ -96,3 +96,22 @@ def test_uneven_full_size_sampled(rasp):
     sel = {k: got[k][ids] for k in ("i", "a", "steps", "status", "uhead", "ylen", "y")}
     sel["mem"] = np.concatenate(mems)
     assert_same_state(sel, st, wl.ell, wl.s, what="uneven full-size sample")
+
+
+def test_autotune_leaves_state_and_keeps_parity(rasp, uneven64k):
+    wl, st = uneven64k
+    with rasp.Batch(wl.mem_words, wl.ell, wl.s) as b:
+        b.load_workload(wl)
+        b.run(50)
+        before = b.read_state()
+        rep = b.autotune(reps=1)
+        after = b.read_state()
+        for k in before:
+            assert np.array_equal(before[k], after[k]), k
+        assert len(rep["trials"]) == 6          # no shared candidate: programs not shared
+        assert rep["chosen"] in [t["schedule"] for t in rep["trials"]]
+        best = min(rep["trials"], key=lambda t: t["ms"])
+        assert rep["chosen"] == best["schedule"]
+        b.run()
+        got = b.read_state()
+    assert_same_state(got, st, wl.ell, wl.s, what="after autotune (%s)" % rep["chosen"])

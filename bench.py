@@ -121,6 +121,10 @@ def make_workload(name: str, rank: int, vms: int = 1 << 20):
                                first_vm=rank * (1 << 22), workers=os.cpu_count() or 1)
         return wl, ("%s uneven programs (length log-U[8,512], n log-U[16,4096], cap log-U[64,65536], "
                     "~30%% non-halting), l=16, s=8" % format(wl.num_vms, ","))
+    if name == "shared":
+        wl = W.shared_programs()
+        return wl, ("16,384 programs (48 instr, loop templates) x 256 tapes of 8 ints U[-50,50] = 4,194,304 VMs, "
+                    "n = 96 program + 128 data words, cap 2048")
     if name == "random":
         return W.random_programs(num_vms=1024, seed=1, first_vm=rank * 1024), \
             "1,024 random programs (32 instr, opcodes U{1..7}, operands U[0,63]), n=64, l=4, s=8, cap 256"
@@ -188,7 +192,7 @@ def main():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
-    ap.add_argument("--workload", default="templates", choices=["templates", "uneven", "random"])
+    ap.add_argument("--workload", default="templates", choices=["templates", "uneven", "shared", "random"])
     ap.add_argument("--flags", type=lambda x: int(x, 0), default=0, help="rasp_config.flags (schedule)")
     ap.add_argument("--epoch", type=int, default=0)
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU-oracle baseline")
@@ -308,18 +312,19 @@ def main():
     if not args.no_e2e:
         pin = lambda a: _pinned_copy(torch, a)
         h_prog, h_poff = pin(wl.programs), pin(wl.prog_off)
+        h_pvm = pin(wl.prog_of_vm) if wl.prog_of_vm is not None else None
         h_tape, h_toff, h_caps = pin(wl.tapes), pin(wl.tape_off), pin(wl.caps)
         out = {k: pin(np.empty(wl.num_vms, dt)) for k, dt in
                (("i", np.int64), ("a", np.int64), ("steps", np.uint64), ("status", np.uint8),
                 ("uhead", np.uint32), ("ylen", np.uint32))}
         out["y"] = pin(np.empty(wl.num_vms * wl.s, np.int64))
-        h2d = sum(x.nbytes for x in (h_prog, h_poff, h_tape, h_toff, h_caps))
+        h2d = sum(x.nbytes for x in (h_prog, h_poff, h_tape, h_toff, h_caps) + ((h_pvm,) if h_pvm is not None else ()))
         d2h = sum(x.nbytes for x in out.values())
         view = R.rasp_state_view(*(R._p(out[k]) for k in ("i", "a", "steps", "status", "uhead", "ylen", "y")),
                                  None, 0)
 
         def e2e_step():
-            R.rasp_load_programs(b.h, h_prog, h_poff)
+            R.rasp_load_programs(b.h, h_prog, h_poff, h_pvm)
             R.rasp_load_inputs(b.h, h_tape, h_toff, h_caps)
             R.rasp_run(b.h)
             R.rasp_read_state(b.h, 0, wl.num_vms, view)

@@ -264,6 +264,53 @@ typedef struct rasp_static_run {
 
 int rasp_run_static(const rasp_static_run* run);
 
+/* ---- serving: continuous batching of rollout requests --------------------
+ * (The paper evaluates fixed batches only; this is the request loop around
+ * the same machine.) A pool owns one device arena of `arena_bytes`. Each
+ * submitted request is a batch of its own (programs, tapes, caps, memory
+ * sizes; all VMs of the pool share cfg's w, semantics, l, s and schedule).
+ * A request is admitted as soon as a first-fit block of the arena can hold
+ * its batch (rasp_batch_bytes), otherwise it waits first-in-first-out.
+ * Admitted requests run on their own streams, concurrently with the ones
+ * already on the device. rasp_pool_read copies a finished request's state out
+ * and frees its block, which admits waiting requests. The pool's calls are
+ * serialised by an internal mutex; errors are reported by
+ * rasp_pool_last_error (thread-local). */
+typedef struct rasp_pool rasp_pool;
+
+enum rasp_request_state { RASP_REQ_QUEUED = 0, RASP_REQ_RUNNING = 1, RASP_REQ_DONE = 2 };
+
+typedef struct rasp_request {
+    const int64_t*  words;        /* program words, as for rasp_load_programs      */
+    const uint64_t* offsets;      /* [num_programs + 1]                            */
+    uint64_t        num_programs;
+    const uint32_t* prog_of_vm;   /* NULL or [num_vms]                             */
+    const int64_t*  tape;         /* inputs, as for rasp_load_inputs               */
+    const uint64_t* tape_off;     /* [num_vms + 1]                                 */
+    const uint64_t* caps;         /* NULL or [num_vms]                             */
+    const uint32_t* mem_words;    /* [num_vms]                                     */
+    uint64_t        num_vms;
+    uint64_t        max_steps;    /* budget of the request's single rasp_run       */
+} rasp_request;
+
+/* EINVAL if cfg->arena is set (the pool owns its arena); ENOMEM if the arena
+ * cannot be allocated. */
+int rasp_pool_create(const rasp_config* cfg, uint64_t arena_bytes, rasp_pool** out);
+/* Copies the request's inputs (host memory), queues it and admits what fits.
+ * EINVAL for a malformed request, ENOMEM if it could never fit the arena.
+ * Load errors found at admission are reported by rasp_pool_read. */
+int rasp_pool_submit(rasp_pool* p, const rasp_request* req, uint64_t* ticket);
+/* Non-blocking: *state = enum rasp_request_state; also admits waiting work. */
+int rasp_pool_poll(rasp_pool* p, uint64_t ticket, int* state);
+/* Copy out a RUNNING or DONE request's final state (waits for it; out may be
+ * NULL to discard), free its memory and forget the ticket. ESTATE while
+ * still QUEUED. */
+int rasp_pool_read(rasp_pool* p, uint64_t ticket, rasp_state_view* out);
+/* Bytes of the arena in use, requests waiting, requests running. */
+int rasp_pool_info(rasp_pool* p, uint64_t* in_use, uint64_t* waiting, uint64_t* running);
+void rasp_pool_destroy(rasp_pool* p);
+const char* rasp_pool_last_error(void);
+
 /* Free the batch (synchronises its stream first). NULL is a no-op. */
 void rasp_batch_destroy(rasp_batch* b);
 

@@ -1,0 +1,104 @@
+"""Serving: continuous batching of rollout requests in one device arena
+(needs a GPU). A request's result must not depend on what else is running."""
+import os
+
+import numpy as np
+import pytest
+
+from paper_2604_12902_gb300 import workloads as W
+from tests.helpers import assert_same_state, oracle_state
+
+pytestmark = pytest.mark.gpu
+THREADS = os.cpu_count() or 1
+
+
+@pytest.fixture(scope="module")
+def serving():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2604_12902_gb300 import rasp as R, serving as S
+    R.lib()
+    return R, S
+
+
+def request(size, k, seed=5):
+    """A rollout request shaped like the uneven batch (sizes as in config 3)."""
+    return W.uneven_programs(num_vms=size, seed=seed, first_vm=k * 200_000)
+
+
+def wait(pool, t):
+    import time
+    for _ in range(200000):
+        if pool.poll(t) == 2:
+            return
+        time.sleep(1e-4)
+    raise AssertionError("request did not finish")
+
+
+def test_request_same_alone_and_in_the_mix(serving):
+    R, S = serving
+    reqs = [request(n, k) for k, n in enumerate([3000, 20000, 1000, 7000, 12000])]
+    A = reqs[0]
+    with S.Pool(8 << 30, A.ell, A.s) as pool:
+        t = pool.submit(A)
+        wait(pool, t)
+        alone = pool.read(t, mem=True)
+        tickets = [pool.submit(r) for r in reqs[1:3]] + [pool.submit(A)] + [pool.submit(r) for r in reqs[3:]]
+        res = {}
+        for tk in tickets:
+            wait(pool, tk)
+        for tk, r in zip(tickets, reqs[1:3] + [A] + reqs[3:]):
+            res[tk] = (r, pool.read(tk, mem=True))
+    mixed = res[tickets[2]][1]
+    for key in alone:
+        assert np.array_equal(alone[key], mixed[key]), key
+    st, _ = oracle_state(A, threads=THREADS)
+    assert_same_state(alone, st, A.ell, A.s, what="request alone")
+    r4, got4 = res[tickets[-1]]
+    st4, _ = oracle_state(r4, threads=THREADS)
+    assert_same_state(got4, st4, r4.ell, r4.s, what="request in the mix")
+
+
+def test_admission_waits_for_memory(serving):
+    R, S = serving
+    reqs = [request(20000, k, seed=6) for k in range(5)]
+    one = max(R.rasp_batch_bytes(R.rasp_config(64, 0, 16, 8, 0, 0, 0, 0, 0, 0, None, None, 0), r.mem_words)
+              for r in reqs)
+    with S.Pool(int(one * 2.2), reqs[0].ell, reqs[0].s) as pool:
+        tickets = [pool.submit(r) for r in reqs]
+        info = pool.info()
+        assert info["waiting"] >= 2 and info["running"] <= 2
+        outs = {}
+        pending = list(tickets)
+        while pending:
+            for tk in list(pending):
+                if pool.poll(tk) == 2:
+                    outs[tk] = pool.read(tk)
+                    pending.remove(tk)
+        assert pool.info()["in_use"] == 0
+    for tk, r in zip(tickets, reqs):
+        st, _ = oracle_state(r, threads=THREADS)
+        got = outs[tk]
+        got["mem"] = None
+        assert np.array_equal(got["steps"], st.steps) and np.array_equal(got["status"], st.status)
+
+
+def test_poisson_short_run(serving):
+    R, S = serving
+    rng = np.random.default_rng(7)
+    sizes = W.log_uniform_int(rng.integers(0, 1 << 32, size=12, dtype=np.uint64).astype(np.uint32), 1000, 20000)
+    reqs = [request(int(n), k, seed=7) for k, n in enumerate(sizes)]
+    with S.Pool(16 << 30, reqs[0].ell, reqs[0].s) as pool:
+        out = S.poisson_run(pool, reqs, lam=200.0, duration=0.5, seed=1, keep_results=True)
+    assert out["requests"] >= 40 and out["p50_ms"] > 0 and out["p99_ms"] >= out["p50_ms"]
+    seen = {}
+    for idx, res in out["results"]:
+        if idx not in seen:
+            seen[idx] = res
+        else:
+            for key in res:                                  # every replay of a request gives the same result
+                assert np.array_equal(seen[idx][key], res[key]), key
+    idx, res = out["results"][0]
+    st, _ = oracle_state(reqs[idx], threads=THREADS)
+    assert np.array_equal(res["steps"], st.steps) and np.array_equal(res["i"].view(np.uint64), st.i)

@@ -113,8 +113,10 @@ class ClockSampler:
 
 def make_workload(name: str, rank: int, vms: int = 1 << 20):
     from paper_2604_12902_gb300 import workloads as W
+    from paper_2604_12902_gb300.shards import shard_range
     if name == "templates":
-        return W.template_programs(num_vms=vms, seed=2, first_vm=rank * vms), \
+        first, count = shard_range(rank, vms)
+        return W.template_programs(num_vms=count, seed=2, first_vm=first), \
             "%s template programs (64 instr, 1-3 loops, trips U[1,64]), n=256, l=16, s=8, cap 4096" % format(vms, ",")
     if name == "uneven":
         wl = W.uneven_programs(num_vms=vms if vms != 1 << 20 else 1 << 22, seed=3,
@@ -186,13 +188,52 @@ def run_reference(args, ws, rank):
     print(json.dumps(line), flush=True)
 
 
+def run_serving(args, ws, rank):
+    """Config 5: open-loop Poisson arrivals of rollout requests (each 1k-100k
+    programs drawn like the uneven batch) into one device arena; requests are
+    admitted as memory frees up and run concurrently (continuous batching)."""
+    import torch
+    from paper_2604_12902_gb300 import serving as SV, workloads as W
+    torch.cuda.set_device(0)
+    rng = np.random.default_rng(11)
+    u = rng.integers(0, 1 << 32, size=args.requests, dtype=np.uint64).astype(np.uint32)
+    sizes = W.log_uniform_int(u, 1000, 100000)
+    t0 = time.perf_counter()
+    reqs = [W.uneven_programs(num_vms=int(n), seed=5, first_vm=k * 100_000, workers=os.cpu_count() or 1)
+            for k, n in enumerate(sizes)]
+    gen_s = time.perf_counter() - t0
+    for wl in reqs:     # requests arrive in page-locked host memory (async H2D)
+        for f in ("programs", "prog_off", "tapes", "tape_off", "caps", "mem_words"):
+            setattr(wl, f, _pinned_copy(torch, getattr(wl, f)))
+    free, _ = torch.cuda.mem_get_info()
+    arena = int(min(args.arena_gb * 2 ** 30, free * 0.8))
+    with SV.Pool(arena, reqs[0].ell, reqs[0].s) as pool:
+        SV.poisson_run(pool, reqs[:4], lam=50.0, duration=0.2, seed=0)      # warm-up (untimed)
+        clk = ClockSampler(torch.cuda.current_device())
+        clk.start()
+        out = SV.poisson_run(pool, reqs, lam=args.lam, duration=args.duration, seed=1)
+        clocks = clk.stop()
+    offered = args.lam * float(np.mean([r.num_vms for r in reqs]))
+    line = {"metric": METRIC, "value": out["vm_steps_per_s"], "unit": UNIT, "n_gpus": 1, "steps": out["requests"],
+            "warmup": 1, "ms_per_step": out["wall_s"] * 1e3 / max(out["requests"], 1), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "int64", "data": "synthetic",
+            "config": {"workload": "serving: Poisson arrivals (lambda %.0f/s) for %.0f s of rollout requests, "
+                                   "each log-U[1e3,1e5] programs drawn as the uneven batch, inputs in pinned host "
+                                   "memory; %d distinct requests cycled; arena %.1f GiB" % (args.lam, args.duration, len(reqs), arena / 2 ** 30)},
+            "serving": {"requests_done": out["requests"], "p50_ms": out["p50_ms"], "p99_ms": out["p99_ms"],
+                        "wall_s": out["wall_s"], "vm_steps": out["vm_steps"], "mean_vms_per_request": out["mean_vms"],
+                        "offered_vms_per_s": offered, "request_gen_s": gen_s},
+            "clocks": clocks}
+    print(json.dumps(line), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
-    ap.add_argument("--workload", default="templates", choices=["templates", "uneven", "shared", "random"])
+    ap.add_argument("--workload", default="templates", choices=["templates", "uneven", "shared", "random", "serving"])
     ap.add_argument("--flags", type=lambda x: int(x, 0), default=0, help="rasp_config.flags (schedule)")
     ap.add_argument("--epoch", type=int, default=0)
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU-oracle baseline")
@@ -201,10 +242,18 @@ def main():
     ap.add_argument("--no-tune", action="store_true", help="skip the (untimed) schedule autotuning")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--vms", type=int, default=1 << 20, help="template programs per GPU (profiling cases)")
+    ap.add_argument("--lam", type=float, default=200.0, help="serving: arrival rate (requests/s)")
+    ap.add_argument("--duration", type=float, default=60.0, help="serving: seconds of arrivals")
+    ap.add_argument("--requests", type=int, default=64, help="serving: distinct requests (cycled)")
+    ap.add_argument("--arena-gb", type=float, default=64.0, help="serving: device arena size")
     args = ap.parse_args()
     ws, rank, local = dist_env()
     if args.impl == "reference":
         run_reference(args, ws, rank)
+        return
+    if args.workload == "serving":
+        if rank == 0:
+            run_serving(args, ws, rank)
         return
     if args.warmup < 3:
         args.warmup = 3
@@ -215,6 +264,7 @@ def main():
         import torch.distributed as dist
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
     from paper_2604_12902_gb300 import rasp as R
+    from paper_2604_12902_gb300.shards import combine
 
     wl, desc = make_workload(args.workload, rank, args.vms)
     stream = torch.cuda.current_stream()
@@ -271,13 +321,9 @@ def main():
     m_bytes = float(wl.mem_words.astype(np.uint64).sum()) * 8.0
     assert st["vm_steps"] == total_steps, "timed runs disagree with the counting run"
 
-    ms_total = torch.tensor([elapsed_ms], device="cuda")
-    steps_total = torch.tensor([float(total_steps)], device="cuda", dtype=torch.float64)
-    if dist:
-        dist.all_reduce(ms_total, op=dist.ReduceOp.MAX)
-        dist.all_reduce(steps_total, op=dist.ReduceOp.SUM)
-    ms_per_step = float(ms_total.item()) / args.steps
-    value = float(steps_total.item()) / (ms_per_step * 1e-3)
+    ms_total, steps_total = combine(dist, elapsed_ms, total_steps, device="cuda")
+    ms_per_step = ms_total / args.steps
+    value = steps_total / (ms_per_step * 1e-3)
 
     hbm, peak_kind = peaks()
     run_avg = float(np.mean(run_ms))
@@ -341,9 +387,8 @@ def main():
         assert int(out["steps"].sum()) == total_steps
         e2e_val = total_steps / dt
         if dist:
-            t = torch.tensor([dt], device="cuda")
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            e2e_val = float(steps_total.item()) / float(t.item())
+            t_max, _ = combine(dist, dt, total_steps, device="cuda")
+            e2e_val = steps_total / t_max
         e2e = {"value": e2e_val, "unit": UNIT, "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h),
                "ms_per_step": dt * 1e3}
 

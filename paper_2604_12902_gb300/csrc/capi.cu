@@ -109,6 +109,7 @@ struct rasp_batch {
   uint32_t num_programs = 0;
   uint32_t max_plen = 0;
   bool dirty_valid = false;    // codedirty is up to date (only the shared kernel tracks it)
+  bool ids_uploaded = false;   // d_ids holds h_ids
 };
 
 namespace {
@@ -237,21 +238,33 @@ void plan_buckets(rasp_batch* b) {
   }
 }
 
+// Power-of-two class of a step cap (0 for caps 0 and 1, 64 for no cap).
+inline uint32_t cap_class(uint64_t c) { return c ? 64u - (uint32_t)__builtin_clzll(c) : 0u; }
+
 // Queue order for the current launch groups: every group's range holds
-// exactly the VMs of its buckets; inside a group, longest cap first (the
-// largest work starts first). Uploads the order.
+// exactly the VMs of its buckets; inside a group, VMs with the larger cap
+// class come first (the largest work starts first), in VM id order within a
+// class -- a stable counting sort, linear in the batch. Uploads the order
+// only when it changed.
 int order_ids(rasp_batch* b) {
-  b->h_ids = b->h_ids_base;
+  std::vector<uint32_t> ids = b->h_ids_base;
   if (!b->h_caps.empty()) {
     const std::vector<uint64_t>& caps = b->h_caps;
+    std::vector<uint32_t> tmp;
     for (const Group& k : b->groups) {
       if (k.count < 2) continue;
-      auto first = b->h_ids.begin() + k.first;
-      std::stable_sort(first, first + k.count, [&](uint32_t x, uint32_t y) { return caps[x] > caps[y]; });
+      uint32_t cnt[66] = {0};
+      for (uint32_t q = k.first; q < k.first + k.count; ++q) cnt[64u - cap_class(caps[ids[q]]) + 1u]++;
+      for (int c = 1; c < 66; ++c) cnt[c] += cnt[c - 1];
+      tmp.assign(ids.begin() + k.first, ids.begin() + k.first + k.count);
+      for (uint32_t v : tmp) ids[k.first + cnt[64u - cap_class(caps[v])]++] = v;
     }
   }
+  if (ids == b->h_ids && b->ids_uploaded) return RASP_OK;
+  b->h_ids.swap(ids);
   CK(cudaMemcpyAsync(b->d_ids, b->h_ids.data(), 4ull * b->V, cudaMemcpyHostToDevice, b->stream));
   CK(cudaStreamSynchronize(b->stream));
+  b->ids_uploaded = true;
   return RASP_OK;
 }
 
@@ -431,6 +444,7 @@ int rasp_batch_create(const rasp_config* cfg, uint64_t num_vms, const uint32_t* 
   CKC(cudaMemcpyAsync((void*)S.n, mem_words, 4 * num_vms, cudaMemcpyHostToDevice, st));
   CKC(cudaMemcpyAsync((void*)S.mem_off, b->h_memoff.data(), 8 * num_vms, cudaMemcpyHostToDevice, st));
   CKC(cudaMemcpyAsync(b->d_ids, b->h_ids.data(), 4 * num_vms, cudaMemcpyHostToDevice, st));
+  b->ids_uploaded = true;
   CKC(cudaMemsetAsync(b->base + L.off_status, RASP_RUNNING, num_vms, st));
   CKC(cudaMemsetAsync(b->d_err, 0, 16, st));
   CKC(cudaMemsetAsync(b->d_hist, 0, 8 * 10, st));
@@ -471,25 +485,26 @@ int rasp_load_programs(rasp_batch* b, const int64_t* words, const uint64_t* offs
   if (total) CK(cudaMemcpyAsync(b->d_prog, words, 8 * total, cudaMemcpyHostToDevice, st));
   CK(cudaMemcpyAsync(b->d_progoff, offsets, 8 * (num_programs + 1), cudaMemcpyHostToDevice, st));
   b->shared_programs = prog_of_vm != nullptr;
-  {
+  b->max_plen = 0;
+  for (uint64_t p = 0; p < num_programs; ++p)
+    b->max_plen = std::max<uint32_t>(b->max_plen, (uint32_t)(offsets[p + 1] - offsets[p]));
+  b->num_programs = (uint32_t)num_programs;
+  if (prog_of_vm || (b->cfg.flags & RASP_SCHED_MASK) == RASP_SCHED_SHARED) {
     // VMs grouped by program (counting sort), for the shared-program schedule
     std::vector<uint32_t> pvoff(num_programs + 1, 0), pvids(b->V);
     for (uint32_t v = 0; v < b->V; ++v) pvoff[(prog_of_vm ? prog_of_vm[v] : v) + 1]++;
     for (uint64_t p = 0; p < num_programs; ++p) pvoff[p + 1] += pvoff[p];
     std::vector<uint32_t> fillp(pvoff.begin(), pvoff.end() - 1);
     for (uint32_t v = 0; v < b->V; ++v) pvids[fillp[prog_of_vm ? prog_of_vm[v] : v]++] = v;
-    b->max_plen = 0;
-    for (uint64_t p = 0; p < num_programs; ++p)
-      b->max_plen = std::max<uint32_t>(b->max_plen, (uint32_t)(offsets[p + 1] - offsets[p]));
     if (b->max_plen * 8ull > 200ull * 1024ull && (b->cfg.flags & RASP_SCHED_MASK) == RASP_SCHED_SHARED)
       return fail(RASP_EINVAL, "shared-program schedule: a program of %u words does not fit in shared memory",
                   b->max_plen);
-    b->num_programs = (uint32_t)num_programs;
     CK(cudaMemcpyAsync(b->d_pvoff, pvoff.data(), 4 * pvoff.size(), cudaMemcpyHostToDevice, st));
     CK(cudaMemcpyAsync(b->d_pvids, pvids.data(), 4ull * b->V, cudaMemcpyHostToDevice, st));
     CK(cudaStreamSynchronize(st));
   }
   if (prog_of_vm) CK(cudaMemcpyAsync(b->d_progvm, prog_of_vm, 4ull * b->V, cudaMemcpyHostToDevice, st));
+  CK(cudaStreamSynchronize(st));   // the caller's buffers are read before the call returns
   CK(cudaMemsetAsync(b->d_hist, 0, 8 * 10, st));
   CK(launch_pack(b->S, b->d_prog, b->d_progoff, b->shared_programs ? b->d_progvm : nullptr, b->V, b->wmask, b->sp, st));
   b->programs_loaded = true;
@@ -535,6 +550,7 @@ int rasp_load_inputs(rasp_batch* b, const int64_t* tape, const uint64_t* offsets
     CK(cudaMemsetAsync(b->d_cap, 0xff, 8ull * b->V, st));
     b->h_caps.clear();
   }
+  CK(cudaStreamSynchronize(st));   // the caller's buffers are read before the call returns
   {
     const int rc = order_ids(b);
     if (rc) return rc;

@@ -31,7 +31,9 @@ int pfail(int code, const std::string& msg) {
 struct Request {
   uint64_t ticket = 0;
   int state = RASP_REQ_QUEUED;
-  // host copies of the inputs until admission
+  uint64_t num_vms = 0;
+  // host copies of the inputs while the request waits for admission (a
+  // request admitted at submit is loaded from the caller's buffers instead)
   std::vector<int64_t> words, tape;
   std::vector<uint64_t> offsets, tape_off, caps;
   std::vector<uint32_t> prog_of_vm, mem_words;
@@ -103,8 +105,9 @@ void fail_request(Request& r, int code, const char* where) {
   r.error_msg = std::string(where) + ": " + rasp_last_error();
 }
 
-// Start one admitted request: batch in its block, own stream, load, run.
-void start(rasp_pool* p, Request& r) {
+// Start one admitted request from the host inputs `q`: batch in its block,
+// own stream, load, run.
+void start(rasp_pool* p, Request& r, const rasp_request& q) {
   rasp_config c = p->cfg;
   c.arena = p->base + r.offset;
   c.arena_bytes = r.bytes;
@@ -117,24 +120,40 @@ void start(rasp_pool* p, Request& r) {
     return;
   }
   c.stream = r.stream;
-  int rc = rasp_batch_create(&c, r.mem_words.size(), r.mem_words.data(), &r.batch);
+  int rc = rasp_batch_create(&c, q.num_vms, q.mem_words, &r.batch);
   if (rc) return fail_request(r, rc, "create");
-  rc = rasp_load_programs(r.batch, r.words.data(), r.offsets.data(), r.num_programs,
-                          r.prog_of_vm.empty() ? nullptr : r.prog_of_vm.data());
+  rc = rasp_load_programs(r.batch, q.words, q.offsets, q.num_programs, q.prog_of_vm);
   if (rc) return fail_request(r, rc, "load_programs");
-  rc = rasp_load_inputs(r.batch, r.tape.data(), r.tape_off.data(), r.has_caps ? r.caps.data() : nullptr);
+  rc = rasp_load_inputs(r.batch, q.tape, q.tape_off, q.caps);
   if (rc) return fail_request(r, rc, "load_inputs");
-  rc = rasp_run(r.batch, r.max_steps);
+  rc = rasp_run(r.batch, q.max_steps);
   if (rc) return fail_request(r, rc, "run");
   cudaEventRecord(r.done, r.stream);
   r.state = RASP_REQ_RUNNING;
   // inputs are on the device now
+  std::vector<uint32_t>().swap(r.mem_words);
   std::vector<int64_t>().swap(r.words);
   std::vector<int64_t>().swap(r.tape);
   std::vector<uint64_t>().swap(r.offsets);
   std::vector<uint64_t>().swap(r.tape_off);
   std::vector<uint64_t>().swap(r.caps);
   std::vector<uint32_t>().swap(r.prog_of_vm);
+}
+
+// The host inputs held by a waiting request.
+rasp_request held_inputs(const Request& r) {
+  rasp_request q{};
+  q.words = r.words.data();
+  q.offsets = r.offsets.data();
+  q.num_programs = r.num_programs;
+  q.prog_of_vm = r.prog_of_vm.empty() ? nullptr : r.prog_of_vm.data();
+  q.tape = r.tape.data();
+  q.tape_off = r.tape_off.data();
+  q.caps = r.has_caps ? r.caps.data() : nullptr;
+  q.mem_words = r.mem_words.data();
+  q.num_vms = r.num_vms;
+  q.max_steps = r.max_steps;
+  return q;
 }
 
 // Admit waiting requests in arrival order while the arena has room.
@@ -145,7 +164,7 @@ void admit(rasp_pool* p) {
     if (!carve(p, r.bytes, &off)) break;
     r.offset = off;
     p->waiting.pop_front();
-    start(p, r);
+    start(p, r, held_inputs(r));
   }
 }
 
@@ -191,8 +210,17 @@ int rasp_pool_submit(rasp_pool* p, const rasp_request* q, uint64_t* ticket) {
   Request& r = p->reqs[t];
   r.ticket = t;
   r.bytes = need;
+  r.num_vms = q->num_vms;
   r.num_programs = q->num_programs;
   r.max_steps = q->max_steps;
+  *ticket = t;
+  uint64_t off = 0;
+  if (p->waiting.empty() && carve(p, need, &off)) {
+    // room now: load straight from the caller's buffers, no host copy
+    r.offset = off;
+    start(p, r, *q);
+    return RASP_OK;
+  }
   const uint64_t nwords = q->offsets[q->num_programs];
   r.words.assign(q->words, q->words + nwords);
   r.offsets.assign(q->offsets, q->offsets + q->num_programs + 1);
@@ -241,7 +269,7 @@ int rasp_pool_read(rasp_pool* p, uint64_t ticket, rasp_state_view* out) {
   int rc = r.error;
   std::string msg = r.error_msg;
   if (!rc && r.batch && out) {
-    rc = rasp_read_state(r.batch, 0, r.mem_words.size(), out);
+    rc = rasp_read_state(r.batch, 0, r.num_vms, out);
     if (rc) msg = rasp_last_error();
   }
   if (r.batch) rasp_batch_destroy(r.batch);

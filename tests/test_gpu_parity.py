@@ -175,6 +175,53 @@ def test_budget_and_resume(rasp, sched):
     assert_same_state(got, full, wl.ell, wl.s, what="resumed")
 
 
+@pytest.mark.parametrize("sched", list(SCHEDS))
+def test_reset_repacks_c0_in_the_run(rasp, sched):
+    """rasp_reset re-packs c_0 (Sec. 2.1). On the HBM-slab persistent schedule
+    the run kernel packs each VM itself just before running it: in chunks of
+    32 queue positions while the queue lasts, one VM at a time in the tail.
+    300,000 VMs is more than the resident lanes, so both paths run. Reading
+    the state between reset and run shows c_0."""
+    wl = W.random_programs(num_vms=300_000, seed=12)
+    full, _ = oracle_state(wl, threads=THREADS)
+    c0, _ = oracle_state(wl, budget=0, threads=THREADS)
+    part, _ = oracle_state(wl, budget=37, threads=THREADS)
+    with rasp.Batch(wl.mem_words, wl.ell, wl.s, flags=SCHEDS[sched]) as b:
+        b.load_workload(wl)
+        b.run()
+        b.reset()
+        got0 = b.read_state()
+        assert (got0["status"] == 0).all(), "reset leaves every VM RUNNING"
+        for key in ("i", "a", "steps", "uhead", "ylen"):
+            assert not got0[key].any(), key
+        assert np.array_equal(got0["mem"].view(np.uint64), c0.mem), "c_0 memory"
+        assert not got0["y"].any()
+        b.run()
+        assert_same_state(b.read_state(), full, wl.ell, wl.s, what="reset+run %s" % sched)
+        b.reset()
+        b.run(37)
+        assert_same_state(b.read_state(), part, wl.ell, wl.s, what="reset+run(37) %s" % sched)
+        b.run()
+        assert_same_state(b.read_state(), full, wl.ell, wl.s, what="reset+run(37)+run %s" % sched)
+        b.reset()
+        b.run()
+        st = b.stats()
+    assert st["vm_steps"] == int(full.steps.sum())
+
+
+def test_reset_repacks_shared_programs(rasp):
+    """c_0 packed in the run kernel from a program shared by many VMs."""
+    wl = W.shared_programs(num_programs=600, vms_per_program=256)
+    full, _ = oracle_state(wl, threads=THREADS)
+    with rasp.Batch(wl.mem_words, wl.ell, wl.s, flags=SCHEDS["persist_gl"]) as b:
+        b.load_workload(wl)
+        b.run(100)
+        b.reset()
+        b.run()
+        got = b.read_state()
+    assert_same_state(got, full, wl.ell, wl.s, what="shared reset+run")
+
+
 def test_checkpoint_restore_roundtrip(rasp):
     wl = W.template_programs(num_vms=3000, seed=9)
     full, _ = oracle_state(wl)

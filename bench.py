@@ -133,6 +133,29 @@ def make_workload(name: str, rank: int, vms: int = 1 << 20):
     raise SystemExit("unknown workload %s" % name)
 
 
+def profiled_traffic(vm_steps: int):
+    """DRAM bytes of one run launch from the committed ncu summary of the run
+    kernel (bytes per VM-step of a captured small case, scaled by VM-steps),
+    or None when the kernel sources changed since that capture."""
+    import hashlib
+    path = os.path.join(ROOT, "profiles", "k_persist_gl_templates_256k.md")
+    try:
+        fields = {}
+        for line in open(path):
+            if ":" in line and line.strip().split(":")[0] in ("traffic_bytes_per_vm_step", "kernel_sources_sha256"):
+                k, v = line.strip().split(":", 1)
+                fields[k] = v.strip()
+        h = hashlib.sha256()
+        for f in ("engine.cuh", "kernels.cu"):
+            with open(os.path.join(ROOT, "paper_2604_12902_gb300", "csrc", f), "rb") as fh:
+                h.update(fh.read())
+        if h.hexdigest() != fields["kernel_sources_sha256"]:
+            return None
+        return float(fields["traffic_bytes_per_vm_step"]) * vm_steps
+    except (OSError, KeyError, ValueError):
+        return None
+
+
 def algorithmic_bytes(stats) -> float:
     ops = stats["op_steps"]
     b = sum(BYTES_PER_OP[k] * ops[k] for k in range(1, 8))
@@ -328,9 +351,13 @@ def main():
     hbm, peak_kind = peaks()
     run_avg = float(np.mean(run_ms))
     achieved = alg_bytes / (run_avg * 1e-3) / 1e9
+    # the summary was taken on the default shape (HBM-slab persistent, epoch 128, 4 warps)
+    same_shape = args.workload == "templates" and args.flags == 0 and not args.epoch and \
+        (tuned is None or tuned.get("chosen") == "persist_gl e128 w4")
+    traffic = profiled_traffic(total_steps) if same_shape else None
     roofline = {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
-                "frac": achieved / hbm, "traffic": None,
-                "kernel": "k_persist", "peak_kind": peak_kind,
+                "frac": achieved / hbm, "traffic": traffic,
+                "kernel": "k_persist_gl", "peak_kind": peak_kind,
                 "bytes_per_step": alg_bytes / max(total_steps, 1),
                 "kernel_ms": run_avg, "pack_ms": float(np.mean(pack_ms))}
 

@@ -311,15 +311,25 @@ __device__ __forceinline__ uint32_t step_general(uint64_t* __restrict__ M, const
 // instead of two in a row, at the price of more registers and loads. A
 // STO/RD that writes the prefetched pair invalidates it.
 
+// Load the instruction pair at i into r.cur when the fast path can use it:
+// r.have is true iff i < n, i is even and i + 1 < n (i even and 2^w - 1 odd,
+// so i (+) 1 = i + 1), and then r.cur = <M[i], M[i+1]>.
+__device__ __forceinline__ void prime(const uint64_t* __restrict__ M, Regs& r) {
+  r.have = (r.ibase == 0ull) & ((r.ip & 1u) == 0u) & (r.ip + 1u < r.n);
+  if (r.have) r.cur = *reinterpret_cast<const ulonglong2*>(M + r.ip);
+}
+
 // Fast path of the default step (w = 64, WRAP, no counters) as one
 // predicated PTX block, the same guarded-sum evaluation as the C++ fast path
 // of one_step below but without a branch: the two pair loads (sequential
 // next pair, aligned pair holding M[j mod n]) go out together, every guard is
 // a predicate, and every update -- a, M[j mod n], y, u_0, y_0, i, the next
-// pair -- is committed under the predicate "not rare". A store into the
-// sequential pair (self-modifying code) is forwarded into it. Precondition:
-// i = ip < n, ip even, ip + 1 < n, <co, cj> = <M[ip], M[ip+1]>. Returns 1, and
-// changes nothing, when the step needs the general path.
+// pair and its flag -- is committed under the predicate "not rare". Rare: an
+// invalid opcode, an operand outside [0, n), the end of the countdown, RD at
+// the end of the tape, BNZ to itself, i (+) 2 reaching n, or a store into the
+// pair just loaded for the next step (self-modifying code). Precondition
+// (have): i = ip < n, ip even, ip + 1 < n, <co, cj> = <M[ip], M[ip+1]>.
+// Returns 1, and changes nothing, when the step needs the general path.
 __device__ __forceinline__ uint32_t fast_step_ptx(uint64_t* M, const uint64_t* T, uint64_t* Y, uint32_t n,
                                                   uint32_t ell, uint32_t s, uint64_t& a, uint64_t& co,
                                                   uint64_t& cj, uint32_t& ip, uint32_t& left, uint32_t& u0,
@@ -327,21 +337,21 @@ __device__ __forceinline__ uint32_t fast_step_ptx(uint64_t* M, const uint64_t* T
   uint32_t rare;
   asm volatile(
       "{\n\t"
-      ".reg .pred pv, pj, pz, pt, pq, prd, pl, po, pa, px, pk, p1, p2, p3, p6, p7, pw, pp, ph, pg, pn;\n\t"
-      ".reg .b32 op, jm, t0, t1, nip;\n\t"
-      ".reg .b64 om, nn, sx, sy, qx, qy, v, sm, pd, na, w, ad, of;\n\t"
-      "cvt.u32.u64 op, %1;\n\t"
-      "cvt.u32.u64 jm, %2;\n\t"
-      "add.u64 om, %1, -1;\n\t"
-      "setp.lt.u64 pv, om, 7;\n\t"
-      "cvt.u64.u32 nn, %12;\n\t"
-      "setp.lt.u64 pj, %2, nn;\n\t"
+      ".reg .pred pv, pj, pz, pt, pq, prd, pl, po, pa, px, pk, p1, p2, p3, p6, p7, pw, pp, ph, pg;\n\t"
+      ".reg .b32 op, oh, jm, jh, t0, t1, t2, nip, ip3;\n\t"
+      ".reg .b64 sx, sy, qx, qy, v, sm, pd, na, w, ad;\n\t"
+      "mov.b64 {op, oh}, %1;\n\t"
+      "mov.b64 {jm, jh}, %2;\n\t"
+      "add.u32 t0, op, -1;\n\t"
+      "setp.lt.u32 pv, t0, 7;\n\t"
+      "setp.eq.and.u32 pv, oh, 0, pv;\n\t"
+      "setp.lt.u32 pj, jm, %12;\n\t"
+      "setp.eq.and.u32 pj, jh, 0, pj;\n\t"
       "setp.ne.u64 pz, %0, 0;\n\t"
       "setp.eq.and.u32 pt, op, 5, pz;\n\t"
-      "add.u32 t0, %3, 3;\n\t"
-      "setp.lt.u32 pq, t0, %12;\n\t"
-      "mul.wide.u32 of, %3, 8;\n\t"
-      "add.u64 ad, %9, of;\n\t"
+      "add.u32 ip3, %3, 3;\n\t"
+      "setp.lt.u32 pq, ip3, %12;\n\t"
+      "mad.wide.u32 ad, %3, 8, %9;\n\t"
       "@pq ld.global.v2.u64 {sx, sy}, [ad+16];\n\t"
       "mov.b32 t1, 0x8C;\n\t"
       "shr.b32 t1, t1, op;\n\t"
@@ -349,11 +359,10 @@ __device__ __forceinline__ uint32_t fast_step_ptx(uint64_t* M, const uint64_t* T
       "setp.ne.or.u32 prd, t1, 0, pt;\n\t"
       "and.pred pl, prd, pj;\n\t"
       "and.b32 t0, jm, -2;\n\t"
-      "mul.wide.u32 of, t0, 8;\n\t"
-      "add.u64 ad, %9, of;\n\t"
+      "mad.wide.u32 ad, t0, 8, %9;\n\t"
       "@pl ld.global.v2.u64 {qx, qy}, [ad];\n\t"
-      "and.b32 t0, jm, 1;\n\t"
-      "setp.ne.u32 po, t0, 0;\n\t"
+      "and.b32 t2, jm, 1;\n\t"
+      "setp.ne.u32 po, t2, 0;\n\t"
       "selp.b64 v, qy, qx, po;\n\t"
       "add.u64 sm, %0, v;\n\t"
       "mul.lo.u64 pd, %0, v;\n\t"
@@ -362,6 +371,7 @@ __device__ __forceinline__ uint32_t fast_step_ptx(uint64_t* M, const uint64_t* T
       "and.b32 t1, t1, 1;\n\t"
       "setp.ne.or.u32 pa, t1, 0, pt;\n\t"
       "setp.eq.u32 p6, op, 6;\n\t"
+      "setp.eq.or.u32 pw, op, 4, p6;\n\t"
       "setp.ge.and.u32 px, %6, %13, p6;\n\t"
       "setp.eq.or.u32 px, %5, 0, px;\n\t"
       "not.pred ph, pj;\n\t"
@@ -374,6 +384,9 @@ __device__ __forceinline__ uint32_t fast_step_ptx(uint64_t* M, const uint64_t* T
       "add.u32 nip, %3, 2;\n\t"
       "setp.ge.and.u32 ph, nip, %12, !pt;\n\t"
       "or.pred px, px, ph;\n\t"
+      "or.b32 t0, jm, 1;\n\t"
+      "setp.eq.and.u32 ph, t0, ip3, pw;\n\t"
+      "or.pred px, px, ph;\n\t"
       "not.pred pk, px;\n\t"
       "setp.eq.u32 p1, op, 1;\n\t"
       "setp.eq.u32 p2, op, 2;\n\t"
@@ -381,43 +394,29 @@ __device__ __forceinline__ uint32_t fast_step_ptx(uint64_t* M, const uint64_t* T
       "selp.b64 na, %2, %0, p1;\n\t"
       "selp.b64 na, sm, na, p2;\n\t"
       "selp.b64 na, pd, na, p3;\n\t"
-      "setp.eq.or.u32 pw, op, 4, p6;\n\t"
       "and.pred pw, pw, pk;\n\t"
       "and.pred pg, p6, pk;\n\t"
       "mov.b64 w, %0;\n\t"
-      "mul.wide.u32 of, %6, 8;\n\t"
-      "add.u64 ad, %10, of;\n\t"
+      "mad.wide.u32 ad, %6, 8, %10;\n\t"
       "@pg ld.global.u64 w, [ad];\n\t"
-      "mul.wide.u32 of, jm, 8;\n\t"
-      "add.u64 ad, %9, of;\n\t"
+      "mad.wide.u32 ad, jm, 8, %9;\n\t"
       "@pw st.global.u64 [ad], w;\n\t"
       "setp.eq.u32 p7, op, 7;\n\t"
       "setp.lt.and.u32 pp, %7, %14, p7;\n\t"
       "and.pred pp, pp, pk;\n\t"
-      "mul.wide.u32 of, %7, 8;\n\t"
-      "add.u64 ad, %11, of;\n\t"
+      "mad.wide.u32 ad, %7, 8, %11;\n\t"
       "@pp st.global.u64 [ad], v;\n\t"
       "@pg add.u32 %6, %6, 1;\n\t"
       "@pp add.u32 %7, %7, 1;\n\t"
       "@pk mov.b64 %0, na;\n\t"
-      "or.b32 t0, jm, 1;\n\t"
-      "add.u32 t1, %3, 3;\n\t"
-      "setp.eq.and.u32 ph, t0, t1, pw;\n\t"
-      "and.b32 t0, jm, 1;\n\t"
-      "setp.eq.and.u32 p1, t0, 0, ph;\n\t"
-      "setp.ne.and.u32 p2, t0, 0, ph;\n\t"
-      "@p1 mov.b64 sx, w;\n\t"
-      "@p2 mov.b64 sy, w;\n\t"
       "@pk selp.b64 %1, qx, sx, pt;\n\t"
       "@pk selp.b64 %2, qy, sy, pt;\n\t"
       "add.u32 t1, jm, 1;\n\t"
       "setp.lt.u32 p3, t1, %12;\n\t"
-      "setp.eq.and.u32 p3, t0, 0, p3;\n\t"
-      "and.pred ph, pt, p3;\n\t"
-      "not.pred pn, pt;\n\t"
-      "and.pred pn, pn, pq;\n\t"
-      "or.pred ph, ph, pn;\n\t"
-      "@pk selp.u32 %8, 1, 0, ph;\n\t"
+      "setp.eq.and.u32 p3, t2, 0, p3;\n\t"
+      "selp.u32 t1, 1, 0, p3;\n\t"
+      "selp.u32 t0, 1, 0, pq;\n\t"
+      "@pk selp.u32 %8, t1, t0, pt;\n\t"
       "@pk selp.b32 %3, jm, nip, pt;\n\t"
       "@pk sub.u32 %5, %5, 1;\n\t"
       "selp.u32 %4, 1, 0, px;\n\t"
@@ -434,12 +433,7 @@ __device__ __forceinline__ uint32_t one_step(uint64_t* __restrict__ M, const uin
                                              const uint64_t* Pg = nullptr, uint32_t plen = 0) {
   const uint32_t ip = r.ip, n = r.n;
   if constexpr (PIPE && !MASKED && !CHECKED && !HIST && !SHARED) {
-    const bool al = ((ip & 1u) == 0u) & (ip + 1u < n) & (r.ibase == 0ull);
-    if (al) {
-      if (!r.have) {
-        r.cur = *reinterpret_cast<const ulonglong2*>(M + ip);
-        r.have = true;
-      }
+    if (r.have) {
       uint64_t co = r.cur.x, cj = r.cur.y;
       uint32_t hv = 1;
       const uint32_t rare = fast_step_ptx(M, T, Y, n, P.ell, P.s, r.a, co, cj, r.ip, r.left, r.u0, r.y0, hv);
@@ -451,7 +445,9 @@ __device__ __forceinline__ uint32_t one_step(uint64_t* __restrict__ M, const uin
       }
     }
     r.have = false;
-    return step_general<MASKED, CHECKED, HIST, SHARED>(M, T, Y, P, r, h, plen);
+    const uint32_t s = step_general<MASKED, CHECKED, HIST, SHARED>(M, T, Y, P, r, h, plen);
+    if (s == CONT) prime(M, r);
+    return s;
   }
   const uint32_t ilim = MASKED ? r.ilim : n;
   // i = ip < n even with ip + 1 < n: i != 2^w - 1 and M[ip], M[ip+1] is one

@@ -372,6 +372,7 @@ __global__ void __launch_bounds__(128, 7) k_persist_gl(DevState S, Params P, Que
         M = S.mem + nmoff;
         T = S.tape + (uint64_t)pf_vm * P.ellp;
         Y = S.y + (uint64_t)pf_vm * P.sp;
+        if (!VOTE) prime(M, r);
         active = true;
       }
       pf = PF_EMPTY;
@@ -447,6 +448,7 @@ __global__ void __launch_bounds__(128, 7) k_persist_gl(DevState S, Params P, Que
         M = S.mem + nmoff;
         T = S.tape + (uint64_t)pf_vm * P.ellp;
         Y = S.y + (uint64_t)pf_vm * P.sp;
+        if (!VOTE) prime(M, r);
         active = true;
       }
     }

@@ -127,6 +127,14 @@ def make_workload(name: str, rank: int, vms: int = 1 << 20):
         wl = W.shared_programs()
         return wl, ("16,384 programs (48 instr, loop templates) x 256 tapes of 8 ints U[-50,50] = 4,194,304 VMs, "
                     "n = 96 program + 128 data words, cap 2048")
+    if name == "halting":
+        from paper_2604_12902_gb300 import sampler as S
+        first, count = shard_range(rank, vms)
+        wl = S.halting_programs_parallel(count, workers=os.cpu_count() or 1, L=100, seed=6, cap=10 ** 6,
+                                         first=first)
+        return wl, ("%s programs of the array language, uniform over valid snippets of L = 100 tokens, "
+                    "lowered (Sec. 2.2), w = 32, n = 250, l = 10, s = 2, tau_max = 10^6 (Sec. 3)"
+                    % format(wl.num_vms, ","))
     if name == "random":
         return W.random_programs(num_vms=1024, seed=1, first_vm=rank * 1024), \
             "1,024 random programs (32 instr, opcodes U{1..7}, operands U[0,63]), n=64, l=4, s=8, cap 256"
@@ -174,7 +182,7 @@ def cpu_baseline(wl, budget_s: float = 15.0, threads: int = 1):
         sub = wl.subset(np.arange(done_vms, hi))
         t0 = time.perf_counter()
         st, _ = oracle.run_packed(sub.programs, sub.prog_off, sub.mem_words, sub.tapes, sub.tape_off,
-                                  sub.ell, sub.s, caps=sub.caps, threads=threads)
+                                  sub.ell, sub.s, caps=sub.caps, w=sub.w, threads=threads)
         t_used += time.perf_counter() - t0
         steps += int(st.steps.sum())
         done_vms = hi
@@ -195,7 +203,7 @@ def run_reference(args, ws, rank):
     for it in range(args.warmup + args.steps):
         t0 = time.perf_counter()
         st, _ = oracle.run_packed(sub.programs, sub.prog_off, sub.mem_words, sub.tapes, sub.tape_off,
-                                  sub.ell, sub.s, caps=sub.caps, threads=threads)
+                                  sub.ell, sub.s, caps=sub.caps, w=sub.w, threads=threads)
         dt = time.perf_counter() - t0
         if it >= args.warmup:
             times.append(dt)
@@ -256,7 +264,7 @@ def main():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
-    ap.add_argument("--workload", default="templates", choices=["templates", "uneven", "shared", "random", "serving"])
+    ap.add_argument("--workload", default="templates", choices=["templates", "uneven", "shared", "random", "serving", "halting"])
     ap.add_argument("--flags", type=lambda x: int(x, 0), default=0, help="rasp_config.flags (schedule)")
     ap.add_argument("--epoch", type=int, default=0)
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU-oracle baseline")
@@ -291,19 +299,23 @@ def main():
 
     wl, desc = make_workload(args.workload, rank, args.vms)
     stream = torch.cuda.current_stream()
-    b = R.Batch(wl.mem_words, wl.ell, wl.s, flags=args.flags, epoch=args.epoch)
+    b = R.Batch(wl.mem_words, wl.ell, wl.s, word_bits=wl.w, flags=args.flags, epoch=args.epoch)
     b.load_workload(wl)
     tuned = None
     if (args.flags & R.SCHED_PERSIST_GL) == 0 and not args.epoch and not args.no_tune:
         tuned = b.autotune(reps=2)      # untimed: measured schedule choice, state unchanged
 
     # opcode mix (and total steps) from an untimed counting run
-    with R.Batch(wl.mem_words, wl.ell, wl.s, flags=args.flags | R.COLLECT_STATS, epoch=args.epoch) as bs:
+    with R.Batch(wl.mem_words, wl.ell, wl.s, word_bits=wl.w, flags=args.flags | R.COLLECT_STATS, epoch=args.epoch) as bs:
         bs.load_workload(wl)
         bs.run()
         stats = bs.stats()
     total_steps = stats["vm_steps"]
     alg_bytes = algorithmic_bytes(stats)
+
+    # halting workload: the tau_h histogram is computed on the device in every step
+    hist_edges = np.concatenate([np.arange(0, 101), [10 ** 6, 1 << 62]]).astype(np.uint64)
+    hist = {}
 
     def step(evs=None):
         if evs:
@@ -314,6 +326,8 @@ def main():
         b.run()
         if evs:
             evs[2].record(stream)
+        if args.workload == "halting":
+            hist["counts"], hist["other"] = b.halting_histogram(hist_edges)
 
     for _ in range(args.warmup):
         step()
@@ -364,7 +378,7 @@ def main():
     # plain one-launch-per-batch form on the same workload (untimed by the contract)
     plain = None
     if not args.no_plain:
-        with R.Batch(wl.mem_words, wl.ell, wl.s, flags=R.SCHED_PLAIN) as bp:
+        with R.Batch(wl.mem_words, wl.ell, wl.s, word_bits=wl.w, flags=R.SCHED_PLAIN) as bp:
             bp.load_workload(wl)
             bp.run()
             torch.cuda.synchronize()
@@ -434,7 +448,18 @@ def main():
                            "schedule_flags": args.flags, "parallelism": "vm shards x%d" % ws,
                            "schedule": tuned["chosen"] if tuned else "flags %#x" % args.flags},
                 "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "plain": plain,
-                "gpu_launches": (1 + run_launches) * args.steps, "clocks": clocks}
+                "gpu_launches": (1 + run_launches + (1 if hist else 0)) * args.steps, "clocks": clocks}
+        if hist:
+            c, o = hist["counts"], hist["other"]
+            halted = int(c.sum() + o[3])
+            line["halting"] = {
+                "programs": wl.num_vms, "halted": halted, "halted_frac": halted / wl.num_vms,
+                "tau_h_lt_100": int(c[:100].sum()), "tau_h_100_to_1e6": int(c[100]), "timeout_1e6": int(o[1]),
+                "mean_tau_h_lt_100": float((c[:100] * np.arange(100)).sum() / max(c[:100].sum(), 1)),
+                "min_tau_h": int(np.nonzero(c)[0][0]) if c.any() else None,
+                "wall_s_per_run": run_avg * 1e-3,
+                "paper_context": "Fig. 1: 8e6 programs (its own sampler), 96.6 % halt, 211 with tau_h in "
+                                 "[100, 1e6), mean tau_h ~18.2; 1x B200 1.1 s for 1e6 programs"}
         print(json.dumps(line), flush=True)
     if dist:
         dist.destroy_process_group()

@@ -190,7 +190,20 @@ int rasp_load_state(rasp_batch* b, uint64_t first, uint64_t count,
 /* Aggregate counters of the batch (synchronises the stream). */
 int rasp_read_stats(rasp_batch* b, rasp_stats* out);
 
-/* Measured schedule choice (SURVEY's autotuner): times candidate schedules
+/* Halting-time histogram of the batch, computed on the device: the
+ * distribution of tau_h (the number of steps after which a machine reached
+ * its fixed point; "Towards a Linear-Algebraic Hypervisor", Sec. 3, Fig. 1b)
+ * over the HALTED machines. edges[0..nbins] (host array, strictly
+ * increasing) delimit the bins: counts[k] = number of HALTED VMs with
+ * edges[k] <= steps < edges[k+1]. other (optional, 4 entries) receives the
+ * number of RUNNING, TIMEOUT and faulted (either kind) VMs, and of HALTED
+ * VMs outside [edges[0], edges[nbins]). counts and other are host arrays
+ * owned by the caller. Synchronises the stream. EINVAL: nbins 0 or above
+ * 4096, edges not strictly increasing. */
+int rasp_halting_histogram(rasp_batch* b, const uint64_t* edges, uint32_t nbins,
+                           uint64_t* counts, uint64_t* other);
+
+/* Measured schedule choice (the autotuner): times candidate schedules
  * (persistent over HBM slabs with several epochs and CTA shapes, plain, and
  * SMEM-staged where it fits) on this batch from its current state with the
  * given step budget, `reps` times each, restoring the state after every

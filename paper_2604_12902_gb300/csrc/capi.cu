@@ -63,7 +63,7 @@ struct Group {
 struct Layout {
   size_t off_i, off_a, off_steps, off_cap, off_status, off_uhead, off_ylen, off_n, off_memoff;
   size_t off_mem, off_prog, off_progoff, off_progvm, off_tape, off_y, off_ids, off_heads, off_err,
-      off_hist, off_stats, off_dirty, off_pvoff, off_pvids;
+      off_hist, off_stats, off_dirty, off_pvoff, off_pvids, off_thist, off_ids2, off_rcount;
   size_t total;
 };
 
@@ -110,6 +110,9 @@ struct rasp_batch {
   uint32_t max_plen = 0;
   bool dirty_valid = false;    // codedirty is up to date (only the shared kernel tracks it)
   bool ids_uploaded = false;   // d_ids holds h_ids
+  uint64_t max_cap = ~0ull;    // largest step cap of the batch (no VM runs further)
+  uint32_t* d_ids2 = nullptr;  // compacted queue between budget rounds
+  uint32_t* d_rcount = nullptr;
 };
 
 namespace {
@@ -170,6 +173,9 @@ Layout make_layout(uint64_t V, uint64_t mem_words, uint32_t ellp, uint32_t sp) {
   L.off_dirty = take(V);
   L.off_pvoff = take(4 * (V + 1));
   L.off_pvids = take(4 * V);
+  L.off_thist = take(8 * (2 * kMaxHistBins + 1 + 4));   // edges, counts, other
+  L.off_ids2 = take(4 * V);                             // compacted queue between budget rounds
+  L.off_rcount = take(4 * kNumBuckets);                 // its length, per launch group
   L.total = o;
   return L;
 }
@@ -393,6 +399,8 @@ int rasp_batch_create(const rasp_config* cfg, uint64_t num_vms, const uint32_t* 
   S.codedirty = (uint8_t*)(B + L.off_dirty);
   b->d_pvoff = (uint32_t*)(B + L.off_pvoff);
   b->d_pvids = (uint32_t*)(B + L.off_pvids);
+  b->d_ids2 = (uint32_t*)(B + L.off_ids2);
+  b->d_rcount = (uint32_t*)(B + L.off_rcount);
 
   // buckets by memory size (stable: VM id order within a bucket)
   std::vector<uint32_t> cls(num_vms);
@@ -540,8 +548,10 @@ int rasp_load_inputs(rasp_batch* b, const int64_t* tape, const uint64_t* offsets
       CK(cudaStreamSynchronize(st));
     }
   }
+  b->max_cap = ~0ull;
   if (caps) {
     CK(cudaMemcpyAsync(b->d_cap, caps, 8ull * b->V, cudaMemcpyHostToDevice, st));
+    b->max_cap = *std::max_element(caps, caps + b->V);
     bool uniform = true;
     for (uint32_t v = 1; v < b->V && uniform; ++v) uniform = caps[v] == caps[0];
     if (uniform) b->h_caps.clear();
@@ -575,7 +585,19 @@ int rasp_reset(rasp_batch* b) {
 
 namespace {
 
-// Enqueue one rasp_run on `st`: reset the queue counters, one launch per group.
+// Budget rounds of the HBM-slab persistent schedule. Round r stops every VM
+// at min(budget_r, its cap); budgets grow geometrically from kRound0, and the
+// last round has the caller's budget (a VM's steps are cumulative, so the
+// rounds together equal one run to that budget). Between rounds the VMs of
+// the launch group that are still RUNNING are compacted into a dense queue:
+// the few long-running VMs then fill whole warps instead of each keeping a
+// warp busy whose other lanes have nothing left to run.
+constexpr uint64_t kRound0 = 4096;
+constexpr uint64_t kRoundGrowth = 8;
+constexpr int kMaxRounds = 6;
+
+// Enqueue one rasp_run on `st`: reset the queue counters, one launch per group
+// (per budget round for the HBM-slab persistent schedule).
 int enqueue_run(rasp_batch* b, cudaStream_t st, uint64_t max_steps) {
   const StepVariant var = variant_of(b);
   Params P{};
@@ -604,10 +626,37 @@ int enqueue_run(rasp_batch* b, cudaStream_t st, uint64_t max_steps) {
     } else if (g.sched == RASP_SCHED_PLAIN) {
       b->dirty_valid = false;
       CK(launch_plain(var, b->S, P, ids, g.count, st));
+    } else if (g.sched == RASP_SCHED_PERSIST) {
+      b->dirty_valid = false;
+      Queue Q{ids, g.count, b->d_heads + k, b->d_heads + kNumBuckets + k, 0, nullptr};
+      CK(launch_persist(var, b->S, P, Q, g.shape, st));
     } else {
       b->dirty_valid = false;
-      Queue Q{ids, g.count, b->d_heads + k, b->d_heads + kNumBuckets + k, 0};
-      CK(launch_persist(var, b->S, P, Q, g.shape, st));
+      std::vector<uint64_t> budgets;
+      const uint64_t limit = std::min(max_steps, b->max_cap);
+      for (uint64_t r = kRound0; r < limit && (int)budgets.size() < kMaxRounds; r *= kRoundGrowth)
+        budgets.push_back(r);
+      budgets.push_back(max_steps);
+      for (size_t r = 0; r < budgets.size(); ++r) {
+        uint32_t* head = b->d_heads + k;
+        uint32_t* tail = b->d_heads + kNumBuckets + k;
+        P.budget = budgets[r];
+        if (r == 0) {
+          Queue Q{ids, g.count, head, tail, 0, nullptr};
+          CK(launch_persist(var, b->S, P, Q, g.shape, st));
+        } else {
+          uint32_t* dense = b->d_ids2 + g.first;
+          CK(launch_compact(ids, g.count, b->S.status, dense, b->d_rcount + k, st));
+          CK(cudaMemsetAsync(head, 0, sizeof(uint32_t), st));
+          CK(cudaMemsetAsync(tail, 0, sizeof(uint32_t), st));
+          Queue Q{dense, g.count, head, tail, 0, b->d_rcount + k};
+          CK(launch_persist(var, b->S, P, Q, g.shape, st));
+          launches++;                      // the compaction kernel
+        }
+        launches++;
+      }
+      P.budget = max_steps;
+      continue;
     }
     launches++;
   }
@@ -751,6 +800,28 @@ int rasp_load_state(rasp_batch* b, uint64_t first, uint64_t count, const rasp_st
     CK(cudaMemsetAsync(b->S.codedirty + first, 1, count, st));   // restored M may differ from the program
   }
   CK(cudaStreamSynchronize(st));
+  return RASP_OK;
+}
+
+int rasp_halting_histogram(rasp_batch* b, const uint64_t* edges, uint32_t nbins, uint64_t* counts,
+                           uint64_t* other) {
+  if (!b || !edges || !counts) return fail(RASP_EINVAL, "batch, edges or counts is NULL");
+  if (nbins == 0 || nbins > kMaxHistBins) return fail(RASP_EINVAL, "nbins must be in 1..%u", kMaxHistBins);
+  for (uint32_t k = 0; k < nbins; ++k)
+    if (edges[k] >= edges[k + 1]) return fail(RASP_EINVAL, "edges must increase strictly (edges[%u])", k);
+  int rc = check_device_error(b);
+  if (rc) return rc;
+  cudaStream_t st = b->stream;
+  uint64_t* d_edges = (uint64_t*)(b->base + b->L.off_thist);
+  unsigned long long* d_counts = (unsigned long long*)(d_edges + kMaxHistBins + 1);
+  unsigned long long* d_other = d_counts + kMaxHistBins;
+  uint64_t oth[4] = {0, 0, 0, 0};
+  CK(cudaMemcpyAsync(d_edges, edges, 8ull * (nbins + 1), cudaMemcpyHostToDevice, st));
+  CK(launch_tau_hist(b->S, b->V, d_edges, nbins, d_counts, d_other, st));
+  CK(cudaMemcpyAsync(counts, d_counts, 8ull * nbins, cudaMemcpyDeviceToHost, st));
+  CK(cudaMemcpyAsync(oth, d_other, sizeof(oth), cudaMemcpyDeviceToHost, st));
+  CK(cudaStreamSynchronize(st));
+  if (other) memcpy(other, oth, sizeof(oth));
   return RASP_OK;
 }
 

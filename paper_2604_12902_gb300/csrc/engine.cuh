@@ -52,10 +52,13 @@ struct Params {
 
 struct Queue {
   const uint32_t* ids;        // VM ids in schedule order
-  uint32_t count;
+  uint32_t count;             // number of ids (when dcount is NULL)
   uint32_t* head;             // next unclaimed position (reset to 0 per launch)
   uint32_t* tail_head;        // next unclaimed tail position (reset to 0 per launch)
   uint32_t soft_end;          // positions >= soft_end are handed out one by one to idle lanes
+  const uint32_t* dcount;     // persistent HBM-slab kernel: if set, the number of ids is read
+                              // here at launch (written by an earlier kernel on the stream) and
+                              // soft_end is derived from it
 };
 
 // Registers of one machine while it runs. The instruction counter is kept
@@ -319,111 +322,122 @@ __device__ __forceinline__ void prime(const uint64_t* __restrict__ M, Regs& r) {
   if (r.have) r.cur = *reinterpret_cast<const ulonglong2*>(M + r.ip);
 }
 
-// Fast path of the default step (w = 64, WRAP, no counters) as one
+// Fast path of the default step (WRAP, no counters; any w) as one
 // predicated PTX block, the same guarded-sum evaluation as the C++ fast path
 // of one_step below but without a branch: the two pair loads (sequential
 // next pair, aligned pair holding M[j mod n]) go out together, every guard is
 // a predicate, and every update -- a, M[j mod n], y, u_0, y_0, i, the next
 // pair and its flag -- is committed under the predicate "not rare". Rare: an
 // invalid opcode, an operand outside [0, n), the end of the countdown, RD at
-// the end of the tape, BNZ to itself, i (+) 2 reaching n, or a store into the
+// the end of the tape, BNZ to itself, i (+) 2 reaching n or 2^w, a store into the
 // pair just loaded for the next step (self-modifying code). Precondition
 // (have): i = ip < n, ip even, ip + 1 < n, <co, cj> = <M[ip], M[ip+1]>.
 // Returns 1, and changes nothing, when the step needs the general path.
+#define RASP_FAST_STEP_A \
+      "{\n\t" \
+      ".reg .pred pv, pj, pz, pt, pq, prd, pl, po, pa, px, pk, p1, p2, p3, p6, p7, pw, pp, ph, pg;\n\t" \
+      ".reg .b32 op, oh, jm, jh, t0, t1, t2, nip, ip3;\n\t" \
+      ".reg .b64 sx, sy, qx, qy, v, sm, pd, na, w, ad;\n\t" \
+      "mov.b64 {op, oh}, %1;\n\t" \
+      "mov.b64 {jm, jh}, %2;\n\t" \
+      "add.u32 t0, op, -1;\n\t" \
+      "setp.lt.u32 pv, t0, 7;\n\t" \
+      "setp.eq.and.u32 pv, oh, 0, pv;\n\t" \
+      "setp.lt.u32 pj, jm, %12;\n\t" \
+      "setp.eq.and.u32 pj, jh, 0, pj;\n\t" \
+      "setp.ne.u64 pz, %0, 0;\n\t" \
+      "setp.eq.and.u32 pt, op, 5, pz;\n\t" \
+      "add.u32 ip3, %3, 3;\n\t" \
+      "setp.lt.u32 pq, ip3, %12;\n\t" \
+      "mad.wide.u32 ad, %3, 8, %9;\n\t" \
+      "@pq ld.global.v2.u64 {sx, sy}, [ad+16];\n\t" \
+      "mov.b32 t1, 0x8C;\n\t" \
+      "shr.b32 t1, t1, op;\n\t" \
+      "and.b32 t1, t1, 1;\n\t" \
+      "setp.ne.or.u32 prd, t1, 0, pt;\n\t" \
+      "and.pred pl, prd, pj;\n\t" \
+      "and.b32 t0, jm, -2;\n\t" \
+      "mad.wide.u32 ad, t0, 8, %9;\n\t" \
+      "@pl ld.global.v2.u64 {qx, qy}, [ad];\n\t" \
+      "and.b32 t2, jm, 1;\n\t" \
+      "setp.ne.u32 po, t2, 0;\n\t" \
+      "selp.b64 v, qy, qx, po;\n\t" \
+      "add.u64 sm, %0, v;\n\t" \
+      "mul.lo.u64 pd, %0, v;\n\t" \
+      "mov.b32 t1, 0xDC;\n\t" \
+      "shr.b32 t1, t1, op;\n\t" \
+      "and.b32 t1, t1, 1;\n\t" \
+      "setp.ne.or.u32 pa, t1, 0, pt;\n\t" \
+      "setp.eq.u32 p6, op, 6;\n\t" \
+      "setp.eq.or.u32 pw, op, 4, p6;\n\t" \
+      "setp.ge.and.u32 px, %6, %13, p6;\n\t" \
+      "setp.eq.or.u32 px, %5, 0, px;\n\t" \
+      "not.pred ph, pj;\n\t" \
+      "and.pred ph, ph, pa;\n\t" \
+      "or.pred px, px, ph;\n\t" \
+      "not.pred ph, pv;\n\t" \
+      "or.pred px, px, ph;\n\t" \
+      "setp.eq.and.u32 ph, jm, %3, pt;\n\t" \
+      "or.pred px, px, ph;\n\t" \
+      "add.u32 nip, %3, 2;\n\t" \
+      "setp.ge.and.u32 ph, nip, %15, !pt;\n\t" \
+      "or.pred px, px, ph;\n\t" \
+      "or.b32 t0, jm, 1;\n\t" \
+      "setp.eq.and.u32 ph, t0, ip3, pw;\n\t" \
+      "or.pred px, px, ph;\n\t" \
+      "not.pred pk, px;\n\t" \
+      "setp.eq.u32 p1, op, 1;\n\t" \
+      "setp.eq.u32 p2, op, 2;\n\t" \
+      "setp.eq.u32 p3, op, 3;\n\t" \
+      "selp.b64 na, %2, %0, p1;\n\t" \
+      "selp.b64 na, sm, na, p2;\n\t" \
+      "selp.b64 na, pd, na, p3;\n\t" \
+      "and.pred pw, pw, pk;\n\t" \
+      "and.pred pg, p6, pk;\n\t" \
+      "mov.b64 w, %0;\n\t" \
+      "mad.wide.u32 ad, %6, 8, %10;\n\t" \
+      "@pg ld.global.u64 w, [ad];\n\t" \
+      "mad.wide.u32 ad, jm, 8, %9;\n\t" \
+      "@pw st.global.u64 [ad], w;\n\t" \
+      "setp.eq.u32 p7, op, 7;\n\t" \
+      "setp.lt.and.u32 pp, %7, %14, p7;\n\t" \
+      "and.pred pp, pp, pk;\n\t" \
+      "mad.wide.u32 ad, %7, 8, %11;\n\t" \
+      "@pp st.global.u64 [ad], v;\n\t" \
+      "@pg add.u32 %6, %6, 1;\n\t" \
+      "@pp add.u32 %7, %7, 1;\n\t"
+#define RASP_FAST_STEP_B \
+      "@pk mov.b64 %0, na;\n\t" \
+      "@pk selp.b64 %1, qx, sx, pt;\n\t" \
+      "@pk selp.b64 %2, qy, sy, pt;\n\t" \
+      "add.u32 t1, jm, 1;\n\t" \
+      "setp.lt.u32 p3, t1, %12;\n\t" \
+      "setp.eq.and.u32 p3, t2, 0, p3;\n\t" \
+      "selp.u32 t1, 1, 0, p3;\n\t" \
+      "selp.u32 t0, 1, 0, pq;\n\t" \
+      "@pk selp.u32 %8, t1, t0, pt;\n\t" \
+      "@pk selp.b32 %3, jm, nip, pt;\n\t" \
+      "@pk sub.u32 %5, %5, 1;\n\t" \
+      "selp.u32 %4, 1, 0, px;\n\t" \
+      "}"
+#define RASP_FAST_STEP_OPERANDS                                                                   \
+  : "+l"(a), "+l"(co), "+l"(cj), "+r"(ip), "=r"(rare), "+r"(left), "+r"(u0), "+r"(y0), "+r"(have) \
+  : "l"(M), "l"(T), "l"(Y), "r"(n), "r"(ell), "r"(s), "r"(ilim), "l"(wmask)                      \
+  : "memory"
+
+template <bool MASKED>
 __device__ __forceinline__ uint32_t fast_step_ptx(uint64_t* M, const uint64_t* T, uint64_t* Y, uint32_t n,
                                                   uint32_t ell, uint32_t s, uint64_t& a, uint64_t& co,
                                                   uint64_t& cj, uint32_t& ip, uint32_t& left, uint32_t& u0,
-                                                  uint32_t& y0, uint32_t& have) {
+                                                  uint32_t& y0, uint32_t& have, uint32_t ilim, uint64_t wmask) {
   uint32_t rare;
-  asm volatile(
-      "{\n\t"
-      ".reg .pred pv, pj, pz, pt, pq, prd, pl, po, pa, px, pk, p1, p2, p3, p6, p7, pw, pp, ph, pg;\n\t"
-      ".reg .b32 op, oh, jm, jh, t0, t1, t2, nip, ip3;\n\t"
-      ".reg .b64 sx, sy, qx, qy, v, sm, pd, na, w, ad;\n\t"
-      "mov.b64 {op, oh}, %1;\n\t"
-      "mov.b64 {jm, jh}, %2;\n\t"
-      "add.u32 t0, op, -1;\n\t"
-      "setp.lt.u32 pv, t0, 7;\n\t"
-      "setp.eq.and.u32 pv, oh, 0, pv;\n\t"
-      "setp.lt.u32 pj, jm, %12;\n\t"
-      "setp.eq.and.u32 pj, jh, 0, pj;\n\t"
-      "setp.ne.u64 pz, %0, 0;\n\t"
-      "setp.eq.and.u32 pt, op, 5, pz;\n\t"
-      "add.u32 ip3, %3, 3;\n\t"
-      "setp.lt.u32 pq, ip3, %12;\n\t"
-      "mad.wide.u32 ad, %3, 8, %9;\n\t"
-      "@pq ld.global.v2.u64 {sx, sy}, [ad+16];\n\t"
-      "mov.b32 t1, 0x8C;\n\t"
-      "shr.b32 t1, t1, op;\n\t"
-      "and.b32 t1, t1, 1;\n\t"
-      "setp.ne.or.u32 prd, t1, 0, pt;\n\t"
-      "and.pred pl, prd, pj;\n\t"
-      "and.b32 t0, jm, -2;\n\t"
-      "mad.wide.u32 ad, t0, 8, %9;\n\t"
-      "@pl ld.global.v2.u64 {qx, qy}, [ad];\n\t"
-      "and.b32 t2, jm, 1;\n\t"
-      "setp.ne.u32 po, t2, 0;\n\t"
-      "selp.b64 v, qy, qx, po;\n\t"
-      "add.u64 sm, %0, v;\n\t"
-      "mul.lo.u64 pd, %0, v;\n\t"
-      "mov.b32 t1, 0xDC;\n\t"
-      "shr.b32 t1, t1, op;\n\t"
-      "and.b32 t1, t1, 1;\n\t"
-      "setp.ne.or.u32 pa, t1, 0, pt;\n\t"
-      "setp.eq.u32 p6, op, 6;\n\t"
-      "setp.eq.or.u32 pw, op, 4, p6;\n\t"
-      "setp.ge.and.u32 px, %6, %13, p6;\n\t"
-      "setp.eq.or.u32 px, %5, 0, px;\n\t"
-      "not.pred ph, pj;\n\t"
-      "and.pred ph, ph, pa;\n\t"
-      "or.pred px, px, ph;\n\t"
-      "not.pred ph, pv;\n\t"
-      "or.pred px, px, ph;\n\t"
-      "setp.eq.and.u32 ph, jm, %3, pt;\n\t"
-      "or.pred px, px, ph;\n\t"
-      "add.u32 nip, %3, 2;\n\t"
-      "setp.ge.and.u32 ph, nip, %12, !pt;\n\t"
-      "or.pred px, px, ph;\n\t"
-      "or.b32 t0, jm, 1;\n\t"
-      "setp.eq.and.u32 ph, t0, ip3, pw;\n\t"
-      "or.pred px, px, ph;\n\t"
-      "not.pred pk, px;\n\t"
-      "setp.eq.u32 p1, op, 1;\n\t"
-      "setp.eq.u32 p2, op, 2;\n\t"
-      "setp.eq.u32 p3, op, 3;\n\t"
-      "selp.b64 na, %2, %0, p1;\n\t"
-      "selp.b64 na, sm, na, p2;\n\t"
-      "selp.b64 na, pd, na, p3;\n\t"
-      "and.pred pw, pw, pk;\n\t"
-      "and.pred pg, p6, pk;\n\t"
-      "mov.b64 w, %0;\n\t"
-      "mad.wide.u32 ad, %6, 8, %10;\n\t"
-      "@pg ld.global.u64 w, [ad];\n\t"
-      "mad.wide.u32 ad, jm, 8, %9;\n\t"
-      "@pw st.global.u64 [ad], w;\n\t"
-      "setp.eq.u32 p7, op, 7;\n\t"
-      "setp.lt.and.u32 pp, %7, %14, p7;\n\t"
-      "and.pred pp, pp, pk;\n\t"
-      "mad.wide.u32 ad, %7, 8, %11;\n\t"
-      "@pp st.global.u64 [ad], v;\n\t"
-      "@pg add.u32 %6, %6, 1;\n\t"
-      "@pp add.u32 %7, %7, 1;\n\t"
-      "@pk mov.b64 %0, na;\n\t"
-      "@pk selp.b64 %1, qx, sx, pt;\n\t"
-      "@pk selp.b64 %2, qy, sy, pt;\n\t"
-      "add.u32 t1, jm, 1;\n\t"
-      "setp.lt.u32 p3, t1, %12;\n\t"
-      "setp.eq.and.u32 p3, t2, 0, p3;\n\t"
-      "selp.u32 t1, 1, 0, p3;\n\t"
-      "selp.u32 t0, 1, 0, pq;\n\t"
-      "@pk selp.u32 %8, t1, t0, pt;\n\t"
-      "@pk selp.b32 %3, jm, nip, pt;\n\t"
-      "@pk sub.u32 %5, %5, 1;\n\t"
-      "selp.u32 %4, 1, 0, px;\n\t"
-      "}"
-      : "+l"(a), "+l"(co), "+l"(cj), "+r"(ip), "=r"(rare), "+r"(left), "+r"(u0), "+r"(y0), "+r"(have)
-      : "l"(M), "l"(T), "l"(Y), "r"(n), "r"(ell), "r"(s)
-      : "memory");
+  if constexpr (MASKED) {
+    // w < 64: the new accumulator is reduced to w bits; i (+) 2 must stay
+    // below ilim = min(n, 2^w)
+    asm volatile(RASP_FAST_STEP_A "and.b64 na, na, %16;\n\t" RASP_FAST_STEP_B RASP_FAST_STEP_OPERANDS);
+  } else {
+    asm volatile(RASP_FAST_STEP_A RASP_FAST_STEP_B RASP_FAST_STEP_OPERANDS);
+  }
   return rare;
 }
 
@@ -432,11 +446,12 @@ __device__ __forceinline__ uint32_t one_step(uint64_t* __restrict__ M, const uin
                                              uint64_t* __restrict__ Y, const Params& P, Regs& r, Hist& h,
                                              const uint64_t* Pg = nullptr, uint32_t plen = 0) {
   const uint32_t ip = r.ip, n = r.n;
-  if constexpr (PIPE && !MASKED && !CHECKED && !HIST && !SHARED) {
+  if constexpr (PIPE && !CHECKED && !HIST && !SHARED) {
     if (r.have) {
       uint64_t co = r.cur.x, cj = r.cur.y;
       uint32_t hv = 1;
-      const uint32_t rare = fast_step_ptx(M, T, Y, n, P.ell, P.s, r.a, co, cj, r.ip, r.left, r.u0, r.y0, hv);
+      const uint32_t rare = fast_step_ptx<MASKED>(M, T, Y, n, P.ell, P.s, r.a, co, cj, r.ip, r.left, r.u0, r.y0,
+                                                  hv, MASKED ? r.ilim : n, P.wmask);
       if (!rare) {
         r.cur.x = co;
         r.cur.y = cj;

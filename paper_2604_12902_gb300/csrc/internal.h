@@ -52,6 +52,17 @@ int persist_configure(const StepVariant& var, PersistShape& shape);
 cudaError_t launch_persist(const StepVariant& var, const DevState& S, const Params& P, const Queue& Q,
                            const PersistShape& shape, cudaStream_t stream);
 
+// Halting-time histogram (device): counts[nbins] of HALTED VMs by
+// edges[k] <= steps < edges[k+1]; other[4] = RUNNING, TIMEOUT, faulted,
+// HALTED outside the edges. edges, counts, other are device pointers.
+constexpr uint32_t kMaxHistBins = 4096;
+cudaError_t launch_tau_hist(const DevState& S, uint32_t num_vms, const uint64_t* edges, uint32_t nbins,
+                            unsigned long long* counts, unsigned long long* other, cudaStream_t stream);
+
+// Dense list of the still-RUNNING VMs among ids[0, count): out[0, *out_count).
+cudaError_t launch_compact(const uint32_t* ids, uint32_t count, const uint8_t* status, uint32_t* out,
+                           uint32_t* out_count, cudaStream_t stream);
+
 // Aggregate: out[0] = sum steps, out[1..5] = count per status.
 cudaError_t launch_stats(const DevState& S, uint32_t num_vms, unsigned long long* out, cudaStream_t stream);
 

@@ -334,9 +334,23 @@ __global__ void __launch_bounds__(128, 7) k_persist_gl(DevState S, Params P, Que
   const uint32_t lt = (1u << lane) - 1u;
   Hist h;
   h.zero();
+  // A compacted queue (budget rounds): its length is read on the device, and
+  // the first chunk of every warp is assigned statically, interleaved across
+  // CTAs (warp w of CTA c takes chunk w * gridDim.x + c), so that a queue
+  // shorter than the resident lanes is spread evenly over the SMs instead of
+  // going to whichever warps win the first atomics. Later chunks are claimed
+  // dynamically past the statically assigned ones; there is no one-at-a-time
+  // tail phase.
+  const bool stat = Q.dcount != nullptr;
+  const uint32_t claim_off = stat ? gridDim.x * blockDim.x : 0u;
+  if (stat) {
+    Q.count = *Q.dcount;
+    Q.soft_end = Q.count;
+  }
   // warp chunk [cpos, cend) of main-phase queue positions
   uint32_t tick = 0;
-  if (lane == 0) tick = atomicAdd(Q.head, 32u);
+  if (stat) tick = (((uint32_t)threadIdx.x >> 5) * gridDim.x + blockIdx.x) * 32u;
+  else if (lane == 0) tick = atomicAdd(Q.head, 32u);
   uint32_t cpos = __shfl_sync(FULL, tick, 0);
   uint32_t cend = cpos < Q.soft_end ? min(cpos + 32u, Q.soft_end) : cpos;
   bool tail = cpos >= Q.soft_end;  // warp-uniform: main positions used up
@@ -398,7 +412,7 @@ __global__ void __launch_bounds__(128, 7) k_persist_gl(DevState S, Params P, Que
         cpos += took;
         needm = __ballot_sync(FULL, pf == PF_EMPTY);
         if (cpos >= cend) {      // chunk used up: take the next one
-          if (!inflight && lane == 0) tick = atomicAdd(Q.head, 32u);
+          if (!inflight && lane == 0) tick = claim_off + atomicAdd(Q.head, 32u);
           inflight = false;
           cpos = __shfl_sync(FULL, tick, 0);
           if (cpos >= Q.soft_end) {
@@ -411,7 +425,7 @@ __global__ void __launch_bounds__(128, 7) k_persist_gl(DevState S, Params P, Que
       }
       // claim the next chunk early so its atomic is in flight while this one drains
       if (!tail && !inflight && cend - cpos <= 16u && cend < Q.soft_end) {
-        if (lane == 0) tick = atomicAdd(Q.head, 32u);
+        if (lane == 0) tick = claim_off + atomicAdd(Q.head, 32u);
         inflight = true;
       }
     }
@@ -548,6 +562,76 @@ __global__ void __launch_bounds__(256) k_stats(DevState S, uint32_t num_vms, uns
   }
 }
 
+// ------------------------------------------------------------------ compaction between budget rounds
+// The ids of the VMs at positions [0, count) of `ids` whose status is still
+// RUNNING, written densely to out[0 .. *out_count) (warp-aggregated; order
+// within the output is not specified). *out_count must be zero on entry.
+__global__ void __launch_bounds__(256) k_compact(const uint32_t* __restrict__ ids, uint32_t count,
+                                                 const uint8_t* __restrict__ status, uint32_t* __restrict__ out,
+                                                 uint32_t* __restrict__ out_count) {
+  const uint32_t lane = threadIdx.x & 31u;
+  const uint32_t stride = gridDim.x * blockDim.x;
+  for (uint32_t base = blockIdx.x * blockDim.x; base < count; base += stride) {
+    const uint32_t q = base + threadIdx.x;
+    uint32_t v = 0;
+    bool run = false;
+    if (q < count) {
+      v = ids[q];
+      run = status[v] == ST_RUNNING;
+    }
+    const uint32_t m = __ballot_sync(FULL, run);
+    uint32_t first = 0;
+    if (lane == 0 && m) first = atomicAdd(out_count, (uint32_t)__popc(m));
+    first = __shfl_sync(FULL, first, 0);
+    if (run) out[first + __popc(m & ((1u << lane) - 1u))] = v;
+  }
+}
+
+// ------------------------------------------------------------------ halting-time histogram
+// Sec. 3 (Fig. 1b): the distribution of tau_h, the number of steps after
+// which a machine reached its fixed point, over the HALTED machines of the
+// batch. counts[k] += number of HALTED VMs with edges[k] <= steps < edges[k+1];
+// other[0..3] += RUNNING, TIMEOUT, faulted (either kind), and HALTED VMs
+// outside [edges[0], edges[nbins]). Per-block shared-memory counters, one
+// global atomic per non-empty bin per block.
+__global__ void __launch_bounds__(256) k_tau_hist(const uint64_t* __restrict__ steps,
+                                                  const uint8_t* __restrict__ status, uint32_t num_vms,
+                                                  const uint64_t* __restrict__ edges, uint32_t nbins,
+                                                  unsigned long long* __restrict__ counts,
+                                                  unsigned long long* __restrict__ other) {
+  extern __shared__ __align__(16) uint64_t se[];       // nbins + 1 edges, then nbins u32 counters
+  uint32_t* sc = reinterpret_cast<uint32_t*>(se + nbins + 1);
+  __shared__ uint32_t so[4];
+  for (uint32_t k = threadIdx.x; k <= nbins; k += blockDim.x) se[k] = edges[k];
+  for (uint32_t k = threadIdx.x; k < nbins; k += blockDim.x) sc[k] = 0u;
+  if (threadIdx.x < 4) so[threadIdx.x] = 0u;
+  __syncthreads();
+  const uint64_t lo = se[0], hi = se[nbins];
+  for (uint32_t v = blockIdx.x * blockDim.x + threadIdx.x; v < num_vms; v += gridDim.x * blockDim.x) {
+    const uint32_t st = status[v];
+    if (st == ST_HALTED) {
+      const uint64_t t = steps[v];
+      if (t < lo || t >= hi) {
+        atomicAdd(&so[3], 1u);
+      } else {
+        uint32_t a = 0, b = nbins;                      // se[a] <= t < se[b]
+        while (b - a > 1u) {
+          const uint32_t m = (a + b) >> 1;
+          if (se[m] <= t) a = m;
+          else b = m;
+        }
+        atomicAdd(&sc[a], 1u);
+      }
+    } else {
+      atomicAdd(&so[st == ST_RUNNING ? 0 : (st == ST_TIMEOUT ? 1 : 2)], 1u);
+    }
+  }
+  __syncthreads();
+  for (uint32_t k = threadIdx.x; k < nbins; k += blockDim.x)
+    if (sc[k]) atomicAdd(&counts[k], (unsigned long long)sc[k]);
+  if (threadIdx.x < 4 && so[threadIdx.x]) atomicAdd(&other[threadIdx.x], (unsigned long long)so[threadIdx.x]);
+}
+
 // ------------------------------------------------------------------ launchers
 namespace {
 
@@ -682,9 +766,9 @@ int persist_configure(const StepVariant& var, PersistShape& sh) {
 
 cudaError_t launch_persist(const StepVariant& var, const DevState& S, const Params& P, const Queue& Q,
                            const PersistShape& sh, cudaStream_t stream) {
-  if (!Q.count || !sh.grid) return cudaSuccess;
+  if ((!Q.count && !Q.dcount) || !sh.grid) return cudaSuccess;
   uint32_t grid = sh.grid;
-  const uint32_t warps_needed = (Q.count + 31u) / 32u;
+  const uint32_t warps_needed = (Q.count + 31u) / 32u;   // with dcount, Q.count is an upper bound
   const uint32_t max_useful = (warps_needed + sh.warps - 1u) / sh.warps;
   if (grid > max_useful) grid = max_useful;
   // the last (resident lanes) positions are the tail: served one VM at a
@@ -697,6 +781,34 @@ cudaError_t launch_persist(const StepVariant& var, const DevState& S, const Para
                                                                  sh.refill_min);
   else
     pick_global(var)<<<grid, 32u * sh.warps, 0, stream>>>(S, P, q, sh.epoch);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_tau_hist(const DevState& S, uint32_t num_vms, const uint64_t* edges, uint32_t nbins,
+                            unsigned long long* counts, unsigned long long* other, cudaStream_t stream) {
+  cudaError_t e = cudaMemsetAsync(counts, 0, 8ull * nbins, stream);
+  if (e == cudaSuccess) e = cudaMemsetAsync(other, 0, 8 * 4, stream);
+  if (e != cudaSuccess || !num_vms) return e;
+  const size_t smem = 8ull * (nbins + 1) + 4ull * nbins;
+  if (smem > 48u * 1024u) {
+    e = cudaFuncSetAttribute(k_tau_hist, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+  }
+  uint32_t blocks = (num_vms + 255u) / 256u;
+  const uint32_t cap = (uint32_t)num_sms() * 4u;
+  if (blocks > cap) blocks = cap;
+  k_tau_hist<<<blocks, 256, smem, stream>>>(S.steps, S.status, num_vms, edges, nbins, counts, other);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_compact(const uint32_t* ids, uint32_t count, const uint8_t* status, uint32_t* out,
+                           uint32_t* out_count, cudaStream_t stream) {
+  cudaError_t e = cudaMemsetAsync(out_count, 0, sizeof(uint32_t), stream);
+  if (e != cudaSuccess || !count) return e;
+  uint32_t blocks = (count + 255u) / 256u;
+  const uint32_t cap = (uint32_t)num_sms() * 8u;
+  if (blocks > cap) blocks = cap;
+  k_compact<<<blocks, 256, 0, stream>>>(ids, count, status, out, out_count);
   return cudaGetLastError();
 }
 

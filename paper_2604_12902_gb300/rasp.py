@@ -61,8 +61,8 @@ class RaspError(RuntimeError):
 _lib = None
 EXPORTS = ["rasp_batch_bytes", "rasp_batch_create", "rasp_load_programs", "rasp_load_inputs",
            "rasp_reset", "rasp_run", "rasp_sync", "rasp_read_state", "rasp_load_state",
-           "rasp_read_stats", "rasp_describe", "rasp_autotune", "rasp_batch_destroy", "rasp_last_error",
-           "rasp_version"]
+           "rasp_read_stats", "rasp_describe", "rasp_autotune", "rasp_halting_histogram",
+           "rasp_batch_destroy", "rasp_last_error", "rasp_version"]
 
 
 def lib():
@@ -86,11 +86,12 @@ def lib():
         L.rasp_read_stats.argtypes = [P, ctypes.POINTER(rasp_stats)]
         L.rasp_describe.argtypes = [P, ctypes.c_char_p, U64]
         L.rasp_autotune.argtypes = [P, U64, U32]
+        L.rasp_halting_histogram.argtypes = [P, P, U32, P, P]
         L.rasp_batch_destroy.argtypes = [P]
         L.rasp_batch_destroy.restype = None
         L.rasp_last_error.restype = ctypes.c_char_p
         L.rasp_version.restype = ctypes.c_char_p
-        for name in EXPORTS[:12]:
+        for name in EXPORTS[:13]:
             getattr(L, name).restype = I
         _lib = L
     return _lib
@@ -174,6 +175,12 @@ def rasp_describe(h) -> dict:
 
 def rasp_autotune(h, max_steps: int = U64_MAX, reps: int = 2):
     _check(lib().rasp_autotune(h, int(max_steps) & U64_MAX, reps))
+
+
+def rasp_halting_histogram(h, edges, counts, other=None):
+    """Device histogram of tau_h over HALTED VMs; counts[k] for
+    edges[k] <= steps < edges[k+1] (uint64 arrays); other[4] optional."""
+    return _check(lib().rasp_halting_histogram(h, _p(edges), len(edges) - 1, _p(counts), _p(other)))
 
 
 def rasp_batch_destroy(h):
@@ -276,6 +283,16 @@ class Batch:
 
     def describe(self) -> dict:
         return rasp_describe(self.h)
+
+    def halting_histogram(self, edges):
+        """(counts per bin, other) of the halting times: counts[k] = HALTED VMs
+        with edges[k] <= steps < edges[k+1]; other = [running, timeout,
+        faulted, halted outside the edges]."""
+        e = np.ascontiguousarray(edges, dtype=np.uint64)
+        counts = np.zeros(len(e) - 1, np.uint64)
+        other = np.zeros(4, np.uint64)
+        rasp_halting_histogram(self.h, e, counts, other)
+        return counts, other
 
     def autotune(self, max_steps: int = U64_MAX, reps: int = 2) -> dict:
         """Time the candidate schedules on this batch (state unchanged) and

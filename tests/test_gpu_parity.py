@@ -222,6 +222,31 @@ def test_reset_repacks_shared_programs(rasp):
     assert_same_state(got, full, wl.ell, wl.s, what="shared reset+run")
 
 
+@pytest.mark.parametrize("w", [64, 32])
+def test_long_runs_across_budget_rounds(rasp, w):
+    """Countdown loops of up to ~320,000 steps with mixed caps (some VMs time
+    out): the persistent schedule runs them in budget rounds with the still-
+    running VMs compacted between rounds; one run, and a run split at budgets
+    that fall inside rounds, both equal the oracle."""
+    rng = np.random.default_rng(21)
+    V = 2048
+    progs, tapes = [], []
+    for v in range(V):
+        T = int(rng.integers(1, 40_000))
+        progs.append(asm((LOD, T), (STO, 40), (LOD, 0), (ADD, 40), (BNZ, 12), (0, 0),
+                         (LOD, -1), (ADD, 40), (STO, 40), (LOD, 1), (BNZ, 4), (PRI, 40)))
+        tapes.append([])
+    caps = rng.integers(1_000, 400_000, size=V).astype(np.uint64)
+    caps[::7] = U64                                   # some VMs uncapped
+    wl = wl_from(progs, tapes, 64, caps, 0, 2, w=w, name="countdown")
+    full, _ = oracle_state(wl, threads=THREADS)
+    assert (full.status == 2).any() and (full.status == 1).any()
+    got, _ = run_gpu(rasp, wl, SCHEDS["persist_gl"])
+    assert_same_state(got, full, wl.ell, wl.s, what="rounds w=%d" % w)
+    got, _ = run_gpu(rasp, wl, 0, steps_split=[3_000, 50_000, 200_001])
+    assert_same_state(got, full, wl.ell, wl.s, what="rounds split w=%d" % w)
+
+
 def test_checkpoint_restore_roundtrip(rasp):
     wl = W.template_programs(num_vms=3000, seed=9)
     full, _ = oracle_state(wl)

@@ -1,0 +1,88 @@
+"""The uniform program sampler of the halting experiment (Sec. 3) against
+brute force: its string counts equal an explicit enumeration of the Sec. 2.2
+grammar (every enumerated string accepted by the independent parser of
+dsl.py), every sample has exactly L tokens and parses back to itself, and on
+a small space the samples are uniform (chi-square)."""
+import numpy as np
+import pytest
+
+from paper_2604_12902_gb300 import dsl, sampler as S
+
+REFG = [(a, "[", str(z), "]") for a in ("ipt", "scr", "opt") for z in range(10)]
+REFP = [(a, "[", str(z), "]") for a in ("scr", "opt") for z in range(10)]
+Z = [(str(z),) for z in range(10)]
+
+
+def enumerate_grammar(maxlen):
+    """All token strings of E, S, B by length, written out from the grammar."""
+    E = {1: list(Z), 4: list(REFG)}
+    E[6] = [g + (op,) + z for g in REFG for op in "+*" for z in Z]
+    E[9] = [g + (op,) + h for g in REFG for op in "+*" for h in REFG]
+    Sx, Bx = {}, {}
+    for l in range(1, maxlen + 1):
+        out = []
+        for p in REFP:
+            out += [p + ("=",) + e for e in E.get(l - 5, [])]
+        for k in range(1, l - 9):
+            for g in REFG:
+                out += [("ife",) + g + ("{",) + b1 + ("}", "{") + b2 + ("}",)
+                        for b1 in Bx.get(k, []) for b2 in Bx.get(l - 9 - k, [])]
+        for g in REFG:
+            out += [("whl",) + g + ("{",) + b + ("}",) for b in Bx.get(l - 7, [])]
+        Sx[l] = out
+        blk = list(out) + ([("hlt",)] if l == 1 else [])
+        for k in range(1, l - 1):
+            blk += [s + (";",) + b for s in Sx.get(k, []) for b in Bx.get(l - k - 1, [])]
+        Bx[l] = blk
+    return Sx, Bx
+
+
+def test_counts_equal_explicit_enumeration_and_parse():
+    maxlen = 15
+    Sx, Bx = enumerate_grammar(maxlen)
+    _, cS, cB = S._counts(maxlen)
+    for l in range(1, maxlen + 1):
+        assert len(set(Bx[l])) == len(Bx[l]) == cB[l], l
+        assert len(Sx[l]) == cS[l], l
+    for body in Bx[13][::97] + Bx[15][::211]:
+        src = "fun f0 ( ipt : W ^ 2 ) -> W ^ 1 { " + " ".join(body) + " }"
+        dsl.parse(src)                       # the independent parser accepts it
+    assert S.count_programs(15 + 13, ell=10, s=2) == 9 * 2 * len(Bx[13])
+    assert S.count_programs(15 + 13, ell=3, s=1) == 3 * 1 * len(Bx[13])
+
+
+@pytest.mark.parametrize("L", [16, 40, 100])
+def test_samples_have_L_tokens_and_parse_back(L):
+    for k in range(60):
+        f = S.sample_fun(L, seed=3, pid=k)
+        toks = S.fun_tokens(f)
+        assert len(toks) == L
+        g = dsl.parse(" ".join(toks))
+        assert (g.arity, g.out_arity, g.body) == (f.arity, f.out_arity, f.body)
+        assert 1 <= f.arity <= 9 and 1 <= f.out_arity <= 2
+
+
+def test_uniform_on_a_small_space():
+    L = 21                                   # 9 x 2 x 200 = 3,600 programs
+    n = S.count_programs(L)
+    assert n == 3600
+    draws = 36000
+    seen = {}
+    for k in range(draws):
+        key = tuple(S.fun_tokens(S.sample_fun(L, seed=11, pid=k)))
+        seen[key] = seen.get(key, 0) + 1
+    assert len(seen) == n                    # every program reached
+    exp = draws / n
+    chi2 = sum((c - exp) ** 2 / exp for c in seen.values())
+    dof = n - 1
+    assert abs(chi2 - dof) < 5 * (2 * dof) ** 0.5, chi2
+
+
+def test_deterministic_and_chunked_generation_equal():
+    a = S.halting_programs(300, L=60, seed=5)
+    b = S.concat([S.halting_programs(100, L=60, seed=5, first=o) for o in (0, 100, 200)])
+    for f in ("programs", "prog_off", "tapes", "tape_off", "caps", "mem_words"):
+        assert np.array_equal(getattr(a, f), getattr(b, f)), f
+    lens = a.prog_off[1:] - a.prog_off[:-1]
+    assert (lens % 2 == 0).all() and (lens // 2 * 2 + 5 + 10 + 2 + 10 <= 250).all()
+    assert (a.tapes >= 0).all() and (a.tapes < 2 ** 32).all()

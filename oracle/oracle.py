@@ -37,7 +37,11 @@ _lib = None
 
 class _Params(ctypes.Structure):
     _fields_ = [("w", ctypes.c_uint32), ("checked", ctypes.c_uint32),
-                ("ell", ctypes.c_uint64), ("s", ctypes.c_uint64)]
+                ("ell", ctypes.c_uint64), ("s", ctypes.c_uint64),
+                ("isa", ctypes.c_uint32), ("pad", ctypes.c_uint32)]
+
+
+ISA_WORD, ISA_CLASSIC = 0, 1
 
 
 def build(force: bool = False) -> str:
@@ -90,8 +94,9 @@ def _u64(x) -> np.ndarray:
 class State:
     """Configurations of a batch of machines, in the paper's layout."""
 
-    def __init__(self, w, checked, ell, s, n, mem_off, mem, i, a, u, y, steps, status):
+    def __init__(self, w, checked, ell, s, n, mem_off, mem, i, a, u, y, steps, status, classic=False):
         self.w, self.checked, self.ell, self.s = int(w), bool(checked), int(ell), int(s)
+        self.classic = bool(classic)
         self.n, self.mem_off, self.mem = n, mem_off, mem
         self.i, self.a, self.u, self.y = i, a, u, y
         self.steps, self.status = steps, status
@@ -101,7 +106,8 @@ class State:
         return int(self.n.shape[0])
 
     def params(self) -> _Params:
-        return _Params(self.w, 1 if self.checked else 0, self.ell, self.s)
+        return _Params(self.w, 1 if self.checked else 0, self.ell, self.s,
+                       ISA_CLASSIC if self.classic else ISA_WORD, 0)
 
     def memory(self, v: int) -> np.ndarray:
         o = int(self.mem_off[v])
@@ -110,13 +116,14 @@ class State:
     def copy(self) -> "State":
         return State(self.w, self.checked, self.ell, self.s, self.n.copy(), self.mem_off.copy(),
                      self.mem.copy(), self.i.copy(), self.a.copy(), self.u.copy(),
-                     self.y.copy(), self.steps.copy(), self.status.copy())
+                     self.y.copy(), self.steps.copy(), self.status.copy(), self.classic)
 
 
 def pack(programs, prog_off, n, tapes, tape_off, ell: int, s: int,
-         w: int = 64, checked: bool = False) -> State:
+         w: int = 64, checked: bool = False, classic: bool = False) -> State:
     """c_0(P, x) for every VM (Sec. 2.1). ``programs``/``tapes`` are flat word
-    arrays with ``*_off`` prefix offsets (length V+1); ``n`` is per-VM memory."""
+    arrays with ``*_off`` prefix offsets (length V+1); ``n`` is per-VM memory.
+    ``classic`` selects the classic opcode set (Sec. 1.1: SUB, BPA)."""
     lib = _load()
     n = _u64(n)
     V = n.shape[0]
@@ -131,7 +138,7 @@ def pack(programs, prog_off, n, tapes, tape_off, ell: int, s: int,
     st = State(w, checked, ell, s, n, mem_off, mem,
                np.zeros(V, np.uint64), np.zeros(V, np.uint64),
                np.zeros(max(V * (ell + 1), 1), np.uint64), np.zeros(max(V * (s + 1), 1), np.uint64),
-               np.zeros(V, np.uint64), np.zeros(V, np.uint8))
+               np.zeros(V, np.uint64), np.zeros(V, np.uint8), classic)
     p = st.params()
     rc = lib.ro_pack(ctypes.byref(p), V, _ptr(n), _ptr(mem_off), _ptr(mem), _ptr(prog), _ptr(po),
                      _ptr(tape), _ptr(to), _ptr(st.i), _ptr(st.a), _ptr(st.u), _ptr(st.y),
@@ -175,11 +182,12 @@ def run(st: State, caps=None, budget: int = U64_MAX, hist: bool = False,
     return None
 
 
-def step_one(w: int, ell: int, s: int, i: int, a: int, M, u, y, checked: bool = False):
+def step_one(w: int, ell: int, s: int, i: int, a: int, M, u, y, checked: bool = False,
+             classic: bool = False):
     """One transition of one machine. Returns (kind, i, a, M, u, y) with kind
     0 = applied, 1 = fixed point, 2 = address fault, 3 = overflow fault."""
     lib = _load()
-    p = _Params(w, 1 if checked else 0, ell, s)
+    p = _Params(w, 1 if checked else 0, ell, s, ISA_CLASSIC if classic else ISA_WORD, 0)
     ii = np.array([i & U64_MAX], np.uint64)
     aa = np.array([a & U64_MAX], np.uint64)
     MM, uu, yy = _u64(list(M)).copy(), _u64(list(u)).copy(), _u64(list(y)).copy()
@@ -189,8 +197,8 @@ def step_one(w: int, ell: int, s: int, i: int, a: int, M, u, y, checked: bool = 
 
 
 def run_packed(programs, prog_off, n, tapes, tape_off, ell, s, caps=None, budget=U64_MAX,
-               w=64, checked=False, hist=False, threads=1):
+               w=64, checked=False, hist=False, threads=1, classic=False):
     """pack + run in one call; returns (State, hist or None)."""
-    st = pack(programs, prog_off, n, tapes, tape_off, ell, s, w=w, checked=checked)
+    st = pack(programs, prog_off, n, tapes, tape_off, ell, s, w=w, checked=checked, classic=classic)
     h = run(st, caps=caps, budget=budget, hist=hist, threads=threads)
     return st, h

@@ -16,6 +16,9 @@
  *   Sec. 2.1  the one-step transition (case equation, opcodes 1 LOD .. 7 PRI,
  *             "otherwise" = identity) and the halting set F = {c : c -> c};
  *   Sec. 3    halting number tau_h = least tau with Phi^tau(c0) = Phi^(tau+1)(c0).
+ *   Sec. 1.1  the classic RASP opcode set, selected by `isa`: opcode 3 is SUB
+ *             (a - M_j) and opcode 5 is BPA (jump when a > 0); the word
+ *             machine of Sec. 2.1 has MUL and BNZ there.
  *
  * Readings of the paper taken here (each is listed in the design notes):
  *   - u[0] is the read head and u[1..l] the zero-padded input; y[0] is the
@@ -34,9 +37,13 @@
  *   - CHECKED semantics (no counterpart in the paper; parity unpinned by the
  *     paper): memory is not circular and arithmetic is signed 64-bit.
  *     Order: (1) fetch range, i in [0, n-1) else FAULT_ADDR; (2) fixed point
- *     -> HALTED; (3) operand range, j in [0, n) for ADD, MUL, STO, PRI and for
- *     RD when it fires, else FAULT_ADDR; (4) signed overflow of ADD or MUL ->
- *     FAULT_OVERFLOW. A faulting step is neither applied nor counted.
+ *     -> HALTED; (3) operand range, j in [0, n) for ADD, MUL/SUB, STO, PRI and
+ *     for RD when it fires, else FAULT_ADDR; (4) signed overflow of ADD or
+ *     MUL/SUB -> FAULT_OVERFLOW. A faulting step is neither applied nor counted.
+ *   - Classic opcode set on w-bit words (Sec. 1.1 states it over the
+ *     integers): SUB is a - M_j modulo 2^w, and BPA's "a > 0" reads the w-bit
+ *     word a as a two's complement integer, so it jumps iff
+ *     1 <= a <= 2^(w-1) - 1. Everything else is the word machine's.
  */
 #include <stdint.h>
 #include <stddef.h>
@@ -52,7 +59,11 @@ typedef struct {
     uint32_t checked;  /* 0: the paper's wrapping machine, 1: CHECKED */
     uint64_t ell;      /* l, input tape capacity                    */
     uint64_t s;        /* s, output tape capacity                   */
+    uint32_t isa;      /* RO_ISA_WORD (Sec. 2.1) or RO_ISA_CLASSIC (Sec. 1.1) */
+    uint32_t pad;
 } ro_params;
+
+enum { RO_ISA_WORD = 0, RO_ISA_CLASSIC = 1 };
 
 /* One machine, viewed in place. */
 typedef struct {
@@ -76,6 +87,14 @@ static uint64_t word_mask(uint32_t w) {
 
 static uint64_t min_u64(uint64_t x, uint64_t y) { return x < y ? x : y; }
 
+/* Does opcode 5 jump? BNZ: a != 0. BPA: a > 0, with a read as a w-bit two's
+   complement integer (its top bit w-1 is the sign). */
+static int branch_taken(const ro_params *p, uint64_t a) {
+    if (p->isa != RO_ISA_CLASSIC) return a != 0;
+    const int negative = (int)((a >> (p->w - 1)) & 1);
+    return a != 0 && !negative;
+}
+
 /* c -> c' (Sec. 2.1 case equation), wrapping semantics. */
 static void successor(const ro_params *p, const ro_vm *c, ro_succ *s) {
     const uint64_t mask = word_mask(p->w);
@@ -97,15 +116,19 @@ static void successor(const ro_params *p, const ro_vm *c, ro_succ *s) {
     case 2:  /* ADD: <i (+) 2, a (+) M_{j mod n}, M, u, y> */
         s->i = i_next; s->a = (a + c->M[k]) & mask;
         break;
-    case 3:  /* MUL: <i (+) 2, a (x) M_{j mod n}, M, u, y> */
-        s->i = i_next; s->a = (a * c->M[k]) & mask;
+    case 3:
+        if (p->isa == RO_ISA_CLASSIC) {   /* SUB: <i (+) 2, a - M_{j mod n}, M, u, y> */
+            s->i = i_next; s->a = (a - c->M[k]) & mask;
+        } else {                          /* MUL: <i (+) 2, a (x) M_{j mod n}, M, u, y> */
+            s->i = i_next; s->a = (a * c->M[k]) & mask;
+        }
         break;
     case 4:  /* STO: <i (+) 2, a, M_{j mod n} <- a, u, y> */
         s->i = i_next;
         s->m_set = 1; s->m_idx = k; s->m_val = a;
         break;
-    case 5:  /* BNZ: <j, a, M, u, y> if a != 0, else <i (+) 2, a, M, u, y> */
-        s->i = (a != 0) ? j : i_next;
+    case 5:  /* BNZ (BPA): <j, a, M, u, y> if a != 0 (a > 0), else <i (+) 2, a, M, u, y> */
+        s->i = branch_taken(p, a) ? j : i_next;
         break;
     case 6:  /* RD, only when u_0 < l:
                 <i (+) 2, a, M_{j mod n} <- u-bullet, u-triangle, y> */
@@ -167,7 +190,8 @@ static int classify(const ro_params *p, const ro_vm *c, ro_succ *s) {
             const int64_t x = (int64_t)*c->a, y = (int64_t)c->M[j];
             int64_t r;
             const int ovf = (o == 2) ? __builtin_add_overflow(x, y, &r)
-                                     : __builtin_mul_overflow(x, y, &r);
+                          : (p->isa == RO_ISA_CLASSIC) ? __builtin_sub_overflow(x, y, &r)
+                                                       : __builtin_mul_overflow(x, y, &r);
             if (ovf) return K_FAULT_OVERFLOW;
         }
     }
@@ -246,7 +270,7 @@ int ro_run(const ro_params *p, uint64_t first, uint64_t count,
             if (hist) {
                 hist[s.op] += 1;
                 if (s.op == 7 && !s.y_set) hist[8] += 1;
-                if (s.op == 5 && *c.a != 0) hist[0] += 1;
+                if (s.op == 5 && branch_taken(p, *c.a)) hist[0] += 1;
             }
             apply(&c, &s);
             steps[v] += 1;

@@ -10,6 +10,10 @@ paper defines no faults).
 
 Configuration: ``(i, a, M, u, y)`` with ``M`` of length n, ``u`` of length
 l+1 (u[0] the read head) and ``y`` of length s+1 (y[0] the output count).
+
+``classic=True`` takes the opcode set of the classic RASP (Sec. 1.1) on the
+same words: opcode 3 is SUB, a - M_j modulo 2^w, and opcode 5 is BPA, which
+jumps when a > 0 with a read as a w-bit two's complement integer.
 """
 from __future__ import annotations
 
@@ -30,8 +34,9 @@ def _set(t: tuple, k: int, v: int) -> tuple:
     return tuple(v if idx == k else t[idx] for idx in range(len(t)))
 
 
-def step(c, ell: int, s: int, w: int):
-    """The one-step transition operator of Sec. 2.1."""
+def step(c, ell: int, s: int, w: int, classic: bool = False):
+    """The one-step transition operator of Sec. 2.1 (Sec. 1.1's opcodes 3
+    and 5 with ``classic``)."""
     i, a, M, u, y = c
     mod = 1 << w
     n = len(M)
@@ -42,13 +47,17 @@ def step(c, ell: int, s: int, w: int):
         return (inc, j, M, u, y)
     if o == 2:
         return (inc, (a + M[j % n]) % mod, M, u, y)
+    if o == 3 and classic:
+        return (inc, (a - M[j % n]) % mod, M, u, y)
     if o == 3:
         return (inc, (a * M[j % n]) % mod, M, u, y)
     if o == 4:
         return (inc, a, _set(M, j % n, a), u, y)
-    if o == 5 and a != 0:
+    signed_a = a - mod if a >= mod // 2 else a
+    jumps = (signed_a > 0) if classic else (a != 0)
+    if o == 5 and jumps:
         return (j, a, M, u, y)
-    if o == 5 and a == 0:
+    if o == 5:
         return (inc, a, M, u, y)
     if o == 6 and u[0] < ell:
         bullet = u[min(u[0] + 1, ell)]
@@ -64,12 +73,12 @@ def step(c, ell: int, s: int, w: int):
     return c
 
 
-def run(c, ell: int, s: int, w: int, cap: int):
+def run(c, ell: int, s: int, w: int, cap: int, classic: bool = False):
     """Iterate until a fixed point or ``cap`` applied steps.
     Returns (c, steps, status) with status 1 = HALTED, 2 = TIMEOUT."""
     steps = 0
     while True:
-        nxt = step(c, ell, s, w)
+        nxt = step(c, ell, s, w, classic)
         if nxt == c:
             return c, steps, 1
         if steps >= cap:

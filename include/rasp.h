@@ -79,6 +79,13 @@ enum rasp_semantics {
 #define RASP_SHARED_PROGRAM    0x2000u /* programs indexed by prog_of_vm       */
 #define RASP_CUDA_GRAPH        0x4000u /* rasp_run replays a CUDA graph captured
                                           once per budget (cached, up to 8)   */
+#define RASP_ISA_CLASSIC       0x8000u /* the classic RASP opcode set (Sec. 1.1)
+                                          on the same words: opcode 3 is SUB
+                                          (a - M_j mod 2^w), opcode 5 is BPA
+                                          (jump when a > 0, a read as a w-bit
+                                          two's complement integer). Plain and
+                                          HBM-slab persistent schedules, select
+                                          dispatch (EINVAL otherwise)          */
 
 typedef struct rasp_config {
     uint32_t word_bits;  /* w, 2..64 (64 for RASP_CHECKED)                     */

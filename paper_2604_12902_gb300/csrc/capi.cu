@@ -131,6 +131,12 @@ int validate_config(const rasp_config* cfg, uint64_t num_vms, const uint32_t* me
   if (sched != RASP_SCHED_AUTO && sched != RASP_SCHED_PLAIN && sched != RASP_SCHED_PERSIST &&
       sched != RASP_SCHED_PERSIST_GL && sched != RASP_SCHED_SHARED)
     return fail(RASP_EINVAL, "unknown schedule flag 0x%x", sched);
+  if (cfg->flags & RASP_ISA_CLASSIC) {
+    if (sched != RASP_SCHED_AUTO && sched != RASP_SCHED_PLAIN && sched != RASP_SCHED_PERSIST_GL)
+      return fail(RASP_EINVAL, "the classic opcode set runs on the plain and HBM-slab persistent schedules only");
+    if (cfg->flags & RASP_DISPATCH_VOTE)
+      return fail(RASP_EINVAL, "the classic opcode set uses the select dispatch only");
+  }
   if (cfg->word_bits < 64) {
     const uint64_t lim = 1ull << cfg->word_bits;
     if (cfg->in_cap >= lim || cfg->out_cap >= lim)
@@ -188,6 +194,7 @@ StepVariant variant_of(const rasp_batch* b) {
   v.checked = b->cfg.semantics == RASP_CHECKED;
   v.hist = (b->cfg.flags & RASP_COLLECT_STATS) != 0;
   v.vote = (b->cfg.flags & RASP_DISPATCH_VOTE) != 0;
+  v.classic = (b->cfg.flags & RASP_ISA_CLASSIC) != 0;
   return v;
 }
 
@@ -904,8 +911,10 @@ int rasp_autotune(rasp_batch* b, uint64_t max_steps, uint32_t reps) {
       {"persist_gl e256 w4", RASP_SCHED_PERSIST_GL, 256, 4}, {"persist_gl e128 w2", RASP_SCHED_PERSIST_GL, 128, 2},
       {"plain", RASP_SCHED_PLAIN, 0, 0},                     {"persist_smem e32 w1", RASP_SCHED_PERSIST, 32, 1},
       {"shared", RASP_SCHED_SHARED, 0, 0}};
-  // the shared-program schedule is a candidate only when programs are shared
-  const int ncand = (int)(sizeof(cands) / sizeof(cands[0])) - (b->shared_programs ? 0 : 1);
+  // the shared-program schedule is a candidate only when programs are shared;
+  // the classic opcode set runs on the HBM-slab persistent and plain schedules only
+  const bool classic = (b->cfg.flags & RASP_ISA_CLASSIC) != 0;
+  const int ncand = classic ? 5 : (int)(sizeof(cands) / sizeof(cands[0])) - (b->shared_programs ? 0 : 1);
   const rasp_config saved = b->cfg;
   cudaEvent_t e0, e1;
   cudaEventCreate(&e0);

@@ -103,6 +103,15 @@ __device__ __forceinline__ uint32_t mod_n(uint64_t x, uint32_t n) {
   return (x < (uint64_t)n) ? (uint32_t)x : mod_n_slow(x, n);
 }
 
+// Opcode 5's condition: BNZ (word machine, Sec. 2.1) jumps when a != 0; BPA
+// (classic opcode set, Sec. 1.1) when a > 0, with the w-bit word a read as a
+// two's complement integer: 1 <= a <= 2^(w-1) - 1 = wm >> 1.
+template <bool CLASSIC>
+__device__ __forceinline__ bool jumps(uint64_t a, uint64_t wm) {
+  if constexpr (CLASSIC) return (a - 1ull) < (wm >> 1);
+  else return a != 0ull;
+}
+
 __device__ __forceinline__ uint64_t stop_of(const Params& P, const Regs& r) {
   return P.budget < r.cap ? P.budget : r.cap;
 }
@@ -174,7 +183,7 @@ __device__ __noinline__ ulonglong2 fetch_slow(WordPtr M, uint32_t ip, uint32_t n
 // if the transition applies (d filled), else the machine's final status for
 // this run: HALTED (fixed point), a CHECKED fault, or TIMEOUT / RUNNING at
 // the step stop.
-template <bool MASKED, bool CHECKED>
+template <bool MASKED, bool CHECKED, bool CLASSIC = false>
 __device__ __forceinline__ uint32_t decode(uint64_t* __restrict__ M, const Params& P, Regs& r, Decoded& d) {
   const uint64_t wm = MASKED ? P.wmask : ~0ull;
   const uint32_t ip = r.ip, n = r.n;
@@ -201,7 +210,7 @@ __device__ __forceinline__ uint32_t decode(uint64_t* __restrict__ M, const Param
   d.j = j;
   d.jin = j < (uint64_t)n;
   d.op = ((o - 1ull) < 7ull) ? (uint32_t)o : 0u;
-  d.taken = (d.op == 5u) & (r.a != 0ull);
+  d.taken = (d.op == 5u) & jumps<CLASSIC>(r.a, wm);
   // j mod n only where j is an address or a jump target (LOD's j is an
   // immediate, an untaken BNZ ignores it)
   const bool addr = ((d.op >= 2u) & (d.op != 5u)) | d.taken;
@@ -254,22 +263,26 @@ __device__ __forceinline__ void count_step(Hist& h, uint32_t op, bool taken) {
 // One transition, general form: every case of the Sec. 2.1 equation,
 // every guard and every wrap. Returns CONT after applying it, else the final
 // status (see decode).
-template <bool MASKED, bool CHECKED, bool HIST, bool SHARED = false>
+template <bool MASKED, bool CHECKED, bool HIST, bool SHARED = false, bool CLASSIC = false>
 __device__ __forceinline__ uint32_t step_general(uint64_t* __restrict__ M, const uint64_t* __restrict__ T,
                                                  uint64_t* __restrict__ Y, const Params& P, Regs& r, Hist& h,
                                                  uint32_t plen = 0) {
   Decoded d;
-  const uint32_t s = decode<MASKED, CHECKED>(M, P, r, d);
+  const uint32_t s = decode<MASKED, CHECKED, CLASSIC>(M, P, r, d);
   if (s != CONT) return s;
   const uint32_t op = d.op, jm = d.jm;
   const uint64_t a = r.a;
   uint64_t v = 0;
   if ((op == 2u) | (op == 3u)) v = M[jm];
   const uint64_t sum = a + v;
-  const uint64_t prod = a * v;
+  const uint64_t prod = CLASSIC ? a - v : a * v;    // opcode 3: MUL, or SUB in the classic set
   if constexpr (CHECKED) {
     if ((op == 2u) & ((int64_t)((a ^ sum) & (v ^ sum)) < 0)) return ST_FAULT_OVERFLOW;
-    if ((op == 3u) && __mul64hi((long long)a, (long long)v) != ((int64_t)prod >> 63)) return ST_FAULT_OVERFLOW;
+    if constexpr (CLASSIC) {
+      if ((op == 3u) & ((int64_t)((a ^ v) & (a ^ prod)) < 0)) return ST_FAULT_OVERFLOW;
+    } else {
+      if ((op == 3u) && __mul64hi((long long)a, (long long)v) != ((int64_t)prod >> 63)) return ST_FAULT_OVERFLOW;
+    }
   }
   uint64_t na = (op == 1u) ? d.j : a;
   na = (op == 2u) ? sum : na;
@@ -333,19 +346,19 @@ __device__ __forceinline__ void prime(const uint64_t* __restrict__ M, Regs& r) {
 // pair just loaded for the next step (self-modifying code). Precondition
 // (have): i = ip < n, ip even, ip + 1 < n, <co, cj> = <M[ip], M[ip+1]>.
 // Returns 1, and changes nothing, when the step needs the general path.
-#define RASP_FAST_STEP_A \
+#define RASP_FAST_STEP_A1 \
       "{\n\t" \
       ".reg .pred pv, pj, pz, pt, pq, prd, pl, po, pa, px, pk, p1, p2, p3, p6, p7, pw, pp, ph, pg;\n\t" \
       ".reg .b32 op, oh, jm, jh, t0, t1, t2, nip, ip3;\n\t" \
-      ".reg .b64 sx, sy, qx, qy, v, sm, pd, na, w, ad;\n\t" \
+      ".reg .b64 sx, sy, qx, qy, v, sm, pd, na, w, ad, am;\n\t" \
       "mov.b64 {op, oh}, %1;\n\t" \
       "mov.b64 {jm, jh}, %2;\n\t" \
       "add.u32 t0, op, -1;\n\t" \
       "setp.lt.u32 pv, t0, 7;\n\t" \
       "setp.eq.and.u32 pv, oh, 0, pv;\n\t" \
       "setp.lt.u32 pj, jm, %12;\n\t" \
-      "setp.eq.and.u32 pj, jh, 0, pj;\n\t" \
-      "setp.ne.u64 pz, %0, 0;\n\t" \
+      "setp.eq.and.u32 pj, jh, 0, pj;\n\t"
+#define RASP_FAST_STEP_A2 \
       "setp.eq.and.u32 pt, op, 5, pz;\n\t" \
       "add.u32 ip3, %3, 3;\n\t" \
       "setp.lt.u32 pq, ip3, %12;\n\t" \
@@ -362,8 +375,8 @@ __device__ __forceinline__ void prime(const uint64_t* __restrict__ M, Regs& r) {
       "and.b32 t2, jm, 1;\n\t" \
       "setp.ne.u32 po, t2, 0;\n\t" \
       "selp.b64 v, qy, qx, po;\n\t" \
-      "add.u64 sm, %0, v;\n\t" \
-      "mul.lo.u64 pd, %0, v;\n\t" \
+      "add.u64 sm, %0, v;\n\t"
+#define RASP_FAST_STEP_A3 \
       "mov.b32 t1, 0xDC;\n\t" \
       "shr.b32 t1, t1, op;\n\t" \
       "and.b32 t1, t1, 1;\n\t" \
@@ -406,6 +419,12 @@ __device__ __forceinline__ void prime(const uint64_t* __restrict__ M, Regs& r) {
       "@pp st.global.u64 [ad], v;\n\t" \
       "@pg add.u32 %6, %6, 1;\n\t" \
       "@pp add.u32 %7, %7, 1;\n\t"
+// opcode 5's condition (pz) and opcode 3's result (pd): word machine BNZ and
+// MUL; classic set BPA (1 <= a <= 2^(w-1) - 1, %17 = 2^(w-1) - 1) and SUB
+#define RASP_FAST_STEP_PZ_WORD "setp.ne.u64 pz, %0, 0;\n\t"
+#define RASP_FAST_STEP_PD_WORD "mul.lo.u64 pd, %0, v;\n\t"
+#define RASP_FAST_STEP_PZ_CLASSIC "add.u64 am, %0, -1;\n\tsetp.lt.u64 pz, am, %17;\n\t"
+#define RASP_FAST_STEP_PD_CLASSIC "sub.u64 pd, %0, v;\n\t"
 #define RASP_FAST_STEP_B \
       "@pk mov.b64 %0, na;\n\t" \
       "@pk selp.b64 %1, qx, sx, pt;\n\t" \
@@ -422,26 +441,34 @@ __device__ __forceinline__ void prime(const uint64_t* __restrict__ M, Regs& r) {
       "}"
 #define RASP_FAST_STEP_OPERANDS                                                                   \
   : "+l"(a), "+l"(co), "+l"(cj), "+r"(ip), "=r"(rare), "+r"(left), "+r"(u0), "+r"(y0), "+r"(have) \
-  : "l"(M), "l"(T), "l"(Y), "r"(n), "r"(ell), "r"(s), "r"(ilim), "l"(wmask)                      \
+  : "l"(M), "l"(T), "l"(Y), "r"(n), "r"(ell), "r"(s), "r"(ilim), "l"(wmask), "l"(wmask >> 1)     \
   : "memory"
 
-template <bool MASKED>
+template <bool MASKED, bool CLASSIC>
 __device__ __forceinline__ uint32_t fast_step_ptx(uint64_t* M, const uint64_t* T, uint64_t* Y, uint32_t n,
                                                   uint32_t ell, uint32_t s, uint64_t& a, uint64_t& co,
                                                   uint64_t& cj, uint32_t& ip, uint32_t& left, uint32_t& u0,
                                                   uint32_t& y0, uint32_t& have, uint32_t ilim, uint64_t wmask) {
   uint32_t rare;
-  if constexpr (MASKED) {
-    // w < 64: the new accumulator is reduced to w bits; i (+) 2 must stay
-    // below ilim = min(n, 2^w)
-    asm volatile(RASP_FAST_STEP_A "and.b64 na, na, %16;\n\t" RASP_FAST_STEP_B RASP_FAST_STEP_OPERANDS);
+  // w < 64: the new accumulator is reduced to w bits (%16 = 2^w - 1); i (+) 2
+  // must stay below ilim = min(n, 2^w)
+  if constexpr (MASKED && CLASSIC) {
+    asm volatile(RASP_FAST_STEP_A1 RASP_FAST_STEP_PZ_CLASSIC RASP_FAST_STEP_A2 RASP_FAST_STEP_PD_CLASSIC
+                 RASP_FAST_STEP_A3 "and.b64 na, na, %16;\n\t" RASP_FAST_STEP_B RASP_FAST_STEP_OPERANDS);
+  } else if constexpr (MASKED) {
+    asm volatile(RASP_FAST_STEP_A1 RASP_FAST_STEP_PZ_WORD RASP_FAST_STEP_A2 RASP_FAST_STEP_PD_WORD
+                 RASP_FAST_STEP_A3 "and.b64 na, na, %16;\n\t" RASP_FAST_STEP_B RASP_FAST_STEP_OPERANDS);
+  } else if constexpr (CLASSIC) {
+    asm volatile(RASP_FAST_STEP_A1 RASP_FAST_STEP_PZ_CLASSIC RASP_FAST_STEP_A2 RASP_FAST_STEP_PD_CLASSIC
+                 RASP_FAST_STEP_A3 RASP_FAST_STEP_B RASP_FAST_STEP_OPERANDS);
   } else {
-    asm volatile(RASP_FAST_STEP_A RASP_FAST_STEP_B RASP_FAST_STEP_OPERANDS);
+    asm volatile(RASP_FAST_STEP_A1 RASP_FAST_STEP_PZ_WORD RASP_FAST_STEP_A2 RASP_FAST_STEP_PD_WORD
+                 RASP_FAST_STEP_A3 RASP_FAST_STEP_B RASP_FAST_STEP_OPERANDS);
   }
   return rare;
 }
 
-template <bool MASKED, bool CHECKED, bool HIST, bool PIPE, bool SHARED = false>
+template <bool MASKED, bool CHECKED, bool HIST, bool PIPE, bool SHARED = false, bool CLASSIC = false>
 __device__ __forceinline__ uint32_t one_step(uint64_t* __restrict__ M, const uint64_t* __restrict__ T,
                                              uint64_t* __restrict__ Y, const Params& P, Regs& r, Hist& h,
                                              const uint64_t* Pg = nullptr, uint32_t plen = 0) {
@@ -450,8 +477,8 @@ __device__ __forceinline__ uint32_t one_step(uint64_t* __restrict__ M, const uin
     if (r.have) {
       uint64_t co = r.cur.x, cj = r.cur.y;
       uint32_t hv = 1;
-      const uint32_t rare = fast_step_ptx<MASKED>(M, T, Y, n, P.ell, P.s, r.a, co, cj, r.ip, r.left, r.u0, r.y0,
-                                                  hv, MASKED ? r.ilim : n, P.wmask);
+      const uint32_t rare = fast_step_ptx<MASKED, CLASSIC>(M, T, Y, n, P.ell, P.s, r.a, co, cj, r.ip, r.left,
+                                                           r.u0, r.y0, hv, MASKED ? r.ilim : n, P.wmask);
       if (!rare) {
         r.cur.x = co;
         r.cur.y = cj;
@@ -460,7 +487,7 @@ __device__ __forceinline__ uint32_t one_step(uint64_t* __restrict__ M, const uin
       }
     }
     r.have = false;
-    const uint32_t s = step_general<MASKED, CHECKED, HIST, SHARED>(M, T, Y, P, r, h, plen);
+    const uint32_t s = step_general<MASKED, CHECKED, HIST, SHARED, CLASSIC>(M, T, Y, P, r, h, plen);
     if (s == CONT) prime(M, r);
     return s;
   }
@@ -482,7 +509,7 @@ __device__ __forceinline__ uint32_t one_step(uint64_t* __restrict__ M, const uin
     const uint32_t op = (uint32_t)o, jm = (uint32_t)j;
     const bool valid = (o - 1ull) < 7ull;
     const bool jin = j < (uint64_t)n;
-    const bool taken = (op == 5u) & (a != 0ull);
+    const bool taken = (op == 5u) & jumps<CLASSIC>(a, MASKED ? P.wmask : ~0ull);
     const bool rd = op == 6u;
     const bool pri = op == 7u;
     const bool seq_ok = ip + 3u < n;
@@ -497,7 +524,7 @@ __device__ __forceinline__ uint32_t one_step(uint64_t* __restrict__ M, const uin
       if (((op == 2u) | (op == 3u) | pri) & jin) v = M[jm];
     }
     const uint64_t sum = a + v;
-    const uint64_t prod = a * v;
+    const uint64_t prod = CLASSIC ? a - v : a * v;       // opcode 3: MUL, or SUB in the classic set
     const bool addr = ((op >= 2u) & (op != 5u)) | taken;   // j used as an address or jump target
     // rare: invalid opcode, operand outside memory, countdown exhausted, RD at
     // the end of the tape, BNZ to itself, i (+) 2 at the end of memory or 2^w
@@ -505,7 +532,8 @@ __device__ __forceinline__ uint32_t one_step(uint64_t* __restrict__ M, const uin
                 (taken ? (jm == ip) : (ip + 2u >= ilim));
     if constexpr (CHECKED) {
       rare |= (op == 2u) & ((int64_t)((a ^ sum) & (v ^ sum)) < 0);
-      rare |= (op == 3u) & (__mul64hi((long long)a, (long long)v) != ((int64_t)prod >> 63));
+      if constexpr (CLASSIC) rare |= (op == 3u) & ((int64_t)((a ^ v) & (a ^ prod)) < 0);
+      else rare |= (op == 3u) & (__mul64hi((long long)a, (long long)v) != ((int64_t)prod >> 63));
     }
     if (!rare) {
       uint64_t na = (op == 1u) ? j : a;
@@ -537,7 +565,7 @@ __device__ __forceinline__ uint32_t one_step(uint64_t* __restrict__ M, const uin
     }
   }
   if (PIPE) r.have = false;
-  return step_general<MASKED, CHECKED, HIST, SHARED>(M, T, Y, P, r, h, plen);
+  return step_general<MASKED, CHECKED, HIST, SHARED, CLASSIC>(M, T, Y, P, r, h, plen);
 }
 
 template <bool HIST>

@@ -14,6 +14,7 @@ struct StepVariant {
   bool checked;  // RASP_CHECKED semantics
   bool hist;     // collect per-opcode counters
   bool vote;     // warp opcode voting instead of guarded selects
+  bool classic;  // classic opcode set (Sec. 1.1: SUB, BPA); plain and HBM-slab persistent, select only
 };
 
 // Persistent-kernel launch shape for one bucket of VMs.

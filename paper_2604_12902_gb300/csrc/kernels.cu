@@ -144,7 +144,7 @@ __device__ __forceinline__ uint32_t vote_step(uint64_t* __restrict__ M, const ui
 }
 
 // ------------------------------------------------------------------ plain
-template <bool MASKED, bool CHECKED, bool HIST, bool VOTE>
+template <bool MASKED, bool CHECKED, bool HIST, bool VOTE, bool CLASSIC = false>
 __global__ void __launch_bounds__(256) k_plain(DevState S, Params P, const uint32_t* __restrict__ ids,
                                                uint32_t count) {
   const uint32_t t = blockIdx.x * blockDim.x + threadIdx.x;
@@ -180,7 +180,7 @@ __global__ void __launch_bounds__(256) k_plain(DevState S, Params P, const uint3
     if (had) store_regs(S, v, r, st);
   } else if (active) {
     do {
-      st = one_step<MASKED, CHECKED, HIST, false>(M, T, Y, P, r, h);
+      st = one_step<MASKED, CHECKED, HIST, false, false, CLASSIC>(M, T, Y, P, r, h);
     } while (st == CONT);
     store_regs(S, v, r, st);
   }
@@ -188,7 +188,7 @@ __global__ void __launch_bounds__(256) k_plain(DevState S, Params P, const uint3
 }
 
 // Run `epoch` steps of every active lane (warp-uniform loop).
-template <bool MASKED, bool CHECKED, bool HIST, bool VOTE, bool PIPE>
+template <bool MASKED, bool CHECKED, bool HIST, bool VOTE, bool PIPE, bool CLASSIC = false>
 __device__ __forceinline__ void run_epoch(uint64_t* M, const uint64_t* T, uint64_t* Y, const Params& P, Regs& r,
                                           Hist& h, bool& active, uint32_t& final_st, uint32_t epoch) {
   if (VOTE) {
@@ -201,7 +201,7 @@ __device__ __forceinline__ void run_epoch(uint64_t* M, const uint64_t* T, uint64
     }
   } else if (active) {
     for (uint32_t t = 0; t < epoch; ++t) {
-      const uint32_t s = one_step<MASKED, CHECKED, HIST, PIPE>(M, T, Y, P, r, h);
+      const uint32_t s = one_step<MASKED, CHECKED, HIST, PIPE, false, CLASSIC>(M, T, Y, P, r, h);
       if (s != CONT) {
         active = false;
         final_st = s;
@@ -328,7 +328,7 @@ __global__ void __launch_bounds__(256) k_persist(DevState S, Params P, Queue Q, 
 // end no VM waits in a busy lane's prefetch slot while other lanes idle.
 enum : uint32_t { PF_EMPTY = 0, PF_ID = 1, PF_REGS = 2, PF_NONE = 3 };
 
-template <bool MASKED, bool CHECKED, bool HIST, bool VOTE>
+template <bool MASKED, bool CHECKED, bool HIST, bool VOTE, bool CLASSIC = false>
 __global__ void __launch_bounds__(128, 7) k_persist_gl(DevState S, Params P, Queue Q, uint32_t epoch) {
   const uint32_t lane = threadIdx.x & 31u;
   const uint32_t lt = (1u << lane) - 1u;
@@ -470,7 +470,7 @@ __global__ void __launch_bounds__(128, 7) k_persist_gl(DevState S, Params P, Que
     if (__all_sync(FULL, vm < 0 && pf == PF_NONE)) break;
 
     // ---- run
-    run_epoch<MASKED, CHECKED, HIST, VOTE, true>(M, T, Y, P, r, h, active, final_st, epoch);
+    run_epoch<MASKED, CHECKED, HIST, VOTE, true, CLASSIC>(M, T, Y, P, r, h, active, final_st, epoch);
   }
   flush_hist<HIST>(P, h);
 }
@@ -655,7 +655,25 @@ PlainFn plain_fn(bool vote) {
   return vote ? k_plain<M_, C_, H_, true> : k_plain<M_, C_, H_, false>;
 }
 
+// The classic opcode set (Sec. 1.1) is built for the select dispatch only.
+template <bool CL>
+PlainFn plain_select(const StepVariant& v) {
+  if (v.checked) return v.hist ? k_plain<false, true, true, false, CL> : k_plain<false, true, false, false, CL>;
+  if (v.masked) return v.hist ? k_plain<true, false, true, false, CL> : k_plain<true, false, false, false, CL>;
+  return v.hist ? k_plain<false, false, true, false, CL> : k_plain<false, false, false, false, CL>;
+}
+
+template <bool CL>
+GlobalFn global_select(const StepVariant& v) {
+  if (v.checked)
+    return v.hist ? k_persist_gl<false, true, true, false, CL> : k_persist_gl<false, true, false, false, CL>;
+  if (v.masked)
+    return v.hist ? k_persist_gl<true, false, true, false, CL> : k_persist_gl<true, false, false, false, CL>;
+  return v.hist ? k_persist_gl<false, false, true, false, CL> : k_persist_gl<false, false, false, false, CL>;
+}
+
 PlainFn pick_plain(const StepVariant& v) {
+  if (v.classic) return plain_select<true>(v);
   if (v.checked) return v.hist ? plain_fn<false, true, true>(v.vote) : plain_fn<false, true, false>(v.vote);
   if (v.masked) return v.hist ? plain_fn<true, false, true>(v.vote) : plain_fn<true, false, false>(v.vote);
   return v.hist ? plain_fn<false, false, true>(v.vote) : plain_fn<false, false, false>(v.vote);
@@ -678,6 +696,7 @@ GlobalFn global_fn(bool vote) {
 }
 
 GlobalFn pick_global(const StepVariant& v) {
+  if (v.classic) return global_select<true>(v);
   if (v.checked) return v.hist ? global_fn<false, true, true>(v.vote) : global_fn<false, true, false>(v.vote);
   if (v.masked) return v.hist ? global_fn<true, false, true>(v.vote) : global_fn<true, false, false>(v.vote);
   return v.hist ? global_fn<false, false, true>(v.vote) : global_fn<false, false, false>(v.vote);

@@ -50,13 +50,14 @@ def busy_beavers():
 
 
 # ------------------------------------------------------------------ parity plumbing
-def oracle_state(wl, budget=U64, checked=False, hist=False, threads=1):
-    """Run a workload through the CPU oracle (programs expanded per VM)."""
+def oracle_state(wl, budget=U64, checked=False, hist=False, threads=1, classic=False):
+    """Run a workload through the CPU oracle (programs expanded per VM);
+    ``classic`` selects the classic opcode set (SUB, BPA)."""
     from oracle import oracle
     progs, po = wl.expanded_programs()
     return oracle.run_packed(progs, po, wl.mem_words, wl.tapes, wl.tape_off, wl.ell, wl.s,
                              caps=wl.caps, budget=budget, w=wl.w, checked=checked, hist=hist,
-                             threads=threads)
+                             threads=threads, classic=classic)
 
 
 def assert_same_state(got, st, ell, s, ids=None, what=""):

@@ -171,7 +171,7 @@ def algorithmic_bytes(stats) -> float:
     return float(b)
 
 
-def cpu_baseline(wl, budget_s: float = 15.0, threads: int = 1):
+def cpu_baseline(wl, budget_s: float = 15.0, threads: int = 1, classic: bool = False):
     """The serial oracle on a prefix of the workload, chunk by chunk until
     `budget_s` seconds have passed."""
     from oracle import oracle
@@ -182,7 +182,7 @@ def cpu_baseline(wl, budget_s: float = 15.0, threads: int = 1):
         sub = wl.subset(np.arange(done_vms, hi))
         t0 = time.perf_counter()
         st, _ = oracle.run_packed(sub.programs, sub.prog_off, sub.mem_words, sub.tapes, sub.tape_off,
-                                  sub.ell, sub.s, caps=sub.caps, w=sub.w, threads=threads)
+                                  sub.ell, sub.s, caps=sub.caps, w=sub.w, threads=threads, classic=classic)
         t_used += time.perf_counter() - t0
         steps += int(st.steps.sum())
         done_vms = hi
@@ -203,7 +203,8 @@ def run_reference(args, ws, rank):
     for it in range(args.warmup + args.steps):
         t0 = time.perf_counter()
         st, _ = oracle.run_packed(sub.programs, sub.prog_off, sub.mem_words, sub.tapes, sub.tape_off,
-                                  sub.ell, sub.s, caps=sub.caps, w=sub.w, threads=threads)
+                                  sub.ell, sub.s, caps=sub.caps, w=sub.w, threads=threads,
+                                  classic=args.isa == "classic")
         dt = time.perf_counter() - t0
         if it >= args.warmup:
             times.append(dt)
@@ -258,14 +259,42 @@ def run_serving(args, ws, rank):
     print(json.dumps(line), flush=True)
 
 
+def run_search(args):
+    """Generate -> run -> filter (busy-beaver search): rounds of programs of
+    L = 100 tokens drawn uniformly, run on the device to tau_max, the best
+    halting programs kept by a device top-k; host generation of the next round
+    overlaps the device run of the current one. Reported end to end."""
+    import torch
+    from paper_2604_12902_gb300 import search
+    torch.cuda.set_device(0)
+    clk = ClockSampler(torch.cuda.current_device())
+    clk.start()
+    res = search.busy_beaver_search(args.rounds, args.vms, k=16, L=100, seed=6, tau_max=args.tau_max)
+    clocks = clk.stop()
+    line = {"metric": METRIC, "value": res["vm_steps"] / res["wall_s"], "unit": UNIT, "n_gpus": 1,
+            "steps": args.rounds, "warmup": 0, "ms_per_step": res["wall_s"] * 1e3 / args.rounds,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int64",
+            "data": "synthetic",
+            "config": {"workload": "busy-beaver search: %d rounds x %s programs of L = 100 tokens (uniform), w = 32, "
+                                   "n = 250, tau_max = %d, device top-16 per round" % (args.rounds, format(args.vms, ","),
+                                                                                    args.tau_max)},
+            "search": {"programs": res["programs"], "programs_per_s": res["programs_per_s"], "halted": res["halted"],
+                       "wall_s": res["wall_s"], "device_s": res["gpu_s"], "waiting_for_generation_s": res["gen_wait_s"],
+                       "best": [{"tau_h": t, "program": pid, "source": src} for t, pid, src in res["best"][:4]]},
+            "clocks": clocks}
+    print(json.dumps(line), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
-    ap.add_argument("--workload", default="templates", choices=["templates", "uneven", "shared", "random", "serving", "halting"])
+    ap.add_argument("--workload", default="templates", choices=["templates", "uneven", "shared", "random", "serving", "halting", "search"])
     ap.add_argument("--flags", type=lambda x: int(x, 0), default=0, help="rasp_config.flags (schedule)")
+    ap.add_argument("--isa", default="word", choices=["word", "classic"],
+                    help="opcode set: the word machine (Sec. 2.1) or the classic one (Sec. 1.1: SUB, BPA)")
     ap.add_argument("--epoch", type=int, default=0)
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU-oracle baseline")
     ap.add_argument("--no-e2e", action="store_true")
@@ -277,6 +306,8 @@ def main():
     ap.add_argument("--duration", type=float, default=60.0, help="serving: seconds of arrivals")
     ap.add_argument("--requests", type=int, default=64, help="serving: distinct requests (cycled)")
     ap.add_argument("--arena-gb", type=float, default=64.0, help="serving: device arena size")
+    ap.add_argument("--rounds", type=int, default=4, help="search: rounds")
+    ap.add_argument("--tau-max", type=int, default=10 ** 5, help="search: step cap")
     args = ap.parse_args()
     ws, rank, local = dist_env()
     if args.impl == "reference":
@@ -285,6 +316,10 @@ def main():
     if args.workload == "serving":
         if rank == 0:
             run_serving(args, ws, rank)
+        return
+    if args.workload == "search":
+        if rank == 0:
+            run_search(args)
         return
     if args.warmup < 3:
         args.warmup = 3
@@ -296,6 +331,8 @@ def main():
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
     from paper_2604_12902_gb300 import rasp as R
     from paper_2604_12902_gb300.shards import combine
+    if args.isa == "classic":
+        args.flags |= R.ISA_CLASSIC
 
     wl, desc = make_workload(args.workload, rank, args.vms)
     stream = torch.cuda.current_stream()
@@ -378,7 +415,7 @@ def main():
     # plain one-launch-per-batch form on the same workload (untimed by the contract)
     plain = None
     if not args.no_plain:
-        with R.Batch(wl.mem_words, wl.ell, wl.s, word_bits=wl.w, flags=R.SCHED_PLAIN) as bp:
+        with R.Batch(wl.mem_words, wl.ell, wl.s, word_bits=wl.w, flags=R.SCHED_PLAIN | (args.flags & R.ISA_CLASSIC)) as bp:
             bp.load_workload(wl)
             bp.run()
             torch.cuda.synchronize()
@@ -435,7 +472,7 @@ def main():
 
     cpu = None
     if rank == 0 and ws == 1 and not args.no_cpu:
-        cpu = cpu_baseline(wl, args.cpu_seconds)
+        cpu = cpu_baseline(wl, args.cpu_seconds, classic=args.isa == "classic")
     b.close()
 
     if rank == 0:
@@ -445,7 +482,7 @@ def main():
                 "config": {"workload": desc, "vms_per_gpu": wl.num_vms, "vm_steps_per_gpu": total_steps,
                            "l2": "inputs larger than L2 (M = %.2f GiB)" % (m_bytes / 2 ** 30)
                                  if m_bytes > 129e6 else "M below L2 size (%.1f MB); no flush" % (m_bytes / 1e6),
-                           "schedule_flags": args.flags, "parallelism": "vm shards x%d" % ws,
+                           "schedule_flags": args.flags, "isa": args.isa, "parallelism": "vm shards x%d" % ws,
                            "schedule": tuned["chosen"] if tuned else "flags %#x" % args.flags},
                 "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "plain": plain,
                 "gpu_launches": (1 + run_launches + (1 if hist else 0)) * args.steps, "clocks": clocks}

@@ -210,6 +210,16 @@ int rasp_read_stats(rasp_batch* b, rasp_stats* out);
 int rasp_halting_histogram(rasp_batch* b, const uint64_t* edges, uint32_t nbins,
                            uint64_t* counts, uint64_t* other);
 
+/* The k HALTED machines with the largest tau_h, selected on the device --
+ * the filter of a generate -> run -> filter search (busy beavers,
+ * superoptimisation; "Towards a Linear-Algebraic Hypervisor", Sec. 3 and
+ * Sec. 5). steps_out[k] and vm_out[k] (caller-owned host arrays) receive
+ * tau_h and the VM index, best first; ties go to the smaller VM index, so
+ * the result is unique. *found = number of entries written (fewer than k if
+ * fewer VMs halted). Synchronises the stream. EINVAL: k = 0 or k > 1024. */
+int rasp_top_halting(rasp_batch* b, uint32_t k, uint64_t* steps_out, uint32_t* vm_out,
+                     uint32_t* found);
+
 /* Measured schedule choice (the autotuner): times candidate schedules
  * (persistent over HBM slabs with several epochs and CTA shapes, plain, and
  * SMEM-staged where it fits) on this batch from its current state with the

@@ -63,7 +63,7 @@ struct Group {
 struct Layout {
   size_t off_i, off_a, off_steps, off_cap, off_status, off_uhead, off_ylen, off_n, off_memoff;
   size_t off_mem, off_prog, off_progoff, off_progvm, off_tape, off_y, off_ids, off_heads, off_err,
-      off_hist, off_stats, off_dirty, off_pvoff, off_pvids, off_thist, off_ids2, off_rcount;
+      off_hist, off_stats, off_dirty, off_pvoff, off_pvids, off_thist, off_ids2, off_rcount, off_topk;
   size_t total;
 };
 
@@ -148,6 +148,9 @@ int validate_config(const rasp_config* cfg, uint64_t num_vms, const uint32_t* me
   return RASP_OK;
 }
 
+// Blocks of the first top-k pass (each takes at least 1024 fresh candidates per tile).
+uint64_t topk_blocks(uint64_t V) { return std::min<uint64_t>(kMaxTopBlocks, (V + 1023) / 1024); }
+
 Layout make_layout(uint64_t V, uint64_t mem_words, uint32_t ellp, uint32_t sp) {
   Layout L{};
   size_t o = 0;
@@ -182,6 +185,7 @@ Layout make_layout(uint64_t V, uint64_t mem_words, uint32_t ellp, uint32_t sp) {
   L.off_thist = take(8 * (2 * kMaxHistBins + 1 + 4));   // edges, counts, other
   L.off_ids2 = take(4 * V);                             // compacted queue between budget rounds
   L.off_rcount = take(4 * kNumBuckets);                 // its length, per launch group
+  L.off_topk = take(sizeof(TopCand) * (topk_blocks(V) + 1) * kMaxTopK);  // top-k candidates, result
   L.total = o;
   return L;
 }
@@ -829,6 +833,27 @@ int rasp_halting_histogram(rasp_batch* b, const uint64_t* edges, uint32_t nbins,
   CK(cudaMemcpyAsync(oth, d_other, sizeof(oth), cudaMemcpyDeviceToHost, st));
   CK(cudaStreamSynchronize(st));
   if (other) memcpy(other, oth, sizeof(oth));
+  return RASP_OK;
+}
+
+int rasp_top_halting(rasp_batch* b, uint32_t k, uint64_t* steps_out, uint32_t* vm_out, uint32_t* found) {
+  if (!b || !steps_out || !vm_out || !found) return fail(RASP_EINVAL, "batch or an output pointer is NULL");
+  if (k == 0 || k > kMaxTopK) return fail(RASP_EINVAL, "k must be in 1..%u", kMaxTopK);
+  int rc = check_device_error(b);
+  if (rc) return rc;
+  cudaStream_t st = b->stream;
+  TopCand* cand = (TopCand*)(b->base + b->L.off_topk);
+  TopCand* best = cand + (size_t)topk_blocks(b->V) * kMaxTopK;
+  std::vector<TopCand> h(k);
+  CK(launch_topk(b->S, b->V, k, cand, best, st));
+  CK(cudaMemcpyAsync(h.data(), best, sizeof(TopCand) * k, cudaMemcpyDeviceToHost, st));
+  CK(cudaStreamSynchronize(st));
+  uint32_t n = 0;
+  for (uint32_t q = 0; q < k && h[q].ok; ++q, ++n) {
+    steps_out[q] = h[q].steps;
+    vm_out[q] = h[q].vm;
+  }
+  *found = n;
   return RASP_OK;
 }
 

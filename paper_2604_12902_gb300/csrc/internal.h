@@ -64,6 +64,19 @@ cudaError_t launch_tau_hist(const DevState& S, uint32_t num_vms, const uint64_t*
 cudaError_t launch_compact(const uint32_t* ids, uint32_t count, const uint8_t* status, uint32_t* out,
                            uint32_t* out_count, cudaStream_t stream);
 
+// Top-k halting times: candidate (tau_h, VM id); ok = 0 marks an empty slot.
+struct TopCand {
+  uint64_t steps;
+  uint32_t vm;
+  uint32_t ok;
+};
+constexpr uint32_t kMaxTopK = 1024;
+constexpr uint32_t kMaxTopBlocks = 256;
+// best[0, k): the k HALTED VMs with the largest steps (ties: smaller id),
+// best first, empty slots last; cand holds kMaxTopBlocks * k entries.
+cudaError_t launch_topk(const DevState& S, uint32_t num_vms, uint32_t k, TopCand* cand, TopCand* best,
+                        cudaStream_t stream);
+
 // Aggregate: out[0] = sum steps, out[1..5] = count per status.
 cudaError_t launch_stats(const DevState& S, uint32_t num_vms, unsigned long long* out, cudaStream_t stream);
 

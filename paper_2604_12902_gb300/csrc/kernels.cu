@@ -632,6 +632,65 @@ __global__ void __launch_bounds__(256) k_tau_hist(const uint64_t* __restrict__ s
   if (threadIdx.x < 4 && so[threadIdx.x]) atomicAdd(&other[threadIdx.x], (unsigned long long)so[threadIdx.x]);
 }
 
+// ------------------------------------------------------------------ top-k halting times
+// The k HALTED VMs with the largest tau_h (ties: smaller VM id first), for
+// the generate -> run -> filter search loop. Each block keeps a running
+// top-k in shared memory: per tile it appends (TILE - k) new candidates
+// behind its current best k and bitonic-sorts the TILE entries, so the first
+// k are the best of both; blocks write their k to a candidate array, which
+// one block reduces the same way.
+constexpr uint32_t TOPK_TILE = 2048;
+
+__device__ __forceinline__ bool topk_better(const TopCand& x, const TopCand& y) {
+  if (x.ok != y.ok) return x.ok > y.ok;
+  if (x.steps != y.steps) return x.steps > y.steps;
+  return x.vm < y.vm;
+}
+
+// items: VMs [0, count) read from steps/status (cands == NULL), or `count`
+// candidates from an earlier pass. out: k candidates per block.
+__global__ void __launch_bounds__(1024) k_topk(const uint64_t* __restrict__ steps, const uint8_t* __restrict__ status,
+                                               const TopCand* __restrict__ cands, uint32_t count, uint32_t k,
+                                               TopCand* __restrict__ out) {
+  __shared__ TopCand buf[TOPK_TILE];
+  const uint32_t t = threadIdx.x;
+  for (uint32_t q = t; q < TOPK_TILE; q += blockDim.x) buf[q] = TopCand{0ull, 0xFFFFFFFFu, 0u};
+  __syncthreads();
+  const uint32_t fresh = TOPK_TILE - k;
+  for (uint64_t base = (uint64_t)blockIdx.x * fresh; base < count; base += (uint64_t)gridDim.x * fresh) {
+    for (uint32_t q = t; q < fresh; q += blockDim.x) {
+      const uint64_t idx = base + q;
+      TopCand c{0ull, 0xFFFFFFFFu, 0u};
+      if (idx < count) {
+        if (cands) {
+          c = cands[idx];
+        } else if (status[idx] == ST_HALTED) {
+          c = TopCand{steps[idx], (uint32_t)idx, 1u};
+        }
+      }
+      buf[k + q] = c;
+    }
+    __syncthreads();
+    // bitonic sort of buf, best first
+    for (uint32_t size = 2; size <= TOPK_TILE; size <<= 1) {
+      for (uint32_t stride = size >> 1; stride > 0; stride >>= 1) {
+        for (uint32_t q = t; q < TOPK_TILE / 2; q += blockDim.x) {
+          const uint32_t lo = 2 * q - (q & (stride - 1));
+          const uint32_t hi = lo + stride;
+          const bool down = (lo & size) == 0;          // this run sorts best first
+          const TopCand x = buf[lo], y = buf[hi];
+          if (topk_better(y, x) == down) {
+            buf[lo] = y;
+            buf[hi] = x;
+          }
+        }
+        __syncthreads();
+      }
+    }
+  }
+  for (uint32_t q = t; q < k; q += blockDim.x) out[(uint64_t)blockIdx.x * k + q] = buf[q];
+}
+
 // ------------------------------------------------------------------ launchers
 namespace {
 
@@ -828,6 +887,19 @@ cudaError_t launch_compact(const uint32_t* ids, uint32_t count, const uint8_t* s
   const uint32_t cap = (uint32_t)num_sms() * 8u;
   if (blocks > cap) blocks = cap;
   k_compact<<<blocks, 256, 0, stream>>>(ids, count, status, out, out_count);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_topk(const DevState& S, uint32_t num_vms, uint32_t k, TopCand* cand, TopCand* best,
+                        cudaStream_t stream) {
+  // at most ceil(num_vms / 1024) blocks (the candidate array is sized so)
+  uint32_t blocks = (num_vms + (TOPK_TILE - k) - 1) / (TOPK_TILE - k);
+  if (blocks > kMaxTopBlocks) blocks = kMaxTopBlocks;
+  if (blocks == 0) blocks = 1;
+  k_topk<<<blocks, 1024, 0, stream>>>(S.steps, S.status, nullptr, num_vms, k, cand);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  k_topk<<<1, 1024, 0, stream>>>(nullptr, nullptr, cand, blocks * k, k, best);
   return cudaGetLastError();
 }
 

@@ -63,7 +63,7 @@ _lib = None
 EXPORTS = ["rasp_batch_bytes", "rasp_batch_create", "rasp_load_programs", "rasp_load_inputs",
            "rasp_reset", "rasp_run", "rasp_sync", "rasp_read_state", "rasp_load_state",
            "rasp_read_stats", "rasp_describe", "rasp_autotune", "rasp_halting_histogram",
-           "rasp_batch_destroy", "rasp_last_error", "rasp_version"]
+           "rasp_top_halting", "rasp_batch_destroy", "rasp_last_error", "rasp_version"]
 
 
 def lib():
@@ -88,11 +88,12 @@ def lib():
         L.rasp_describe.argtypes = [P, ctypes.c_char_p, U64]
         L.rasp_autotune.argtypes = [P, U64, U32]
         L.rasp_halting_histogram.argtypes = [P, P, U32, P, P]
+        L.rasp_top_halting.argtypes = [P, U32, P, P, P]
         L.rasp_batch_destroy.argtypes = [P]
         L.rasp_batch_destroy.restype = None
         L.rasp_last_error.restype = ctypes.c_char_p
         L.rasp_version.restype = ctypes.c_char_p
-        for name in EXPORTS[:13]:
+        for name in EXPORTS[:14]:
             getattr(L, name).restype = I
         _lib = L
     return _lib
@@ -182,6 +183,17 @@ def rasp_halting_histogram(h, edges, counts, other=None):
     """Device histogram of tau_h over HALTED VMs; counts[k] for
     edges[k] <= steps < edges[k+1] (uint64 arrays); other[4] optional."""
     return _check(lib().rasp_halting_histogram(h, _p(edges), len(edges) - 1, _p(counts), _p(other)))
+
+
+def rasp_top_halting(h, k: int):
+    """(tau_h, vm) of the k HALTED VMs with the largest tau_h, best first
+    (ties: smaller VM index), selected on the device."""
+    st = np.zeros(k, np.uint64)
+    vm = np.zeros(k, np.uint32)
+    found = np.zeros(1, np.uint32)
+    _check(lib().rasp_top_halting(h, int(k), _p(st), _p(vm), _p(found)))
+    n = int(found[0])
+    return st[:n], vm[:n]
 
 
 def rasp_batch_destroy(h):
@@ -284,6 +296,10 @@ class Batch:
 
     def describe(self) -> dict:
         return rasp_describe(self.h)
+
+    def top_halting(self, k: int):
+        """(tau_h, vm) of the k HALTED VMs with the largest tau_h, best first."""
+        return rasp_top_halting(self.h, k)
 
     def halting_histogram(self, edges):
         """(counts per bin, other) of the halting times: counts[k] = HALTED VMs

@@ -21,6 +21,9 @@
  *    asynchronous; rasp_read_state, rasp_read_stats and rasp_sync synchronise
  *    that stream.
  *  - VM outcomes (halt, timeout, fault) are status values, never errors.
+ *  - Testing hook: with the environment variable RASP_FAULT_INJECT=alloc,
+ *    every device allocation the library would make fails with RASP_ENOMEM
+ *    (no CUDA call is made for it).
  */
 #ifndef RASP_GB300_RASP_H
 #define RASP_GB300_RASP_H
@@ -336,6 +339,10 @@ int rasp_pool_poll(rasp_pool* p, uint64_t ticket, int* state);
  * NULL to discard), free its memory and forget the ticket. ESTATE while
  * still QUEUED. */
 int rasp_pool_read(rasp_pool* p, uint64_t ticket, rasp_state_view* out);
+/* Withdraw a request that is still waiting for admission (QUEUED): it is
+ * forgotten and its ticket becomes unknown. ESTATE once it was admitted (read
+ * it with rasp_pool_read instead), EINVAL for an unknown ticket. */
+int rasp_pool_cancel(rasp_pool* p, uint64_t ticket);
 /* Bytes of the arena in use, requests waiting, requests running. */
 int rasp_pool_info(rasp_pool* p, uint64_t* in_use, uint64_t* waiting, uint64_t* running);
 void rasp_pool_destroy(rasp_pool* p);

@@ -4,6 +4,7 @@
 #include <algorithm>
 #include <cstdarg>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <new>
 #include <numeric>
@@ -15,6 +16,11 @@
 #include "internal.h"
 
 using namespace rasp;
+
+bool rasp::inject_alloc_failure() {
+  const char* v = getenv("RASP_FAULT_INJECT");
+  return v && strcmp(v, "alloc") == 0;
+}
 
 namespace {
 
@@ -374,6 +380,10 @@ int rasp_batch_create(const rasp_config* cfg, uint64_t num_vms, const uint32_t* 
     b->owns = false;
   } else {
     void* p = nullptr;
+    if (inject_alloc_failure()) {
+      delete b;
+      return fail(RASP_ENOMEM, "injected allocation failure (RASP_FAULT_INJECT=alloc)");
+    }
     cudaError_t e = cudaMalloc(&p, b->L.total);
     if (e != cudaSuccess) {
       cudaGetLastError();
@@ -915,7 +925,7 @@ int rasp_autotune(rasp_batch* b, uint64_t max_steps, uint32_t reps) {
   size_t total = 0;
   for (auto& sp : spans) total += sp[1] - sp[0];
   char* snap = nullptr;
-  if (cudaMalloc(&snap, total) != cudaSuccess) {
+  if (inject_alloc_failure() || cudaMalloc(&snap, total) != cudaSuccess) {
     cudaGetLastError();
     return fail(RASP_ENOMEM, "autotune needs %llu bytes for a snapshot of the state", (unsigned long long)total);
   }

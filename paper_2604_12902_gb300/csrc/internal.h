@@ -77,6 +77,12 @@ constexpr uint32_t kMaxTopBlocks = 256;
 cudaError_t launch_topk(const DevState& S, uint32_t num_vms, uint32_t k, TopCand* cand, TopCand* best,
                         cudaStream_t stream);
 
+// Host-side fault injection for tests: true when the environment variable
+// RASP_FAULT_INJECT is "alloc", in which case every device allocation the
+// library would make (a batch, the autotuner's snapshot, a pool arena)
+// fails as if cudaMalloc had, with RASP_ENOMEM. Nothing reaches the GPU.
+bool inject_alloc_failure();
+
 // Aggregate: out[0] = sum steps, out[1..5] = count per status.
 cudaError_t launch_stats(const DevState& S, uint32_t num_vms, unsigned long long* out, cudaStream_t stream);
 

@@ -18,6 +18,7 @@
 #include <vector>
 
 #include "../../include/rasp.h"
+#include "internal.h"
 
 namespace {
 
@@ -184,7 +185,7 @@ int rasp_pool_create(const rasp_config* cfg, uint64_t arena_bytes, rasp_pool** o
   p->cfg.stream = nullptr;
   arena_bytes = (arena_bytes + kAlign - 1) & ~(kAlign - 1);
   void* base = nullptr;
-  if (cudaMalloc(&base, arena_bytes) != cudaSuccess) {
+  if (rasp::inject_alloc_failure() || cudaMalloc(&base, arena_bytes) != cudaSuccess) {
     cudaGetLastError();
     delete p;
     return pfail(RASP_ENOMEM, "cudaMalloc of the pool arena failed");
@@ -279,6 +280,23 @@ int rasp_pool_read(rasp_pool* p, uint64_t ticket, rasp_state_view* out) {
   p->reqs.erase(it);
   admit(p);
   if (rc) return pfail(rc, msg);
+  return RASP_OK;
+}
+
+int rasp_pool_cancel(rasp_pool* p, uint64_t ticket) {
+  if (!p) return pfail(RASP_EINVAL, "pool is NULL");
+  std::lock_guard<std::mutex> lock(p->mu);
+  auto it = p->reqs.find(ticket);
+  if (it == p->reqs.end()) return pfail(RASP_EINVAL, "unknown ticket");
+  if (it->second.state != RASP_REQ_QUEUED)
+    return pfail(RASP_ESTATE, "request already admitted; read it with rasp_pool_read");
+  for (auto w = p->waiting.begin(); w != p->waiting.end(); ++w)
+    if (*w == ticket) {
+      p->waiting.erase(w);
+      break;
+    }
+  p->reqs.erase(it);
+  admit(p);                     // the next waiting request may fit now
   return RASP_OK;
 }
 

@@ -40,10 +40,12 @@ def _lib():
         L.rasp_pool_poll.argtypes = [P, U64, ctypes.POINTER(ctypes.c_int)]
         L.rasp_pool_read.argtypes = [P, U64, ctypes.POINTER(R.rasp_state_view)]
         L.rasp_pool_info.argtypes = [P, ctypes.POINTER(U64), ctypes.POINTER(U64), ctypes.POINTER(U64)]
+        L.rasp_pool_cancel.argtypes = [P, U64]
         L.rasp_pool_destroy.argtypes = [P]
         L.rasp_pool_destroy.restype = None
         L.rasp_pool_last_error.restype = ctypes.c_char_p
-        for name in ("rasp_pool_create", "rasp_pool_submit", "rasp_pool_poll", "rasp_pool_read", "rasp_pool_info"):
+        for name in ("rasp_pool_create", "rasp_pool_submit", "rasp_pool_poll", "rasp_pool_read", "rasp_pool_info",
+                     "rasp_pool_cancel"):
             getattr(L, name).restype = ctypes.c_int
         _typed = True
     return L
@@ -100,6 +102,11 @@ class Pool:
                               R._p(out["mem"]) if mem else None, nw)
         _check(_lib().rasp_pool_read(self.h, ticket, ctypes.byref(v)))
         return out
+
+    def cancel(self, ticket: int):
+        """Withdraw a request still waiting for admission."""
+        _check(_lib().rasp_pool_cancel(self.h, ticket))
+        self.meta.pop(ticket, None)
 
     def info(self) -> dict:
         a, b, c = ctypes.c_uint64(), ctypes.c_uint64(), ctypes.c_uint64()

@@ -102,3 +102,30 @@ def test_poisson_short_run(serving):
     idx, res = out["results"][0]
     st, _ = oracle_state(reqs[idx], threads=THREADS)
     assert np.array_equal(res["steps"], st.steps) and np.array_equal(res["i"].view(np.uint64), st.i)
+
+
+def test_cancel_a_waiting_request(serving):
+    """A request still waiting for memory can be withdrawn; the others run to
+    the same results as alone; an admitted request cannot be cancelled."""
+    R, S = serving
+    reqs = [request(20000, k, seed=8) for k in range(4)]
+    one = max(R.rasp_batch_bytes(R.rasp_config(64, 0, 16, 8, 0, 0, 0, 0, 0, 0, None, None, 0), r.mem_words)
+              for r in reqs)
+    with S.Pool(int(one * 1.5), reqs[0].ell, reqs[0].s) as pool:
+        tickets = [pool.submit(r) for r in reqs]
+        assert pool.info()["waiting"] == 3
+        pool.cancel(tickets[2])
+        assert pool.info()["waiting"] == 2
+        with pytest.raises(R.RaspError) as e:
+            pool.cancel(tickets[0])                   # running
+        assert e.value.code == R.RASP_ESTATE
+        with pytest.raises(R.RaspError):
+            pool.poll(tickets[2])                     # forgotten
+        outs = {}
+        for tk in (tickets[0], tickets[1], tickets[3]):
+            wait(pool, tk)
+            outs[tk] = pool.read(tk)
+    for k in (0, 1, 3):
+        st, _ = oracle_state(reqs[k], threads=THREADS)
+        got = outs[tickets[k]]
+        assert np.array_equal(got["steps"], st.steps) and np.array_equal(got["status"], st.status)

@@ -40,6 +40,23 @@ def _stale(target, deps):
     return any(os.path.getmtime(d) > t for d in deps)
 
 
+GEN_SRC = os.path.join(PKG, "gen", "progsampler.c")
+GEN_LIB = os.path.join(BUILD, "libprogsampler.so")
+
+
+def build_generator(force: bool = False) -> str:
+    """Compile the C program sampler (input generation, host code) with gcc."""
+    os.makedirs(BUILD, exist_ok=True)
+    if force or _stale(GEN_LIB, [GEN_SRC]):
+        tmp = GEN_LIB + ".%d.tmp" % os.getpid()
+        r = subprocess.run(["gcc", "-O2", "-std=c11", "-shared", "-fPIC", "-Wall", "-o", tmp, GEN_SRC],
+                           capture_output=True, text=True)
+        if r.returncode != 0:
+            raise RuntimeError("gcc failed for %s:\n%s" % (GEN_SRC, r.stderr))
+        os.replace(tmp, GEN_LIB)
+    return GEN_LIB
+
+
 def build(force: bool = False, verbose: bool = False, ptxas_v: bool = False) -> str:
     os.makedirs(BUILD, exist_ok=True)
     headers = [os.path.join(CSRC, f) for f in os.listdir(CSRC) if f.endswith((".cuh", ".h"))]
@@ -65,6 +82,7 @@ def build(force: bool = False, verbose: bool = False, ptxas_v: bool = False) -> 
         for log in logs:
             if log:
                 sys.stderr.write(log)
+    build_generator(force)
     if force or _stale(LIB, objs):
         tmp = LIB + ".%d.tmp" % os.getpid()
         cmd = [cc] + ARCH + ["-shared", "-Xcompiler", "-fPIC", "-o", tmp] + objs + ["-lcudart"]

@@ -227,14 +227,89 @@ def fun_tokens(f: dsl.Fun) -> list:
             + block(f.body) + ["}"])
 
 
+# ---------------------------------------------------------------- C transcription
+class _GenTables(__import__("ctypes").Structure):
+    import ctypes as _c
+    _fields_ = [("L", _c.c_uint32),
+                ("s_off", _c.c_void_p), ("s_cum", _c.c_void_p), ("s_kind", _c.c_void_p), ("s_a", _c.c_void_p),
+                ("s_b", _c.c_void_p),
+                ("b_off", _c.c_void_p), ("b_cum", _c.c_void_p), ("b_kind", _c.c_void_p), ("b_a", _c.c_void_p),
+                ("b_b", _c.c_void_p)]
+
+
+_gen_lib = None
+_KIND = {"put": 0, "ife": 1, "whl": 2, "S": 0, "hlt": 1, "seq": 2}
+
+
+def _gen():
+    global _gen_lib
+    if _gen_lib is None:
+        import ctypes
+        from . import build as B
+        lib = ctypes.CDLL(B.build_generator())
+        P, U32, U64 = ctypes.c_void_p, ctypes.c_uint32, ctypes.c_uint64
+        lib.gen_halting_programs.argtypes = [P, U64, U64, U64, U32, U32, U32, U32, U32, ctypes.c_int,
+                                             P, P, P, P, P]
+        lib.gen_halting_programs.restype = ctypes.c_int
+        _gen_lib = lib
+    return _gen_lib
+
+
+@lru_cache(maxsize=None)
+def _flat_tables(L: int):
+    """The alternatives tables of every length, flattened for the C sampler
+    (same doubles as the Python walk uses)."""
+    out = {}
+    for kind, key in (("S", "s"), ("B", "b")):
+        off, cum, kd, a, b = [0], [], [], [], []
+        for l in range(L + 1):
+            try:
+                cs, ds = _table(kind, l, L)
+            except ValueError:
+                cs, ds = [], []
+            for c, d in zip(cs, ds):
+                cum.append(c)
+                kd.append(_KIND[d[0]])
+                a.append(d[1] if len(d) > 1 else 0)
+                b.append(d[2] if len(d) > 2 else 0)
+            off.append(len(cum))
+        out[key] = (np.array(off, np.uint32), np.array(cum, np.float64), np.array(kd, np.int32),
+                    np.array(a, np.int32), np.array(b, np.int32))
+    return out
+
+
+def _halting_programs_c(num_programs, L, seed, w, n, ell, s, mu, cap, first, read_inputs):
+    t = _flat_tables(L)
+    keep = [t["s"], t["b"]]
+    ptr = lambda x: x.ctypes.data
+    T = _GenTables(L, *(ptr(x) for x in t["s"]), *(ptr(x) for x in t["b"]))
+    words = np.zeros(max(num_programs * n, 1), np.int64)
+    po = np.zeros(num_programs + 1, np.uint64)
+    tape = np.zeros(max(num_programs * 9, 1), np.int64)
+    to = np.zeros(num_programs + 1, np.uint64)
+    red = np.zeros(1, np.uint64)
+    import ctypes
+    rc = _gen().gen_halting_programs(ctypes.byref(T), seed, first, num_programs, ell, s, mu, n, w,
+                                     1 if read_inputs else 0, ptr(words), ptr(po), ptr(tape), ptr(to), ptr(red))
+    del keep
+    if rc != 0:
+        raise RuntimeError("the C program sampler rejected its parameters")
+    return W.Workload("halting", words[:int(po[-1])].copy(), po, np.full(num_programs, n, np.uint32),
+                      tape[:int(to[-1])].copy(), to, np.full(num_programs, cap, np.uint64), ell, s, w,
+                      meta=dict(L=L, seed=seed, redraws=int(red[0]), read_inputs=read_inputs))
+
+
 def halting_programs(num_programs: int, L: int = 100, seed: int = 6, w: int = 32, n: int = 250,
                      ell: int = 10, s: int = 2, mu: int = 10, cap: int = 10 ** 6,
-                     first: int = 0, read_inputs: bool = False) -> W.Workload:
+                     first: int = 0, read_inputs: bool = False, impl: str = "c") -> W.Workload:
     """The Sec. 3 halting workload: programs k = first .. first+count-1, each
     drawn uniformly among valid programs of L tokens and lowered by the
     Sec. 2.2 rules, on an input tape x of N uniform w-bit words. As printed,
     the Fun rule reads no input (so ipt starts at zero and x is inert, as in
-    App. B); read_inputs=True prepends one RD per input word."""
+    App. B); read_inputs=True prepends one RD per input word. impl = "c" uses
+    the C transcription (progsampler.c, the same words), "py" this module."""
+    if impl == "c":
+        return _halting_programs_c(num_programs, L, seed, w, n, ell, s, mu, cap, first, read_inputs)
     ids = np.arange(first, first + num_programs, dtype=np.uint64)
     blocks = W.draws(seed, 0x51A0000, ids, 64)
     progs, tapes, redraws = [], [], 0
@@ -289,13 +364,18 @@ def _chunk_job(a):
 
 
 def halting_programs_parallel(num_programs: int, workers: int = 1, chunk: int = 1 << 15, **kw) -> W.Workload:
-    """halting_programs over `workers` processes (spawned), chunk by chunk;
+    """halting_programs chunk by chunk on `workers` threads (the C sampler runs
+    without the interpreter lock) or, for impl="py", spawned processes;
     identical to one call, since every program is a function of (seed, k)."""
     first = kw.pop("first", 0)
     jobs = [dict(kw, num_programs=min(chunk, num_programs - o), first=first + o)
             for o in range(0, num_programs, chunk)]
     if workers <= 1 or len(jobs) == 1:
         return concat([_chunk_job(j) for j in jobs])
+    if kw.get("impl", "c") == "c":
+        from concurrent.futures import ThreadPoolExecutor
+        with ThreadPoolExecutor(workers) as ex:
+            return concat(list(ex.map(_chunk_job, jobs)))
     import multiprocessing as mp
     with mp.get_context("spawn").Pool(workers) as pool:
         return concat(pool.map(_chunk_job, jobs))

@@ -7,8 +7,8 @@ programs r*B .. (r+1)*B - 1 uniformly among the valid programs of L tokens
 rounds, the k halting programs with the largest tau_h -- the longest-running
 programs that still halt, i.e. busy-beaver candidates for L tokens. The
 filter runs on the device (``rasp_top_halting``); only k (tau_h, id) pairs per
-round come back. Generating round r+1 on the host (a process pool) overlaps
-the device run of round r.
+round come back. Generating round r+1 on the host (the C sampler on a thread
+pool) overlaps the device run of round r.
 
 Ties in tau_h go to the smaller program id, so the result is a function of
 (L, seed, rounds, B, k, tau_max) alone.
@@ -17,7 +17,7 @@ from __future__ import annotations
 
 import os
 import time
-from concurrent.futures import ProcessPoolExecutor
+from concurrent.futures import ThreadPoolExecutor
 
 import numpy as np
 
@@ -52,7 +52,7 @@ def busy_beaver_search(rounds: int, batch: int, k: int = 16, L: int = 100, seed:
     best: list[tuple[int, int]] = []          # (-tau_h, program id)
     steps_total = 0
     halted_total = 0
-    with ProcessPoolExecutor(workers, mp_context=__import__("multiprocessing").get_context("spawn")) as ex:
+    with ThreadPoolExecutor(workers) as ex:
         def submit(r):
             return [ex.submit(_gen, (f, c, kw)) for f, c in _chunks(r * batch, batch, chunk)]
 

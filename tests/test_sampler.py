@@ -86,3 +86,18 @@ def test_deterministic_and_chunked_generation_equal():
     lens = a.prog_off[1:] - a.prog_off[:-1]
     assert (lens % 2 == 0).all() and (lens // 2 * 2 + 5 + 10 + 2 + 10 <= 250).all()
     assert (a.tapes >= 0).all() and (a.tapes < 2 ** 32).all()
+
+
+@pytest.mark.parametrize("L,read_inputs,w,n,first", [(100, False, 32, 250, 0), (100, True, 64, 250, 9000),
+                                                     (60, False, 8, 250, 3), (100, False, 32, 130, 0),
+                                                     (160, True, 32, 250, 11)])
+def test_c_sampler_equals_the_python_definition(L, read_inputs, w, n, first):
+    """progsampler.c draws the same programs and tapes as this module (word for
+    word), including redraws when a lowering does not fit n words."""
+    a = S.halting_programs(1500, L=L, read_inputs=read_inputs, w=w, n=n, first=first, impl="py")
+    b = S.halting_programs(1500, L=L, read_inputs=read_inputs, w=w, n=n, first=first, impl="c")
+    for f in ("programs", "prog_off", "tapes", "tape_off", "caps", "mem_words"):
+        assert np.array_equal(getattr(a, f), getattr(b, f)), f
+    assert a.meta["redraws"] == b.meta["redraws"]
+    if n == 130:
+        assert a.meta["redraws"] > 0

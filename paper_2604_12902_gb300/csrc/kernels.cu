@@ -319,14 +319,16 @@ __global__ void __launch_bounds__(256) k_persist(DevState S, Params P, Queue Q, 
 // ------------------------------------------------------------------ persistent, M in HBM
 // Each lane runs one VM at a time with M, tape and y in HBM (cached in L1).
 // The next VM of every lane is prefetched in stages that overlap the
-// running VM -- queue position, VM id (ids[pos]), registers -- so a lane
-// whose VM stops swaps the next one in without waiting on memory. Queue
+// running VM -- queue position, VM id (ids[pos]), then its state-store
+// entries warmed into L2 -- so a lane whose VM stops swaps the next one in
+// with one L2 round trip. (Holding the next VM's registers instead cost ~14
+// live registers in the step loop and forced spills.) Queue
 // positions below Q.soft_end are claimed in warp chunks of 32, the next
 // chunk's atomic issued while the current one is still being used. The
 // last positions (as many as there are resident lanes) form the tail: they
 // are claimed one at a time, only by lanes that are idle, so that near the
 // end no VM waits in a busy lane's prefetch slot while other lanes idle.
-enum : uint32_t { PF_EMPTY = 0, PF_ID = 1, PF_REGS = 2, PF_NONE = 3 };
+enum : uint32_t { PF_EMPTY = 0, PF_ID = 1, PF_REGS = 2, PF_NONE = 3 };   // PF_REGS: entries warmed in L2
 
 template <bool MASKED, bool CHECKED, bool HIST, bool VOTE, bool CLASSIC = false>
 __global__ void __launch_bounds__(128, 7) k_persist_gl(DevState S, Params P, Queue Q, uint32_t epoch) {
@@ -367,9 +369,6 @@ __global__ void __launch_bounds__(128, 7) k_persist_gl(DevState S, Params P, Que
   uint64_t* Y = S.y;
   // prefetched VM
   uint32_t pf = PF_EMPTY, pf_pos = 0, pf_vm = 0;
-  Regs nr{};
-  uint64_t nmoff = 0;
-  uint8_t nstatus = 0;
 
   for (;;) {
     // ---- boundary: retire stopped VMs
@@ -379,11 +378,12 @@ __global__ void __launch_bounds__(128, 7) k_persist_gl(DevState S, Params P, Que
     }
     // swap in the prefetched VM (its loads were issued a boundary ago)
     if (vm < 0 && pf == PF_REGS) {
-      if (nstatus == ST_RUNNING) {
-        r = nr;
+      if (S.status[pf_vm] == ST_RUNNING) {
+        load_regs(S, P, pf_vm, r);
+        const uint64_t moff = S.mem_off[pf_vm];
         arm_regs(P, r);
         vm = (int32_t)pf_vm;
-        M = S.mem + nmoff;
+        M = S.mem + moff;
         T = S.tape + (uint64_t)pf_vm * P.ellp;
         Y = S.y + (uint64_t)pf_vm * P.sp;
         if (!VOTE) prime(M, r);
@@ -391,11 +391,17 @@ __global__ void __launch_bounds__(128, 7) k_persist_gl(DevState S, Params P, Que
       }
       pf = PF_EMPTY;
     }
-    // advance the prefetch pipeline: id -> registers
+    // advance the prefetch pipeline: id -> the VM's entries warmed in L2
     if (pf == PF_ID) {         // pf_vm = ids[pf_pos] was issued a boundary ago
-      nstatus = S.status[pf_vm];
-      load_regs(S, P, pf_vm, nr);
-      nmoff = S.mem_off[pf_vm];
+      asm volatile("prefetch.global.L2 [%0];" :: "l"(S.status + pf_vm));
+      asm volatile("prefetch.global.L2 [%0];" :: "l"(S.i + pf_vm));
+      asm volatile("prefetch.global.L2 [%0];" :: "l"(S.a + pf_vm));
+      asm volatile("prefetch.global.L2 [%0];" :: "l"(S.steps + pf_vm));
+      asm volatile("prefetch.global.L2 [%0];" :: "l"(S.cap + pf_vm));
+      asm volatile("prefetch.global.L2 [%0];" :: "l"(S.n + pf_vm));
+      asm volatile("prefetch.global.L2 [%0];" :: "l"(S.uhead + pf_vm));
+      asm volatile("prefetch.global.L2 [%0];" :: "l"(S.ylen + pf_vm));
+      asm volatile("prefetch.global.L2 [%0];" :: "l"(S.mem_off + pf_vm));
       pf = PF_REGS;
     }
     // ---- new queue positions
@@ -451,15 +457,13 @@ __global__ void __launch_bounds__(128, 7) k_persist_gl(DevState S, Params P, Que
     if (tail && vm < 0 && pf == PF_ID) {
       // an idle lane in the tail starts its VM at once (waiting on the loads
       // here) instead of two boundaries later
-      nstatus = S.status[pf_vm];
-      load_regs(S, P, pf_vm, nr);
-      nmoff = S.mem_off[pf_vm];
       pf = PF_EMPTY;
-      if (nstatus == ST_RUNNING) {
-        r = nr;
+      if (S.status[pf_vm] == ST_RUNNING) {
+        load_regs(S, P, pf_vm, r);
+        const uint64_t moff = S.mem_off[pf_vm];
         arm_regs(P, r);
         vm = (int32_t)pf_vm;
-        M = S.mem + nmoff;
+        M = S.mem + moff;
         T = S.tape + (uint64_t)pf_vm * P.ellp;
         Y = S.y + (uint64_t)pf_vm * P.sp;
         if (!VOTE) prime(M, r);

@@ -940,16 +940,21 @@ int rasp_autotune(rasp_batch* b, uint64_t max_steps, uint32_t reps) {
     }
     return cudaSuccess;
   };
-  struct Cand { const char* name; uint32_t sched, epoch, warps; };
+  // HBM-slab persistent shapes: epochs, CTA sizes and resident CTAs per SM
+  // (fewer resident VMs keep large memories in L1/L2: the uneven batch runs
+  // best at 12 warps per SM, the template batch at 28)
+  struct Cand { const char* name; uint32_t sched, epoch, warps, ctas; };
   static const Cand cands[] = {
-      {"persist_gl e128 w4", RASP_SCHED_PERSIST_GL, 128, 4}, {"persist_gl e64 w4", RASP_SCHED_PERSIST_GL, 64, 4},
-      {"persist_gl e256 w4", RASP_SCHED_PERSIST_GL, 256, 4}, {"persist_gl e128 w2", RASP_SCHED_PERSIST_GL, 128, 2},
-      {"plain", RASP_SCHED_PLAIN, 0, 0},                     {"persist_smem e32 w1", RASP_SCHED_PERSIST, 32, 1},
-      {"shared", RASP_SCHED_SHARED, 0, 0}};
+      {"persist_gl e128 w4", RASP_SCHED_PERSIST_GL, 128, 4, 0}, {"persist_gl e64 w4", RASP_SCHED_PERSIST_GL, 64, 4, 0},
+      {"persist_gl e256 w4", RASP_SCHED_PERSIST_GL, 256, 4, 0}, {"persist_gl e128 w2", RASP_SCHED_PERSIST_GL, 128, 2, 0},
+      {"persist_gl e128 w4 c3", RASP_SCHED_PERSIST_GL, 128, 4, 3},
+      {"persist_gl e128 w4 c5", RASP_SCHED_PERSIST_GL, 128, 4, 5},
+      {"plain", RASP_SCHED_PLAIN, 0, 0, 0},                     {"persist_smem e32 w1", RASP_SCHED_PERSIST, 32, 1, 0},
+      {"shared", RASP_SCHED_SHARED, 0, 0, 0}};
   // the shared-program schedule is a candidate only when programs are shared;
   // the classic opcode set runs on the HBM-slab persistent and plain schedules only
   const bool classic = (b->cfg.flags & RASP_ISA_CLASSIC) != 0;
-  const int ncand = classic ? 5 : (int)(sizeof(cands) / sizeof(cands[0])) - (b->shared_programs ? 0 : 1);
+  const int ncand = classic ? 7 : (int)(sizeof(cands) / sizeof(cands[0])) - (b->shared_programs ? 0 : 1);
   const rasp_config saved = b->cfg;
   cudaEvent_t e0, e1;
   cudaEventCreate(&e0);
@@ -962,6 +967,7 @@ int rasp_autotune(rasp_batch* b, uint64_t max_steps, uint32_t reps) {
     b->cfg.flags = (saved.flags & ~RASP_SCHED_MASK) | cands[k].sched;
     b->cfg.epoch = cands[k].epoch;
     b->cfg.warps_per_cta = cands[k].warps;
+    b->cfg.ctas_per_sm = cands[k].ctas;
     rc = replan(b);
     if (rc) break;
     float tmin = 1e30f;
@@ -999,6 +1005,7 @@ int rasp_autotune(rasp_batch* b, uint64_t max_steps, uint32_t reps) {
     b->cfg.flags = (saved.flags & ~RASP_SCHED_MASK) | cands[best_k].sched;
     b->cfg.epoch = cands[best_k].epoch;
     b->cfg.warps_per_cta = cands[best_k].warps;
+    b->cfg.ctas_per_sm = cands[best_k].ctas;
   }
   const int rc2 = replan(b);
   if (rc) return rc;

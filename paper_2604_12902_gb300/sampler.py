@@ -26,6 +26,7 @@ pure function of (seed, k).
 from __future__ import annotations
 
 import bisect
+import ctypes
 from functools import lru_cache
 
 import numpy as np
@@ -228,13 +229,13 @@ def fun_tokens(f: dsl.Fun) -> list:
 
 
 # ---------------------------------------------------------------- C transcription
-class _GenTables(__import__("ctypes").Structure):
-    import ctypes as _c
-    _fields_ = [("L", _c.c_uint32),
-                ("s_off", _c.c_void_p), ("s_cum", _c.c_void_p), ("s_kind", _c.c_void_p), ("s_a", _c.c_void_p),
-                ("s_b", _c.c_void_p),
-                ("b_off", _c.c_void_p), ("b_cum", _c.c_void_p), ("b_kind", _c.c_void_p), ("b_a", _c.c_void_p),
-                ("b_b", _c.c_void_p)]
+class _GenTables(ctypes.Structure):
+    """gen_tables of progsampler.c: the alternatives of S and B by length."""
+    _fields_ = [("L", ctypes.c_uint32),
+                ("s_off", ctypes.c_void_p), ("s_cum", ctypes.c_void_p), ("s_kind", ctypes.c_void_p),
+                ("s_a", ctypes.c_void_p), ("s_b", ctypes.c_void_p),
+                ("b_off", ctypes.c_void_p), ("b_cum", ctypes.c_void_p), ("b_kind", ctypes.c_void_p),
+                ("b_a", ctypes.c_void_p), ("b_b", ctypes.c_void_p)]
 
 
 _gen_lib = None
@@ -244,7 +245,6 @@ _KIND = {"put": 0, "ife": 1, "whl": 2, "S": 0, "hlt": 1, "seq": 2}
 def _gen():
     global _gen_lib
     if _gen_lib is None:
-        import ctypes
         from . import build as B
         lib = ctypes.CDLL(B.build_generator())
         P, U32, U64 = ctypes.c_void_p, ctypes.c_uint32, ctypes.c_uint64
@@ -288,7 +288,6 @@ def _halting_programs_c(num_programs, L, seed, w, n, ell, s, mu, cap, first, rea
     tape = np.zeros(max(num_programs * 9, 1), np.int64)
     to = np.zeros(num_programs + 1, np.uint64)
     red = np.zeros(1, np.uint64)
-    import ctypes
     rc = _gen().gen_halting_programs(ctypes.byref(T), seed, first, num_programs, ell, s, mu, n, w,
                                      1 if read_inputs else 0, ptr(words), ptr(po), ptr(tape), ptr(to), ptr(red))
     del keep

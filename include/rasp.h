@@ -82,6 +82,12 @@ enum rasp_semantics {
 #define RASP_SHARED_PROGRAM    0x2000u /* programs indexed by prog_of_vm       */
 #define RASP_CUDA_GRAPH        0x4000u /* rasp_run replays a CUDA graph captured
                                           once per budget (cached, up to 8)   */
+#define RASP_BUDGET_ROUNDS     0x10000u /* HBM-slab persistent schedule: always run
+                                          in budget rounds (4096 x 8^k steps)
+                                          with the still-running VMs compacted
+                                          between rounds; by default only
+                                          batches larger than the resident
+                                          lanes do                             */
 #define RASP_ISA_CLASSIC       0x8000u /* the classic RASP opcode set (Sec. 1.1)
                                           on the same words: opcode 3 is SUB
                                           (a - M_j mod 2^w), opcode 5 is BPA

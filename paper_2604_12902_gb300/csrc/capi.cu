@@ -612,7 +612,12 @@ namespace {
 // rounds together equal one run to that budget). Between rounds the VMs of
 // the launch group that are still RUNNING are compacted into a dense queue:
 // the few long-running VMs then fill whole warps instead of each keeping a
-// warp busy whose other lanes have nothing left to run.
+// warp busy whose other lanes have nothing left to run. Rounds are used for
+// launch groups larger than the resident lanes (whose lanes are refilled
+// from the queue, so that the survivors end up scattered), or always with
+// RASP_BUDGET_ROUNDS; a group that fits the resident lanes runs in one launch,
+// which also lets concurrent batches (the serving pool) share the GPU without
+// waiting for SMs at every round.
 constexpr uint64_t kRound0 = 4096;
 constexpr uint64_t kRoundGrowth = 8;
 constexpr int kMaxRounds = 6;
@@ -655,7 +660,9 @@ int enqueue_run(rasp_batch* b, cudaStream_t st, uint64_t max_steps) {
       b->dirty_valid = false;
       std::vector<uint64_t> budgets;
       const uint64_t limit = std::min(max_steps, b->max_cap);
-      for (uint64_t r = kRound0; r < limit && (int)budgets.size() < kMaxRounds; r *= kRoundGrowth)
+      const uint64_t lanes = (uint64_t)g.shape.grid * g.shape.warps * 32u;
+      const bool rounds = (b->cfg.flags & RASP_BUDGET_ROUNDS) || g.count > lanes;
+      for (uint64_t r = kRound0; rounds && r < limit && (int)budgets.size() < kMaxRounds; r *= kRoundGrowth)
         budgets.push_back(r);
       budgets.push_back(max_steps);
       for (size_t r = 0; r < budgets.size(); ++r) {

@@ -24,6 +24,7 @@ SCHED_AUTO, SCHED_PLAIN, SCHED_PERSIST, SCHED_PERSIST_GL = 0x00, 0x10, 0x20, 0x3
 DISPATCH_SELECT, DISPATCH_VOTE = 0x000, 0x100
 COLLECT_STATS = 0x1000
 ISA_CLASSIC = 0x8000
+BUDGET_ROUNDS = 0x10000
 SHARED_PROGRAM = 0x2000
 CUDA_GRAPH = 0x4000
 U64_MAX = (1 << 64) - 1

@@ -79,7 +79,7 @@ def test_countdowns_across_budget_rounds(rasp):
     halted = st.status == 1
     assert np.array_equal(st.steps[halted], (4 + 2 * np.maximum(Ts, 1))[halted].astype(np.uint64))
     for split in (None, [5_000, 40_000, 100_001]):
-        got, _ = run_gpu(rasp, wl, SCHEDS["persist_gl"], split=split)
+        got, _ = run_gpu(rasp, wl, SCHEDS["persist_gl"] | rasp.BUDGET_ROUNDS, split=split)
         assert_same_state(got, st, 0, 2, what="classic countdown split=%s" % split)
 
 

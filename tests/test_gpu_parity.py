@@ -241,9 +241,10 @@ def test_long_runs_across_budget_rounds(rasp, w):
     wl = wl_from(progs, tapes, 64, caps, 0, 2, w=w, name="countdown")
     full, _ = oracle_state(wl, threads=THREADS)
     assert (full.status == 2).any() and (full.status == 1).any()
-    got, _ = run_gpu(rasp, wl, SCHEDS["persist_gl"])
-    assert_same_state(got, full, wl.ell, wl.s, what="rounds w=%d" % w)
-    got, _ = run_gpu(rasp, wl, 0, steps_split=[3_000, 50_000, 200_001])
+    for flags in (SCHEDS["persist_gl"] | 0x10000, 0x10000, SCHEDS["persist_gl"]):   # forced rounds, and one launch
+        got, _ = run_gpu(rasp, wl, flags)
+        assert_same_state(got, full, wl.ell, wl.s, what="rounds w=%d flags %#x" % (w, flags))
+    got, _ = run_gpu(rasp, wl, 0x10000, steps_split=[3_000, 50_000, 200_001])
     assert_same_state(got, full, wl.ell, wl.s, what="rounds split w=%d" % w)
 
 

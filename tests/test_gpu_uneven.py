@@ -63,20 +63,27 @@ def test_graph_replay_with_budgets(rasp, uneven64k):
 
 
 def test_auto_schedule_merges_buckets_into_one_launch_group(rasp, uneven64k):
-    """All memory buckets run in one persistent launch group; the group runs
+    """All memory buckets run in one persistent launch group: 65,536 VMs fit
+    the resident lanes, so one launch; with RASP_BUDGET_ROUNDS the group runs
     in budget rounds (4096, x8, ... below the largest cap, then the run's
     budget), each round after the first preceded by a compaction launch."""
-    wl, _ = uneven64k
+    wl, full = uneven64k
     with rasp.Batch(wl.mem_words, wl.ell, wl.s) as b:
         d = b.describe()
         assert len(d["buckets"]) >= 5
         assert len(d["launches"]) == 1 and d["launches"][0]["vms"] == wl.num_vms
         b.load_workload(wl)
         b.run()
+        assert b.stats()["launches"] == 1
+    with rasp.Batch(wl.mem_words, wl.ell, wl.s, flags=rasp.BUDGET_ROUNDS) as b:
+        b.load_workload(wl)
+        b.run()
         rounds, r = 1, 4096
         while r < int(wl.caps.max()) and rounds <= 6:
             rounds, r = rounds + 1, r * 8
         assert b.stats()["launches"] == 1 + 2 * (rounds - 1)
+        got = b.read_state()
+    assert_same_state(got, full, wl.ell, wl.s, what="uneven with budget rounds")
 
 
 def test_uneven_full_size_sampled(rasp):

@@ -239,12 +239,20 @@ def run_serving(args, ws, rank):
             setattr(wl, f, _pinned_copy(torch, getattr(wl, f)))
     free, _ = torch.cuda.mem_get_info()
     arena = int(min(args.arena_gb * 2 ** 30, free * 0.8))
+    sweep = []
     with SV.Pool(arena, reqs[0].ell, reqs[0].s) as pool:
         SV.poisson_run(pool, reqs[:4], lam=50.0, duration=0.2, seed=0)      # warm-up (untimed)
         clk = ClockSampler(torch.cuda.current_device())
         clk.start()
         out = SV.poisson_run(pool, reqs, lam=args.lam, duration=args.duration, seed=1)
         clocks = clk.stop()
+        # higher arrival rates on the same requests: where does latency grow?
+        for lam in [float(x) for x in args.lam_sweep.split(",") if x]:
+            o = SV.poisson_run(pool, reqs, lam=lam, duration=args.duration, seed=2, max_waiting=32)
+            sweep.append({"lambda": lam, "p50_ms": o["p50_ms"], "p99_ms": o["p99_ms"],
+                          "vm_steps_per_s": o["vm_steps_per_s"], "requests_done": o["requests"],
+                          "rejected": o["rejected"],
+                          "wall_s": o["wall_s"], "offered_vms_per_s": lam * float(np.mean([r.num_vms for r in reqs]))})
     offered = args.lam * float(np.mean([r.num_vms for r in reqs]))
     line = {"metric": METRIC, "value": out["vm_steps_per_s"], "unit": UNIT, "n_gpus": 1, "steps": out["requests"],
             "warmup": 1, "ms_per_step": out["wall_s"] * 1e3 / max(out["requests"], 1), "higher_is_better": True,
@@ -254,7 +262,7 @@ def run_serving(args, ws, rank):
                                    "memory; %d distinct requests cycled; arena %.1f GiB" % (args.lam, args.duration, len(reqs), arena / 2 ** 30)},
             "serving": {"requests_done": out["requests"], "p50_ms": out["p50_ms"], "p99_ms": out["p99_ms"],
                         "wall_s": out["wall_s"], "vm_steps": out["vm_steps"], "mean_vms_per_request": out["mean_vms"],
-                        "offered_vms_per_s": offered, "request_gen_s": gen_s},
+                        "offered_vms_per_s": offered, "request_gen_s": gen_s, "lambda_sweep": sweep},
             "clocks": clocks}
     print(json.dumps(line), flush=True)
 
@@ -306,6 +314,7 @@ def main():
     ap.add_argument("--duration", type=float, default=60.0, help="serving: seconds of arrivals")
     ap.add_argument("--requests", type=int, default=64, help="serving: distinct requests (cycled)")
     ap.add_argument("--arena-gb", type=float, default=64.0, help="serving: device arena size")
+    ap.add_argument("--lam-sweep", default="", help="serving: further arrival rates to run, comma separated")
     ap.add_argument("--rounds", type=int, default=4, help="search: rounds")
     ap.add_argument("--tau-max", type=int, default=10 ** 5, help="search: step cap")
     args = ap.parse_args()

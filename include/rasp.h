@@ -341,6 +341,12 @@ int rasp_pool_create(const rasp_config* cfg, uint64_t arena_bytes, rasp_pool** o
 int rasp_pool_submit(rasp_pool* p, const rasp_request* req, uint64_t* ticket);
 /* Non-blocking: *state = enum rasp_request_state; also admits waiting work. */
 int rasp_pool_poll(rasp_pool* p, uint64_t ticket, int* state);
+/* Non-blocking: *ticket = a request that has finished (DONE, including one
+ * that failed at admission or that rasp_pool_poll saw finish) and has not been
+ * handed out by this call before nor read, or 0 if there is none now. One call
+ * checks every running request, so a server need not poll its tickets one by
+ * one. Also admits waiting work. */
+int rasp_pool_next_done(rasp_pool* p, uint64_t* ticket);
 /* Copy out a RUNNING or DONE request's final state (waits for it; out may be
  * NULL to discard), free its memory and forget the ticket. ESTATE while
  * still QUEUED. */

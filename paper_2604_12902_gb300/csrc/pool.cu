@@ -61,6 +61,7 @@ struct rasp_pool {
   std::deque<uint64_t> waiting;
   uint64_t next_ticket = 1;
   uint64_t in_use = 0;
+  std::deque<uint64_t> done;                  // finished, not yet handed out by rasp_pool_next_done
   std::mutex mu;
 };
 
@@ -166,6 +167,7 @@ void admit(rasp_pool* p) {
     r.offset = off;
     p->waiting.pop_front();
     start(p, r, held_inputs(r));
+    if (r.state == RASP_REQ_DONE) p->done.push_back(r.ticket);   // failed at admission
   }
 }
 
@@ -220,6 +222,7 @@ int rasp_pool_submit(rasp_pool* p, const rasp_request* q, uint64_t* ticket) {
     // room now: load straight from the caller's buffers, no host copy
     r.offset = off;
     start(p, r, *q);
+    if (r.state == RASP_REQ_DONE) p->done.push_back(t);             // failed at admission
     return RASP_OK;
   }
   const uint64_t nwords = q->offsets[q->num_programs];
@@ -248,15 +251,48 @@ int rasp_pool_poll(rasp_pool* p, uint64_t ticket, int* state) {
   Request& r = it->second;
   if (r.state == RASP_REQ_RUNNING) {
     const cudaError_t e = cudaEventQuery(r.done);
-    if (e == cudaSuccess) r.state = RASP_REQ_DONE;
-    else if (e != cudaErrorNotReady) {
+    if (e != cudaErrorNotReady) {
       r.state = RASP_REQ_DONE;
-      r.error = RASP_ECUDA;
-      r.error_msg = cudaGetErrorString(e);
+      if (e != cudaSuccess) {
+        r.error = RASP_ECUDA;
+        r.error_msg = cudaGetErrorString(e);
+      }
+      p->done.push_back(ticket);
     }
   }
   admit(p);
   *state = r.state;
+  return RASP_OK;
+}
+
+int rasp_pool_next_done(rasp_pool* p, uint64_t* ticket) {
+  if (!p || !ticket) return pfail(RASP_EINVAL, "pool or ticket is NULL");
+  std::lock_guard<std::mutex> lock(p->mu);
+  if (p->done.empty()) {
+    // one pass over the running requests (in ticket order)
+    for (auto& kv : p->reqs) {
+      Request& r = kv.second;
+      if (r.state != RASP_REQ_RUNNING) continue;
+      const cudaError_t e = cudaEventQuery(r.done);
+      if (e == cudaErrorNotReady) continue;
+      r.state = RASP_REQ_DONE;
+      if (e != cudaSuccess) {
+        r.error = RASP_ECUDA;
+        r.error_msg = cudaGetErrorString(e);
+      }
+      p->done.push_back(kv.first);
+    }
+    admit(p);
+  }
+  while (!p->done.empty()) {
+    const uint64_t t = p->done.front();
+    p->done.pop_front();
+    if (p->reqs.count(t)) {        // still unread
+      *ticket = t;
+      return RASP_OK;
+    }
+  }
+  *ticket = 0;
   return RASP_OK;
 }
 

@@ -4,7 +4,7 @@
 drives it open-loop: requests arrive at exponential inter-arrival times,
 are submitted when they arrive, and are polled until done; a finished
 request is read back (which frees its device memory and admits waiting
-requests). Latency is measured from arrival to the first poll that sees the
+requests). Latency is measured from arrival to the first pass that sees the
 request done; throughput is the VM-steps of all finished requests over the
 wall time of the run.
 """
@@ -41,11 +41,12 @@ def _lib():
         L.rasp_pool_read.argtypes = [P, U64, ctypes.POINTER(R.rasp_state_view)]
         L.rasp_pool_info.argtypes = [P, ctypes.POINTER(U64), ctypes.POINTER(U64), ctypes.POINTER(U64)]
         L.rasp_pool_cancel.argtypes = [P, U64]
+        L.rasp_pool_next_done.argtypes = [P, ctypes.POINTER(U64)]
         L.rasp_pool_destroy.argtypes = [P]
         L.rasp_pool_destroy.restype = None
         L.rasp_pool_last_error.restype = ctypes.c_char_p
         for name in ("rasp_pool_create", "rasp_pool_submit", "rasp_pool_poll", "rasp_pool_read", "rasp_pool_info",
-                     "rasp_pool_cancel"):
+                     "rasp_pool_cancel", "rasp_pool_next_done"):
             getattr(L, name).restype = ctypes.c_int
         _typed = True
     return L
@@ -103,6 +104,12 @@ class Pool:
         _check(_lib().rasp_pool_read(self.h, ticket, ctypes.byref(v)))
         return out
 
+    def next_done(self) -> int:
+        """A finished request not handed out before, or 0 (non-blocking)."""
+        t = ctypes.c_uint64(0)
+        _check(_lib().rasp_pool_next_done(self.h, ctypes.byref(t)))
+        return t.value
+
     def cancel(self, ticket: int):
         """Withdraw a request still waiting for admission."""
         _check(_lib().rasp_pool_cancel(self.h, ticket))
@@ -126,40 +133,48 @@ class Pool:
 
 
 def poisson_run(pool: Pool, requests, lam: float, duration: float, seed: int = 0, max_steps: int = R.U64_MAX,
-                poll_interval: float = 2e-4, keep_results: bool = False):
+                poll_interval: float = 2e-4, keep_results: bool = False, max_waiting: int | None = None):
     """Open-loop Poisson arrivals (rate `lam` per second) for `duration`
     seconds, cycling through the pre-built `requests` (workloads); then drain.
-    Returns a dict with per-request latencies (s), VM-steps and throughput."""
+    With `max_waiting`, an arrival that finds that many requests waiting for
+    admission is rejected (admission control: an overloaded pool would
+    otherwise hold an ever-growing backlog of request copies). Returns a dict
+    with per-request latencies (s), VM-steps, throughput and rejections."""
     rng = np.random.default_rng(seed)
     t0 = time.perf_counter()
     next_arrival = t0 + rng.exponential(1.0 / lam)
     inflight = {}                      # ticket -> (arrival time, request index)
     lat, steps, sizes, results = [], 0, [], []
-    k = 0
+    k = rejected = 0
     while True:
         now = time.perf_counter()
         while now >= next_arrival and next_arrival - t0 < duration:
             idx = k % len(requests)
-            tk = pool.submit(requests[idx], max_steps)
-            inflight[tk] = (next_arrival, idx)
+            if max_waiting is not None and pool.info()["waiting"] >= max_waiting:
+                rejected += 1
+            else:
+                tk = pool.submit(requests[idx], max_steps)
+                inflight[tk] = (next_arrival, idx)
             k += 1
             next_arrival += rng.exponential(1.0 / lam)
-        for tk in list(inflight):
-            if pool.poll(tk) == DONE:
-                t_done = time.perf_counter()
-                arr, idx = inflight.pop(tk)
-                res = pool.read(tk)
-                lat.append(t_done - arr)
-                steps += int(res["steps"].sum())
-                sizes.append(requests[idx].num_vms)
-                if keep_results:
-                    results.append((idx, res))
+        while True:                          # every request that finished since the last pass
+            tk = pool.next_done()
+            if not tk:
+                break
+            t_done = time.perf_counter()
+            arr, idx = inflight.pop(tk)
+            res = pool.read(tk)
+            lat.append(t_done - arr)
+            steps += int(res["steps"].sum())
+            sizes.append(requests[idx].num_vms)
+            if keep_results:
+                results.append((idx, res))
         if next_arrival - t0 >= duration and not inflight:
             break
         time.sleep(poll_interval)
     wall = time.perf_counter() - t0
     lat = np.array(lat)
-    return dict(requests=len(lat), wall_s=wall, vm_steps=steps, vm_steps_per_s=steps / wall,
+    return dict(requests=len(lat), rejected=rejected, wall_s=wall, vm_steps=steps, vm_steps_per_s=steps / wall,
                 p50_ms=float(np.percentile(lat, 50) * 1e3) if len(lat) else None,
                 p99_ms=float(np.percentile(lat, 99) * 1e3) if len(lat) else None,
                 mean_vms=float(np.mean(sizes)) if sizes else 0.0, results=results, latencies=lat)

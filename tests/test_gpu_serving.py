@@ -129,3 +129,21 @@ def test_cancel_a_waiting_request(serving):
         st, _ = oracle_state(reqs[k], threads=THREADS)
         got = outs[tickets[k]]
         assert np.array_equal(got["steps"], st.steps) and np.array_equal(got["status"], st.status)
+
+
+def test_next_done_hands_out_every_request_once(serving):
+    R, S = serving
+    reqs = [request(3000 + 500 * k, k, seed=10) for k in range(6)]
+    with S.Pool(4 << 30, reqs[0].ell, reqs[0].s) as pool:
+        tickets = [pool.submit(r) for r in reqs]
+        assert pool.poll(tickets[0]) in (1, 2)          # a poll may see it finish first
+        seen = []
+        for _ in range(200000):
+            t = pool.next_done()
+            if t:
+                seen.append(t)
+                pool.read(t)
+            if len(seen) == len(tickets):
+                break
+        assert sorted(seen) == sorted(tickets)
+        assert pool.next_done() == 0

@@ -225,7 +225,7 @@ void plan_buckets(rasp_batch* b) {
       if ((w & 3u) == 0) w += 2u;          // stride = 2 mod 4 words: conflict-free 16-byte rows
       return w;
     }();
-    const size_t staged_bytes = (size_t)(32u + 32u * slot) * 8u;
+    const size_t staged_bytes = (32ull + 32ull * slot) * 8ull;   // 64-bit: slot reaches 2^31
     // default before autotuning: persistent workers over HBM-resident slabs
     // (measured fastest on the 256-word template workload)
     if (sched == RASP_SCHED_AUTO) sched = RASP_SCHED_PERSIST_GL;

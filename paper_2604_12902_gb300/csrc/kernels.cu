@@ -825,7 +825,7 @@ cudaError_t launch_plain(const StepVariant& var, const DevState& S, const Params
 
 int persist_configure(const StepVariant& var, PersistShape& sh) {
   const void* fn = persist_symbol(var, sh.staged);
-  const size_t per_warp = sh.staged ? (size_t)(32u + 32u * sh.slot_words) * 8u : 0u;
+  const size_t per_warp = sh.staged ? (32ull + 32ull * sh.slot_words) * 8ull : 0u;
   sh.smem = per_warp * sh.warps;
   if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sh.smem) != cudaSuccess) {
     cudaGetLastError();

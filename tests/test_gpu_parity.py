@@ -321,6 +321,40 @@ def test_shared_programs_match_expanded(rasp):
         assert_same_state(got, st, 8, 8, what="shared %x" % sched)
 
 
+def slab_over_4gib_workload():
+    """One VM whose M slab is larger than 4 GiB (n = 2^29 + 6 words), then a
+    small VM whose slab starts past 4 GiB. The big VM keeps a counter, a
+    data word and a self-written instruction at the top of its memory, reads
+    them through operands j >= n (j mod n), jumps to the instruction it wrote
+    at n - 2, whose i (+) 2 = n fetches M[0] again (circular fetch), and
+    leaves through a jump to n - 1, where the pair <M[n-1], M[0]> is an
+    invalid opcode (a fixed point)."""
+    N = (1 << 29) + 6
+    big = asm((LOD, 1), (ADD, N - 4), (STO, N - 4),        # 0: c <- c + 1
+              (ADD, 41), (BNZ, 14),                        # 6: c - 3 != 0 -> body
+              (LOD, 1), (BNZ, N - 1),                      # 10: exit through <M[n-1], M[0]>
+              (RD, N - 5), (LOD, 0), (ADD, 2 * N - 3),     # 14: body
+              (ADD, N - 5), (MUL, 3 * N - 5), (STO, N - 3), (PRI, 4 * N - 3),
+              (LOD, MUL), (STO, N - 2), (LOD, N - 3), (STO, N - 1),   # 28: M[n-2..] <- MUL n-3
+              (LOD, 1), (BNZ, N - 2),                      # 36: run it; i (+) 2 = n
+              (LOD, -3))                                   # 40: M[41] = -3, never run
+    small = asm((RD, 10), (LOD, 5), (ADD, 10), (STO, 11), (PRI, 11), (LOD, 1), (BNZ, 12))
+    return wl_from([big, small], [[11, -7, 5], [9]], [N, 16], [10 ** 4, 100], 3, 3), N
+
+
+def test_memory_slab_over_4gib(rasp):
+    """Byte offsets past 2^32 inside one slab and between slabs, on every
+    schedule (a forced staged schedule falls back to HBM slabs for this n)."""
+    wl, N = slab_over_4gib_workload()
+    st, _ = oracle_state(wl)
+    assert list(st.status) == [1, 1] and st.steps[0] > 40        # both halt, the loop ran
+    assert st.mem[N - 4] == 3 and st.mem[N - 2] == MUL
+    for sched in SCHEDS.values():
+        got, _ = run_gpu(rasp, wl, sched)
+        assert_same_state(got, st, 3, 3, what="slab > 4 GiB %x" % sched)
+        del got
+
+
 def test_argument_errors(rasp):
     R = rasp
     wl = W.random_programs(num_vms=8)

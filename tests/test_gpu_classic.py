@@ -110,3 +110,15 @@ def test_autotune_and_rejected_configurations(rasp):
         with pytest.raises(rasp.RaspError) as e:
             rasp.Batch(wl.mem_words, wl.ell, wl.s, flags=flags)
         assert e.value.code == rasp.RASP_EINVAL
+
+
+def test_templates_full_size_classic(rasp):
+    """The classic-opcode benchmark workload (1,048,576 template programs,
+    n = 256, cap 4096) in its launch configuration: every VM against the
+    oracle run with the classic opcode set."""
+    wl = W.template_programs(num_vms=1 << 20, seed=2)
+    st, _ = oracle_state(wl, threads=THREADS, classic=True)
+    got, stats = run_gpu(rasp, wl, 0)
+    assert_same_state(got, st, wl.ell, wl.s, what="classic templates full")
+    assert stats["halted"] == int((st.status == 1).sum())
+    assert stats["vm_steps"] == int(st.steps.sum())

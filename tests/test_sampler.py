@@ -3,6 +3,8 @@ brute force: its string counts equal an explicit enumeration of the Sec. 2.2
 grammar (every enumerated string accepted by the independent parser of
 dsl.py), every sample has exactly L tokens and parses back to itself, and on
 a small space the samples are uniform (chi-square)."""
+import os
+
 import numpy as np
 import pytest
 
@@ -101,3 +103,20 @@ def test_c_sampler_equals_the_python_definition(L, read_inputs, w, n, first):
     assert a.meta["redraws"] == b.meta["redraws"]
     if n == 130:
         assert a.meta["redraws"] > 0
+
+
+def test_minimum_halting_time_under_both_input_readings():
+    """Sec. 3 / Fig. 1b report a minimum tau_h of 5 over the sampled programs.
+    With the lowering pinned by App. B, the shortest run is an untaken
+    ``ife`` on a zero word whose else-branch is ``hlt``: Get (2) + BNZ (1) +
+    one PRI per output (e >= 1), so 3 + e = 4 when the program reads no
+    input, and N + 3 + e = 5 (N >= 1 input words) when it first reads its
+    inputs with RD. The sampler, lowering and oracle together must give
+    exactly these minima."""
+    from tests.helpers import oracle_state
+    for read_inputs, want in ((False, 4), (True, 5)):
+        wl = S.halting_programs(50000, L=100, seed=6, w=32, n=250, ell=10, s=2, cap=10 ** 4,
+                                read_inputs=read_inputs)
+        st, _ = oracle_state(wl, threads=os.cpu_count() or 1)
+        halted = st.steps[st.status == 1]
+        assert int(halted.min()) == want, (read_inputs, int(halted.min()))

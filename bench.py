@@ -111,7 +111,7 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
-def make_workload(name: str, rank: int, vms: int = 1 << 20):
+def make_workload(name: str, rank: int, vms: int = 1 << 20, out_arity: int = 0):
     from paper_2604_12902_gb300 import workloads as W
     from paper_2604_12902_gb300.shards import shard_range
     if name == "templates":
@@ -131,10 +131,10 @@ def make_workload(name: str, rank: int, vms: int = 1 << 20):
         from paper_2604_12902_gb300 import sampler as S
         first, count = shard_range(rank, vms)
         wl = S.halting_programs_parallel(count, workers=os.cpu_count() or 1, L=100, seed=6, cap=10 ** 6,
-                                         first=first)
+                                         first=first, out_arity=out_arity)
         return wl, ("%s programs of the array language, uniform over valid snippets of L = 100 tokens, "
-                    "lowered (Sec. 2.2), w = 32, n = 250, l = 10, s = 2, tau_max = 10^6 (Sec. 3)"
-                    % format(wl.num_vms, ","))
+                    "lowered (Sec. 2.2), w = 32, n = 250, l = 10, s = 2, tau_max = 10^6 (Sec. 3)%s"
+                    % (format(wl.num_vms, ","), ", output arity %d" % out_arity if out_arity else ""))
     if name == "random":
         return W.random_programs(num_vms=1024, seed=1, first_vm=rank * 1024), \
             "1,024 random programs (32 instr, opcodes U{1..7}, operands U[0,63]), n=64, l=4, s=8, cap 256"
@@ -195,7 +195,7 @@ def run_reference(args, ws, rank):
     if rank != 0:
         return
     from oracle import oracle
-    wl, desc = make_workload(args.workload, 0)
+    wl, desc = make_workload(args.workload, 0, out_arity=args.out_arity)
     threads = os.cpu_count() or 1
     sample = min(wl.num_vms, 1 << 16)
     sub = wl.subset(np.arange(sample))
@@ -317,6 +317,8 @@ def main():
     ap.add_argument("--lam-sweep", default="", help="serving: further arrival rates to run, comma separated")
     ap.add_argument("--rounds", type=int, default=4, help="search: rounds")
     ap.add_argument("--tau-max", type=int, default=10 ** 5, help="search: step cap")
+    ap.add_argument("--out-arity", type=int, default=0,
+                    help="halting: output arity of the sampled programs (0 = drawn from 1..s, as the grammar allows)")
     args = ap.parse_args()
     ws, rank, local = dist_env()
     if args.impl == "reference":
@@ -343,7 +345,7 @@ def main():
     if args.isa == "classic":
         args.flags |= R.ISA_CLASSIC
 
-    wl, desc = make_workload(args.workload, rank, args.vms)
+    wl, desc = make_workload(args.workload, rank, args.vms, args.out_arity)
     stream = torch.cuda.current_stream()
     b = R.Batch(wl.mem_words, wl.ell, wl.s, word_bits=wl.w, flags=args.flags, epoch=args.epoch)
     b.load_workload(wl)

@@ -266,16 +266,20 @@ static void lower_block(emitter *E, const stmt *st, int32_t b) {
  * Programs first .. first+count-1 of the halting workload: words_out gets
  * each program's words back to back (at most n per program), prog_off the
  * offsets (count+1), tape_out / tape_off the input words (arity per program,
- * uniform w-bit words). Returns 0, or -1 if a program could not be drawn
+ * uniform w-bit words). out_arity 0 draws the output arity e uniformly
+ * from 1..min(9, s); 1..min(9, s) fixes it (the draw is still taken, so the
+ * body of program k does not depend on it). Returns 0, or -1 if a program could not be drawn
  * within the fixed working space (never for the grammar's lengths here) or
  * a parameter is out of range; *redraws counts programs redrawn because
  * their lowering did not fit n words.
  */
 int gen_halting_programs(const gen_tables *T, uint64_t seed, uint64_t first, uint64_t count,
                          uint32_t ell, uint32_t s, uint32_t mu, uint32_t n, uint32_t w, int read_inputs,
-                         int64_t *words_out, uint64_t *prog_off, int64_t *tape_out, uint64_t *tape_off,
+                         uint32_t out_arity, int64_t *words_out, uint64_t *prog_off, int64_t *tape_out,
+                         uint64_t *tape_off,
                          uint64_t *redraws) {
     if (T->L <= 15 || w < 1 || w > 64 || ell < 1 || s < 1) return -1;
+    if (out_arity > (s < 9 ? s : 9)) return -1;
     enum { MAXST = 4096, MAXCODE = 8192, MAXLAB = 8192 };
     stmt *st = (stmt *)malloc(sizeof(stmt) * MAXST);
     insn *code = (insn *)malloc(sizeof(insn) * MAXCODE);
@@ -292,7 +296,8 @@ int gen_halting_programs(const gen_tables *T, uint64_t seed, uint64_t first, uin
         for (uint32_t attempt = 0;; ++attempt) {
             stream r = {seed, pid, 0x51A0000u + 4096u * attempt, 0, 0, {0, 0, 0, 0}, ~0u};
             const uint32_t nin = 1 + below(&r, in_max);
-            const uint32_t nout = 1 + below(&r, out_max);
+            const uint32_t drawn = 1 + below(&r, out_max);    /* drawn even when fixed: same body */
+            const uint32_t nout = out_arity ? out_arity : drawn;
             sampler S = {T, &r, st, 0, MAXST, 0};
             const int32_t body = sample_block(&S, (int32_t)T->L - 15);
             emitter E = {code, 0, MAXCODE, label, 0, MAXLAB, (int32_t)nout, S.overflow};

@@ -186,15 +186,17 @@ class _Sampler:
 
 
 def sample_fun(L: int, seed: int, pid: int, ell: int = 10, s: int = 2, attempt: int = 0,
-               first_block=None) -> dsl.Fun:
+               first_block=None, out_arity: int = 0) -> dsl.Fun:
     """The AST of program `pid` (attempt `attempt`): uniform over programs of
-    exactly L tokens with input arity <= min(9, l), output arity <= min(9, s)."""
+    exactly L tokens with input arity <= min(9, l), output arity <= min(9, s)
+    (or exactly `out_arity` when it is nonzero; the arity draw is taken
+    either way, so the body does not depend on it)."""
     if L <= HEADER:
         raise ValueError("L must exceed the %d header tokens" % HEADER)
     rng = _Stream(seed, pid, 0x51A0000 + 4096 * attempt, first_block if attempt == 0 else None)
     nin = 1 + rng.below(min(9, ell))
     nout = 1 + rng.below(min(9, s))
-    return dsl.Fun(nin, nout, _Sampler(L, rng).block(L - HEADER))
+    return dsl.Fun(nin, out_arity or nout, _Sampler(L, rng).block(L - HEADER))
 
 
 def fun_tokens(f: dsl.Fun) -> list:
@@ -249,7 +251,7 @@ def _gen():
         lib = ctypes.CDLL(B.build_generator())
         P, U32, U64 = ctypes.c_void_p, ctypes.c_uint32, ctypes.c_uint64
         lib.gen_halting_programs.argtypes = [P, U64, U64, U64, U32, U32, U32, U32, U32, ctypes.c_int,
-                                             P, P, P, P, P]
+                                             U32, P, P, P, P, P]
         lib.gen_halting_programs.restype = ctypes.c_int
         _gen_lib = lib
     return _gen_lib
@@ -278,7 +280,7 @@ def _flat_tables(L: int):
     return out
 
 
-def _halting_programs_c(num_programs, L, seed, w, n, ell, s, mu, cap, first, read_inputs):
+def _halting_programs_c(num_programs, L, seed, w, n, ell, s, mu, cap, first, read_inputs, out_arity):
     t = _flat_tables(L)
     keep = [t["s"], t["b"]]
     ptr = lambda x: x.ctypes.data
@@ -289,33 +291,41 @@ def _halting_programs_c(num_programs, L, seed, w, n, ell, s, mu, cap, first, rea
     to = np.zeros(num_programs + 1, np.uint64)
     red = np.zeros(1, np.uint64)
     rc = _gen().gen_halting_programs(ctypes.byref(T), seed, first, num_programs, ell, s, mu, n, w,
-                                     1 if read_inputs else 0, ptr(words), ptr(po), ptr(tape), ptr(to), ptr(red))
+                                     1 if read_inputs else 0, out_arity, ptr(words), ptr(po), ptr(tape), ptr(to),
+                                     ptr(red))
     del keep
     if rc != 0:
         raise RuntimeError("the C program sampler rejected its parameters")
     return W.Workload("halting", words[:int(po[-1])].copy(), po, np.full(num_programs, n, np.uint32),
                       tape[:int(to[-1])].copy(), to, np.full(num_programs, cap, np.uint64), ell, s, w,
-                      meta=dict(L=L, seed=seed, redraws=int(red[0]), read_inputs=read_inputs))
+                      meta=dict(L=L, seed=seed, redraws=int(red[0]), read_inputs=read_inputs,
+                                out_arity=out_arity))
 
 
 def halting_programs(num_programs: int, L: int = 100, seed: int = 6, w: int = 32, n: int = 250,
                      ell: int = 10, s: int = 2, mu: int = 10, cap: int = 10 ** 6,
-                     first: int = 0, read_inputs: bool = False, impl: str = "c") -> W.Workload:
+                     first: int = 0, read_inputs: bool = False, impl: str = "c",
+                     out_arity: int = 0) -> W.Workload:
     """The Sec. 3 halting workload: programs k = first .. first+count-1, each
     drawn uniformly among valid programs of L tokens and lowered by the
     Sec. 2.2 rules, on an input tape x of N uniform w-bit words. As printed,
     the Fun rule reads no input (so ipt starts at zero and x is inert, as in
-    App. B); read_inputs=True prepends one RD per input word. impl = "c" uses
-    the C transcription (progsampler.c, the same words), "py" this module."""
+    App. B); read_inputs=True prepends one RD per input word. out_arity 0
+    draws the output arity e uniformly from 1..min(9, s) as the grammar
+    allows; 1..min(9, s) fixes it (the program bodies stay the same). impl =
+    "c" uses the C transcription (progsampler.c, the same words), "py" this
+    module."""
+    if not 0 <= out_arity <= min(9, s):
+        raise ValueError("out_arity must be 0 (drawn) or in 1..min(9, s)")
     if impl == "c":
-        return _halting_programs_c(num_programs, L, seed, w, n, ell, s, mu, cap, first, read_inputs)
+        return _halting_programs_c(num_programs, L, seed, w, n, ell, s, mu, cap, first, read_inputs, out_arity)
     ids = np.arange(first, first + num_programs, dtype=np.uint64)
     blocks = W.draws(seed, 0x51A0000, ids, 64)
     progs, tapes, redraws = [], [], 0
     for k, pid in enumerate(ids):
         attempt = 0
         while True:
-            f = sample_fun(L, seed, int(pid), ell, s, attempt, blocks[k])
+            f = sample_fun(L, seed, int(pid), ell, s, attempt, blocks[k], out_arity)
             low = dsl.lower(f, ell=ell, s=s, mu=mu, read_inputs=read_inputs)
             if low.min_mem <= n:
                 break
@@ -337,7 +347,7 @@ def halting_programs(num_programs: int, L: int = 100, seed: int = 6, w: int = 32
     flat = np.concatenate(progs) if progs else np.zeros(0, np.int64)
     return W.Workload("halting", flat, off, np.full(num_programs, n, np.uint32), tape, tape_off,
                       np.full(num_programs, cap, np.uint64), ell, s, w,
-                      meta=dict(L=L, seed=seed, redraws=redraws, read_inputs=read_inputs))
+                      meta=dict(L=L, seed=seed, redraws=redraws, read_inputs=read_inputs, out_arity=out_arity))
 
 
 def concat(parts) -> W.Workload:

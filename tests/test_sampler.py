@@ -90,14 +90,15 @@ def test_deterministic_and_chunked_generation_equal():
     assert (a.tapes >= 0).all() and (a.tapes < 2 ** 32).all()
 
 
-@pytest.mark.parametrize("L,read_inputs,w,n,first", [(100, False, 32, 250, 0), (100, True, 64, 250, 9000),
-                                                     (60, False, 8, 250, 3), (100, False, 32, 130, 0),
-                                                     (160, True, 32, 250, 11)])
-def test_c_sampler_equals_the_python_definition(L, read_inputs, w, n, first):
+@pytest.mark.parametrize("L,read_inputs,w,n,first,e", [(100, False, 32, 250, 0, 0), (100, True, 64, 250, 9000, 0),
+                                                       (60, False, 8, 250, 3, 0), (100, False, 32, 130, 0, 0),
+                                                       (160, True, 32, 250, 11, 0), (100, False, 32, 250, 0, 1),
+                                                       (100, True, 32, 130, 5, 2)])
+def test_c_sampler_equals_the_python_definition(L, read_inputs, w, n, first, e):
     """progsampler.c draws the same programs and tapes as this module (word for
     word), including redraws when a lowering does not fit n words."""
-    a = S.halting_programs(1500, L=L, read_inputs=read_inputs, w=w, n=n, first=first, impl="py")
-    b = S.halting_programs(1500, L=L, read_inputs=read_inputs, w=w, n=n, first=first, impl="c")
+    a = S.halting_programs(1500, L=L, read_inputs=read_inputs, w=w, n=n, first=first, impl="py", out_arity=e)
+    b = S.halting_programs(1500, L=L, read_inputs=read_inputs, w=w, n=n, first=first, impl="c", out_arity=e)
     for f in ("programs", "prog_off", "tapes", "tape_off", "caps", "mem_words"):
         assert np.array_equal(getattr(a, f), getattr(b, f)), f
     assert a.meta["redraws"] == b.meta["redraws"]
@@ -120,3 +121,19 @@ def test_minimum_halting_time_under_both_input_readings():
         st, _ = oracle_state(wl, threads=os.cpu_count() or 1)
         halted = st.steps[st.status == 1]
         assert int(halted.min()) == want, (read_inputs, int(halted.min()))
+
+
+def test_fixed_output_arity_keeps_the_body():
+    """out_arity fixes e (every program ends in exactly e PRIs and the HLT
+    pair) while the body drawn for program k stays the same."""
+    from paper_2604_12902_gb300 import dsl
+    for pid in range(200):
+        drawn = S.sample_fun(100, 6, pid)
+        fixed = S.sample_fun(100, 6, pid, out_arity=1)
+        assert fixed.out_arity == 1 and fixed.body == drawn.body and fixed.arity == drawn.arity
+    wl = S.halting_programs(300, out_arity=2, impl="c")
+    for k in range(wl.num_vms):
+        p = wl.programs[int(wl.prog_off[k]):int(wl.prog_off[k + 1])]
+        assert list(p[-2:]) == [0, 0] and list(p[-6:-2:2]) == [dsl.PRI, dsl.PRI] and p[-8] != dsl.PRI
+    with pytest.raises(ValueError):
+        S.halting_programs(10, s=2, out_arity=3)

@@ -357,7 +357,11 @@ int rasp_pool_read(rasp_pool* p, uint64_t ticket, rasp_state_view* out);
 int rasp_pool_cancel(rasp_pool* p, uint64_t ticket);
 /* Bytes of the arena in use, requests waiting, requests running. */
 int rasp_pool_info(rasp_pool* p, uint64_t* in_use, uint64_t* waiting, uint64_t* running);
+/* Wait for the requests still running, discard every request (running,
+ * done or waiting; their results are lost), free the arena and the pool.
+ * NULL is a no-op. */
 void rasp_pool_destroy(rasp_pool* p);
+/* Thread-local description of the last pool error on this thread. */
 const char* rasp_pool_last_error(void);
 
 /* Free the batch (synchronises its stream first). NULL is a no-op. */

@@ -87,3 +87,23 @@ def test_histogram_rejects_bad_edges(rasp):
         counts, other = b.halting_histogram(np.array([0, 1 << 62], np.uint64))
         st = b.read_state(mem=False)
         assert int(counts[0]) == int((st["status"] == 1).sum())
+
+
+def test_histogram_at_the_maximum_bin_count(rasp):
+    """4096 unit bins (the documented maximum; the edges and counters need
+    more than the default 48 KB of shared memory) equal numpy on the
+    read-back state; 4097 bins are refused."""
+    wl = S.halting_programs(20000, L=100, seed=8, cap=5000)
+    edges = np.arange(0, 4097, dtype=np.uint64)
+    with rasp.Batch(wl.mem_words, wl.ell, wl.s, word_bits=wl.w) as b:
+        b.load_workload(wl)
+        b.run()
+        got = b.read_state(mem=False)
+        counts, other = b.halting_histogram(edges)
+        with pytest.raises(rasp.RaspError) as e:
+            b.halting_histogram(np.arange(0, 4098, dtype=np.uint64))
+        assert e.value.code == rasp.RASP_EINVAL
+    want_c, want_o = expected_histogram(got["steps"], got["status"], edges)
+    assert counts.shape == (4096,)
+    assert np.array_equal(counts, want_c) and np.array_equal(other, want_o)
+    assert int(want_c.sum()) > 10000 and int(np.count_nonzero(want_c)) > 30

@@ -336,7 +336,9 @@ typedef struct rasp_request {
  * cannot be allocated. */
 int rasp_pool_create(const rasp_config* cfg, uint64_t arena_bytes, rasp_pool** out);
 /* Copies the request's inputs (host memory), queues it and admits what fits.
- * EINVAL for a malformed request, ENOMEM if it could never fit the arena.
+ * EINVAL for a malformed request (no VMs or programs; mem_words, offsets or
+ * tape_off NULL; words or tape NULL while the offsets ask for words), ENOMEM
+ * if it could never fit the arena.
  * Load errors found at admission are reported by rasp_pool_read. */
 int rasp_pool_submit(rasp_pool* p, const rasp_request* req, uint64_t* ticket);
 /* Non-blocking: *state = enum rasp_request_state; also admits waiting work. */

@@ -203,6 +203,11 @@ int rasp_pool_submit(rasp_pool* p, const rasp_request* q, uint64_t* ticket) {
   if (!p || !q || !ticket) return pfail(RASP_EINVAL, "pool, request or ticket is NULL");
   if (!q->num_vms || !q->mem_words || !q->offsets || !q->tape_off)
     return pfail(RASP_EINVAL, "request needs num_vms, mem_words, offsets and tape_off");
+  // a waiting request copies its inputs before they are validated by the
+  // loads at admission: refuse buffers that the copy itself would read wrongly
+  if (!q->num_programs) return pfail(RASP_EINVAL, "request has no programs");
+  if (q->offsets[q->num_programs] && !q->words) return pfail(RASP_EINVAL, "words is NULL");
+  if (q->tape_off[q->num_vms] && !q->tape) return pfail(RASP_EINVAL, "tape is NULL");
   uint64_t need = 0;
   int rc = rasp_batch_bytes(&p->cfg, q->num_vms, q->mem_words, &need);
   if (rc) return pfail(rc, std::string("request rejected: ") + rasp_last_error());

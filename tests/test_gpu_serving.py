@@ -147,3 +147,31 @@ def test_next_done_hands_out_every_request_once(serving):
                 break
         assert sorted(seen) == sorted(tickets)
         assert pool.next_done() == 0
+
+
+def test_submit_refuses_null_buffers(serving):
+    """Requests whose buffers a waiting copy would misread are refused at
+    submit (EINVAL), the pool stays usable."""
+    import ctypes
+    R, S = serving
+    wl = request(500, 0)
+    pool = S.Pool(1 << 28, wl.ell, wl.s)
+    try:
+        po = np.ascontiguousarray(wl.prog_off, np.uint64)
+        to = np.ascontiguousarray(wl.tape_off, np.uint64)
+        mem = np.ascontiguousarray(wl.mem_words, np.uint32)
+        tape = np.ascontiguousarray(wl.tapes, np.int64)
+        words = np.ascontiguousarray(wl.programs, np.int64)
+        L = S._lib()
+        t = ctypes.c_uint64(0)
+        for w_ptr, t_ptr, nprog in ((None, R._p(tape), wl.num_vms), (R._p(words), None, wl.num_vms),
+                                    (R._p(words), R._p(tape), 0)):
+            q = S.rasp_request(w_ptr, R._p(po), nprog, None, t_ptr, R._p(to), None, R._p(mem), wl.num_vms,
+                               R.U64_MAX)
+            assert L.rasp_pool_submit(pool.h, ctypes.byref(q), ctypes.byref(t)) == R.RASP_EINVAL
+        st, _ = oracle_state(wl, threads=THREADS)
+        k = pool.submit(wl)
+        wait(pool, k)
+        assert_same_state(pool.read(k), st, wl.ell, wl.s, what="after refused submits")
+    finally:
+        pool.close()

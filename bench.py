@@ -164,6 +164,16 @@ def profiled_traffic(vm_steps: int):
         return None
 
 
+def outcomes(stats) -> dict:
+    """Final statuses of the batch after a step, with the realised timeout
+    rate (the fraction of VMs stopped by their step cap)."""
+    keys = ("halted", "timeout", "running", "fault_overflow", "fault_addr")
+    out = {k: int(stats[k]) for k in keys}
+    total = sum(out.values())
+    out["timeout_frac"] = out["timeout"] / total if total else 0.0
+    return out
+
+
 def algorithmic_bytes(stats) -> float:
     ops = stats["op_steps"]
     b = sum(BYTES_PER_OP[k] * ops[k] for k in range(1, 8))
@@ -496,7 +506,8 @@ def main():
                            "schedule_flags": args.flags, "isa": args.isa, "parallelism": "vm shards x%d" % ws,
                            "schedule": tuned["chosen"] if tuned else "flags %#x" % args.flags},
                 "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "plain": plain,
-                "gpu_launches": (1 + run_launches + (1 if hist else 0)) * args.steps, "clocks": clocks}
+                "gpu_launches": (1 + run_launches + (1 if hist else 0)) * args.steps, "clocks": clocks,
+                "outcomes": outcomes(st)}
         if hist:
             c, o = hist["counts"], hist["other"]
             halted = int(c.sum() + o[3])

@@ -19,3 +19,10 @@ def test_reference_arm_prints_the_contract_line():
     assert line["impl"] == "reference" and line["value"] > 0 and line["higher_is_better"] is True
     assert line["cpu_baseline"]["kind"] == "oracle" and line["cpu_baseline"]["cores"] >= 1
     assert line["e2e"]["h2d_bytes_per_step"] == 0 and line["e2e"]["value"] == line["value"]
+
+
+def test_outcomes_reports_the_realised_timeout_rate():
+    import bench
+    o = bench.outcomes(dict(vm_steps=9, running=1, halted=6, timeout=3, fault_overflow=0, fault_addr=0))
+    assert o["timeout"] == 3 and o["halted"] == 6 and abs(o["timeout_frac"] - 0.3) < 1e-12
+    assert bench.outcomes(dict(running=0, halted=0, timeout=0, fault_overflow=0, fault_addr=0))["timeout_frac"] == 0.0

@@ -117,3 +117,21 @@ def test_parser_rejects_bad_programs():
                 "fun f0(ipt: W ^ 1) -> W ^ 1 { opt[10] = 1 }"]:
         with pytest.raises(SyntaxError):
             dsl.parse(bad)
+
+
+def test_readme_example_results():
+    """The README's quick-start program gives the results printed there
+    (status HALTED, 6 steps, first outputs 12 and 2), by the oracle."""
+    import os
+    import re
+    from oracle import spec
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    text = open(os.path.join(root, "README.md")).read()
+    m = re.search(r"^prog = (\[[-0-9, ]+\])$", text, flags=re.M)
+    assert m, "README example program not found"
+    prog = [int(v) for v in m.group(1).strip("[]").split(",")]
+    assert "# [1 1] [6 6] [12  2]" in text
+    for x, y1 in (([7], 12), ([-3], 2)):
+        c = spec.initial(prog, [v % (1 << 64) for v in x], 16, 2, 2, 64)
+        (i, a, M, u, y), steps, status = spec.run(c, 2, 2, 64, 10 ** 6)
+        assert (status, steps, y[0], y[1]) == (1, 6, 1, y1)

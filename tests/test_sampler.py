@@ -137,3 +137,48 @@ def test_fixed_output_arity_keeps_the_body():
         assert list(p[-2:]) == [0, 0] and list(p[-6:-2:2]) == [dsl.PRI, dsl.PRI] and p[-8] != dsl.PRI
     with pytest.raises(ValueError):
         S.halting_programs(10, s=2, out_arity=3)
+
+
+def _fig1b():
+    """(counts for tau_h = 1..99, mass at >= 100, total) printed in Fig. 1b."""
+    import os
+    path = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", "fig1b_counts.txt")
+    c = np.zeros(100)
+    long_ = 0
+    for line in open(path):
+        if line.startswith("#") or not line.strip():
+            continue
+        k, v = line.split()
+        if k.isdigit():
+            c[int(k)] = int(v)
+        else:
+            long_ += int(v)
+    return c, long_, c.sum() + long_
+
+
+def _distance_to_fig1b(wl):
+    """Total variation distance between the tau_h distribution of `wl` (bins
+    1..99 and the mass at >= 100, halting or not) and Fig. 1b's."""
+    from tests.helpers import oracle_state
+    c, long_, total = _fig1b()
+    st, _ = oracle_state(wl, threads=os.cpu_count() or 1)
+    t = st.steps[st.status == 1].astype(np.int64)
+    q = np.bincount(t[t < 100], minlength=100)[:100].astype(float)
+    ours = np.concatenate([q, [wl.num_vms - q.sum()]]) / wl.num_vms
+    paper = np.concatenate([c, [long_]]) / total
+    return 0.5 * np.abs(ours - paper).sum()
+
+
+def test_fig1b_counts_and_the_distance_of_the_readings():
+    """Fig. 1b's printed counts (8e6 programs, 3.36 % not halted within 10^6
+    steps) against the sampler + lowering + oracle: the printed-rule reading
+    is within about 0.2 in total variation, and fixing the output arity at 1
+    (the App. B programs' arity) comes closer."""
+    c, long_, total = _fig1b()
+    assert abs(total - 8e6) < 100 and abs(269104 / total - 0.0336) < 5e-5
+    assert c[:5].sum() == 0 and c[5] == 15462 and c.argmax() == 6   # nothing below 5; tau = 6 the mode
+    kw = dict(L=100, seed=6, w=32, n=250, ell=10, s=2, cap=10 ** 4)
+    d_default = _distance_to_fig1b(S.halting_programs(50000, **kw))
+    d_e1 = _distance_to_fig1b(S.halting_programs(50000, out_arity=1, **kw))
+    assert 0.15 < d_default < 0.27, d_default
+    assert d_e1 < d_default - 0.01, (d_e1, d_default)

@@ -67,3 +67,46 @@ def test_shard_range_is_disjoint_and_contiguous():
     assert ranges == [(0, 1000), (1000, 1000), (2000, 1000), (3000, 1000)]
     with pytest.raises(ValueError):
         shards.shard_range(-1, 10)
+
+
+def _best_bottleneck(c, k):
+    """Smallest possible largest range cost over all splits of c into at most
+    k contiguous ranges (brute force by dynamic programming)."""
+    import functools
+    pre = np.concatenate([[0], np.cumsum(c)])
+
+    @functools.lru_cache(maxsize=None)
+    def f(i, k):
+        if i == len(c):
+            return 0
+        if k == 0:
+            return float("inf")
+        return min(max(int(pre[j] - pre[i]), f(j, k - 1)) for j in range(i + 1, len(c) + 1))
+    return f(0, k)
+
+
+def test_balanced_ranges_are_optimal_contiguous_splits():
+    rng = np.random.default_rng(5)
+    for _ in range(300):
+        V = int(rng.integers(1, 13))
+        k = int(rng.integers(1, 5))
+        c = rng.integers(0, 50, size=V)
+        r = shards.balanced_ranges(c, k)
+        assert len(r) == k
+        assert r[0][0] == 0 and all(a[0] + a[1] == b[0] for a, b in zip(r, r[1:]))
+        assert r[-1][0] + r[-1][1] == V
+        worst = max(int(c[f:f + n].sum()) for f, n in r)
+        assert worst == _best_bottleneck(tuple(int(x) for x in c), k)
+
+
+def test_balanced_ranges_on_the_uneven_batch():
+    """Caps of the uneven batch vary over three orders of magnitude: balanced
+    ranges differ from equal counts and cut the largest shard's cap sum."""
+    wl = W.uneven_programs(num_vms=4096, seed=3)
+    cost = shards.estimated_cost(wl)
+    r = shards.balanced_ranges(cost, 4)
+    worst = max(int(cost[f:f + n].sum()) for f, n in r)
+    equal = max(int(cost[k * 1024:(k + 1) * 1024].sum()) for k in range(4))
+    assert worst <= equal and worst - int(cost.sum()) / 4 <= int(cost.max())
+    sub = W.uneven_programs(num_vms=r[2][1], seed=3, first_vm=r[2][0])
+    assert np.array_equal(sub.caps, wl.caps[r[2][0]:r[2][0] + r[2][1]])

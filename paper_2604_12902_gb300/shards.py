@@ -79,3 +79,17 @@ def combine(dist, elapsed_ms: float, vm_steps: int, device=None) -> tuple[float,
     dist.all_reduce(t, op=dist.ReduceOp.MAX)
     dist.all_reduce(n, op=dist.ReduceOp.SUM)
     return float(t.item()), int(n.item())
+
+
+def combine_counts(dist, counts, device=None):
+    """Element-wise sum over ranks of a small integer array (a tau_h
+    histogram, status counts): the only other exchange the sharded path has.
+    `dist` as for combine; returns a numpy int64 array."""
+    import numpy as np
+    a = np.asarray(counts, np.int64)
+    if dist is None:
+        return a.copy()
+    import torch
+    t = torch.as_tensor(a, device=device).clone()
+    dist.all_reduce(t, op=dist.ReduceOp.SUM)
+    return t.cpu().numpy()

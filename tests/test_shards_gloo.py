@@ -3,8 +3,9 @@
 Every rank generates its own disjoint shard of the template workload and runs
 it through the oracle; nothing is exchanged but the final reduction. The
 shards must partition the one-process workload exactly -- the same programs,
-tapes and caps, VM by VM -- and the reduction must give the total VM-steps and
-the slowest rank's time, as bench.py reports them."""
+tapes and caps, VM by VM -- and the reductions must give the total VM-steps,
+the slowest rank's time (as bench.py reports them) and the whole batch's
+tau_h histogram."""
 import os
 import socket
 
@@ -15,6 +16,7 @@ from paper_2604_12902_gb300 import shards, workloads as W
 
 PER_RANK = 384
 WORLD = 2
+HIST_BINS = 4097       # template VMs take at most 4096 steps
 
 
 def _free_port():
@@ -37,8 +39,10 @@ def _rank_main(rank, world, port, out_dir):
                                   wl.ell, wl.s, caps=wl.caps)
         fake_ms = 10.0 + rank                      # the slowest rank's time must win
         ms, steps = shards.combine(dist, fake_ms, int(st.steps.sum()))
+        hist = shards.combine_counts(dist, np.bincount(st.steps.astype(np.int64), minlength=HIST_BINS)[:HIST_BINS])
         np.savez(os.path.join(out_dir, "rank%d.npz" % rank), steps=st.steps, status=st.status, i=st.i,
-                 a=st.a, y=st.y, programs=wl.programs, tapes=wl.tapes, total_ms=ms, total_steps=steps)
+                 a=st.a, y=st.y, programs=wl.programs, tapes=wl.tapes, total_ms=ms, total_steps=steps,
+                 hist=hist)
     finally:
         dist.destroy_process_group()
 
@@ -57,9 +61,11 @@ def test_shards_partition_the_workload_and_reduce(tmp_path):
     np.testing.assert_array_equal(np.concatenate([p["tapes"] for p in parts]), whole.tapes)
     for key in ("steps", "status", "i", "a", "y"):
         np.testing.assert_array_equal(np.concatenate([p[key] for p in parts]), getattr(st, key), err_msg=key)
+    want_hist = np.bincount(st.steps.astype(np.int64), minlength=HIST_BINS)[:HIST_BINS]
     for p in parts:
         assert int(p["total_steps"]) == int(st.steps.sum())
         assert float(p["total_ms"]) == 10.0 + (WORLD - 1)
+        np.testing.assert_array_equal(p["hist"], want_hist)
 
 
 def test_shard_range_is_disjoint_and_contiguous():

@@ -333,3 +333,26 @@ def test_heads_monotone_and_single_word_writes():
             assert u[0] <= u2[0] <= ell and y[0] <= y2[0] <= s
             assert u2[1:] == u[1:]                                    # the tape itself is read-only
             i, a, M, u, y = i2, a2, M2, u2, y2
+
+
+@pytest.mark.parametrize("w", [64, 32, 29, 5, 2])
+@pytest.mark.parametrize("classic", [False, True])
+def test_random_and_template_programs_match_spec_in_every_field(w, classic):
+    """The C oracle and the independent spec.py transcription agree on every
+    field of the final configuration for random programs (self-modifying,
+    n = 64) and template programs (loops, hundreds of steps), at several word
+    sizes and with both opcode sets."""
+    from paper_2604_12902_gb300.workloads import random_programs, template_programs
+    for wl in (random_programs(num_vms=120, seed=13 + w), template_programs(num_vms=12, seed=7 + w)):
+        st, _ = oracle.run_packed(wl.programs, wl.prog_off, wl.mem_words, wl.tapes, wl.tape_off,
+                                  wl.ell, wl.s, caps=wl.caps, w=w, classic=classic)
+        ell, s = wl.ell, wl.s
+        for v in range(wl.num_vms):
+            c0 = spec.initial([int(q) for q in wl.program_of(v)], [int(q) for q in wl.tape_of(v)],
+                              int(wl.mem_words[v]), ell, s, w)
+            (i, a, M, u, y), steps, status = spec.run(c0, ell, s, w, int(wl.caps[v]), classic=classic)
+            assert (int(st.steps[v]), int(st.status[v])) == (steps, status), (v, w, classic)
+            assert (int(st.i[v]), int(st.a[v])) == (i, a)
+            assert [int(q) for q in st.memory(v)] == list(M)
+            assert [int(q) for q in st.u[v * (ell + 1):(v + 1) * (ell + 1)]] == list(u)
+            assert [int(q) for q in st.y[v * (s + 1):(v + 1) * (s + 1)]] == list(y)

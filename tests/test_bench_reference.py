@@ -26,3 +26,17 @@ def test_outcomes_reports_the_realised_timeout_rate():
     o = bench.outcomes(dict(vm_steps=9, running=1, halted=6, timeout=3, fault_overflow=0, fault_addr=0))
     assert o["timeout"] == 3 and o["halted"] == 6 and abs(o["timeout_frac"] - 0.3) < 1e-12
     assert bench.outcomes(dict(running=0, halted=0, timeout=0, fault_overflow=0, fault_addr=0))["timeout_frac"] == 0.0
+
+
+def test_clock_summary_from_nvidia_smi_lines():
+    import bench
+    lines = ["0, 2070, 2070, 812.40, 0x0000000000000000, Not Active, Not Active, Not Active, Not Active",
+             "0, 1980, 2070, 1390.02, 0x0000000000000004, Not Active, Not Active, Not Active, Active",
+             "0, 2070, 2070, 1101.7, 0x0000000000000000, Not Active, Not Active, Not Active, Not Active",
+             "0, [N/A], 2070, 900, 0x0, Not Active, Not Active, Not Active, Not Active",   # unreadable sample
+             "garbage"]
+    c = bench.summarize_clocks(lines)
+    assert c == {"sm_mhz": 2070.0, "sm_max_mhz": 2070.0, "reasons": ["sw_power_cap"], "samples": 3}
+    assert bench.summarize_clocks([]) is None
+    hot = bench.summarize_clocks(["0, 1500, 2070, 1400, 0x48, Active, Not Active, Active, Not Active"])
+    assert hot["reasons"] == ["hw_slowdown", "sw_thermal_slowdown"]

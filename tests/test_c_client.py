@@ -84,3 +84,23 @@ def test_c_client_runs_batches_like_the_oracle(client, tmp_path, case):
     r = subprocess.run([client, str(src), str(dst)], capture_output=True, text=True, timeout=300)
     assert r.returncode == 0, (r.returncode, r.stderr)
     assert_same_state(read_state(dst, wl), st, wl.ell, wl.s, what="C client " + case)
+
+
+def test_header_compiles_and_links_from_cpp(tmp_path):
+    """include/rasp.h is usable from C++ (extern "C" linkage) without a GPU."""
+    from paper_2604_12902_gb300 import build
+    libdir = os.path.dirname(build.build())
+    src = tmp_path / "client.cpp"
+    src.write_text('#include "rasp.h"\n#include <cstdio>\n#include <cstring>\n'
+                   'int main() {\n'
+                   '  rasp_config cfg; std::memset(&cfg, 0, sizeof cfg); cfg.word_bits = 1;\n'
+                   '  uint32_t n[1] = {8}; uint64_t bytes = 0;\n'
+                   '  if (rasp_batch_bytes(&cfg, 1, n, &bytes) != RASP_EINVAL) return 1;\n'
+                   '  std::printf("%s\\n", rasp_version());\n  return 0;\n}\n')
+    exe = str(tmp_path / "client")
+    r = subprocess.run(["g++", "-std=c++11", "-Wall", "-Werror", "-I", os.path.join(ROOT, "include"), str(src),
+                        "-o", exe, "-L", libdir, "-lrasp_gb300", "-Wl,-rpath," + libdir],
+                       capture_output=True, text=True)
+    assert r.returncode == 0, r.stderr
+    r = subprocess.run([exe], capture_output=True, text=True)
+    assert r.returncode == 0 and r.stdout.startswith("rasp_gb300")

@@ -129,7 +129,7 @@ def make_workload(name: str, rank: int, vms: int = 1 << 20, out_arity: int = 0):
         wl = W.uneven_programs(num_vms=vms if vms != 1 << 20 else 1 << 22, seed=3,
                                first_vm=rank * (1 << 22), workers=os.cpu_count() or 1)
         return wl, ("%s uneven programs (length log-U[8,512], n log-U[16,4096], cap log-U[64,65536], "
-                    "~30%% non-halting), l=16, s=8" % format(wl.num_vms, ","))
+                    "15%% built never to halt, ~33%% time out), l=16, s=8" % format(wl.num_vms, ","))
     if name == "shared":
         wl = W.shared_programs()
         return wl, ("16,384 programs (48 instr, loop templates) x 256 tapes of 8 ints U[-50,50] = 4,194,304 VMs, "

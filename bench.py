@@ -149,25 +149,22 @@ def make_workload(name: str, rank: int, vms: int = 1 << 20, out_arity: int = 0):
 
 
 def profiled_traffic(vm_steps: int):
-    """DRAM bytes of one run launch from the committed ncu summary of the run
-    kernel (bytes per VM-step of a captured small case, scaled by VM-steps),
-    or None when the kernel sources changed since that capture."""
+    """DRAM bytes of one run launch from the committed ncu measurement of the
+    run kernel (`profiles/traffic.json`: bytes per VM-step of a captured small
+    case, scaled by VM-steps), or None when a source file the kernel is built
+    from changed since that capture."""
     import hashlib
-    path = os.path.join(ROOT, "profiles", "k_persist_gl_templates_256k.md")
     try:
-        fields = {}
-        for line in open(path):
-            if ":" in line and line.strip().split(":")[0] in ("traffic_bytes_per_vm_step", "kernel_sources_sha256"):
-                k, v = line.strip().split(":", 1)
-                fields[k] = v.strip()
+        with open(os.path.join(ROOT, "profiles", "traffic.json")) as f:
+            rec = json.load(f)["k_persist_gl templates"]
         h = hashlib.sha256()
-        for f in ("engine.cuh", "kernels.cu"):
-            with open(os.path.join(ROOT, "paper_2604_12902_gb300", "csrc", f), "rb") as fh:
+        for name in rec["sources"]:
+            with open(os.path.join(ROOT, "paper_2604_12902_gb300", "csrc", name), "rb") as fh:
                 h.update(fh.read())
-        if h.hexdigest() != fields["kernel_sources_sha256"]:
+        if h.hexdigest() != rec["sources_sha256"]:
             return None
-        return float(fields["traffic_bytes_per_vm_step"]) * vm_steps
-    except (OSError, KeyError, ValueError):
+        return float(rec["dram_bytes_per_vm_step"]) * vm_steps
+    except (OSError, KeyError, ValueError, TypeError):
         return None
 
 

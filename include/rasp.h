@@ -152,6 +152,8 @@ int rasp_batch_bytes(const rasp_config* cfg, uint64_t num_vms,
                      const uint32_t* mem_words, uint64_t* out_bytes);
 
 /* Create a batch of num_vms machines; mem_words[v] = n of VM v (>= 1).
+ * Each machine lives in the configuration space of Sec. 2.1,
+ * C_w = W x W x W^n x W^(l+1) x W^(s+1) (i, a, M, u, y), with its own n.
  * Allocates the structure-of-arrays state store (i, a, steps, cap, status,
  * u_0, y_0 per VM), the per-VM M slabs, the tapes and outputs, and buckets
  * the VMs by n for scheduling. No machine is runnable until both
@@ -183,7 +185,11 @@ int rasp_load_inputs(rasp_batch* b, const int64_t* tape,
 int rasp_reset(rasp_batch* b);
 
 /* Advance every RUNNING machine until it halts (fixed point), faults, or has
- * taken min(max_steps, cap_v) steps in total. steps is cumulative, so
+ * taken min(max_steps, cap_v) steps in total: the one-step transition of
+ * Sec. 2.1 (the case equation over LOD, ADD, MUL, STO, BNZ, RD, PRI) applied
+ * repeatedly, i.e. the vectorised map Phi of Sec. 2 iterated over the batch,
+ * with halting on the fixed-point set F = {c : c -> c} of Sec. 2.1 and
+ * resumable epochs as in the persistent workers of App. A (Alg. 1). steps is cumulative, so
  * rasp_run(T1) followed by rasp_run(T2) equals rasp_run(T2). A VM that stops
  * on the budget (max_steps < cap) stays RUNNING unless it is a fixed point.
  * Asynchronous on the batch stream. ESTATE before both loads. */
@@ -193,7 +199,10 @@ int rasp_run(rasp_batch* b, uint64_t max_steps);
 int rasp_sync(rasp_batch* b);
 
 /* Copy state of VMs [first, first+count) into caller-owned host arrays
- * (synchronises the stream). EINVAL: range outside the batch, mem too small. */
+ * (synchronises the stream): each machine's configuration <i, a, M, u_0, y>
+ * of Sec. 2.1 (u_0 the read head, y_0 the output count, y_1..y_s the
+ * outputs), its applied steps (tau_h of Sec. 3 for a halted machine) and
+ * status. EINVAL: range outside the batch, mem too small. */
 int rasp_read_state(rasp_batch* b, uint64_t first, uint64_t count,
                     rasp_state_view* out);
 
@@ -246,34 +255,46 @@ int rasp_autotune(rasp_batch* b, uint64_t max_steps, uint32_t reps);
 int rasp_describe(const rasp_batch* b, char* buf, uint64_t size);
 
 /* ---- running a caller-owned state store without allocating ---------------
- * The paper has no counterpart to this call: it exists for callers that
- * cannot allocate when they run machines -- code recording a CUDA graph
- * (stream capture forbids cudaMalloc), engines whose device memory belongs
- * to another framework's allocator, real-time loops that must not allocate.
- * rasp_run_static advances VMs [0, num_vms) of a state store that the caller
- * owns, in place, exactly as rasp_run does (same statuses, same cumulative
- * step budget), and calls no cudaMalloc, cudaFree or other allocator.
+ * The paper has no counterpart to this call. It exists for callers that
+ * cannot allocate at the moment they run machines: engines whose device
+ * memory belongs to another framework's allocator (a cudaMalloc behind that
+ * allocator's back breaks its accounting, and fails when it holds the free
+ * memory), and real-time loops that must not allocate (cudaMalloc and
+ * cudaFree can synchronise the device). rasp_run_static advances VMs
+ * [0, num_vms) of a state store that the caller owns, in place, exactly as
+ * rasp_run does (same statuses, same cumulative step budget), and calls no
+ * cudaMalloc, cudaFree or other allocator.
  *
  * Its only extra memory is a fixed scratch area inside the library (a queue
  * of up to RASP_STATIC_MAX_VMS VM ids and a few counters, about 4 MiB) that
  * every GPU loading the library keeps until the process exits. The first
- * call on each device looks up that area's device address (a one-time
- * set-up with that device current); make that first call before any stream
- * capture. Every call on a device shares the area and resets its counters,
- * so calls whose work overlaps on the GPU (e.g. on two streams at once)
- * race: order them on one stream or serialise them.
+ * call on each device does a one-time set-up with that device current: it
+ * looks up that area's device address and loads the call's kernels. Make
+ * that first call before any stream capture. The set-up is cached per device
+ * ordinal; after cudaDeviceReset on a device the cached address is stale, so
+ * do not use this call on a device that was reset in the same process.
+ * Every call on a device shares the area and resets its counters, so calls
+ * whose work overlaps on the GPU (e.g. on two streams at once) race: order
+ * them on one stream or serialise them.
  *
  * Layout of the caller's device buffers (all device pointers, the caller
  * owns them): i, a, steps, cap, status, uhead, ylen, n, mem_off are arrays
  * of num_vms entries as in rasp_state_view (cap = per-VM step cap). VM v's
- * memory is mem[mem_off[v] .. mem_off[v] + n[v]); mem_off[v] must be even
- * and mem 16-byte aligned. The tape of VM v (u_1..u_l, zero padded) is
+ * memory is mem[mem_off[v] .. mem_off[v] + n[v]); mem holds mem_words
+ * int64 words and is 16-byte aligned. For every VM, 1 <= n[v] <= 2^31-1,
+ * mem_off[v] is even and mem_off[v] + n[v] rounded up to even is at most
+ * mem_words. The tape of VM v (u_1..u_l, zero padded) is
  * tape[v*lp .. v*lp + l) and its output y_1..y_s is y[v*sp .. v*sp + s),
  * with lp, sp = in_cap, out_cap rounded up to even; tape and y 16-byte
- * aligned. Words must already be reduced to w bits.
+ * aligned and num_vms*lp, num_vms*sp words long. Words must already be
+ * reduced to w bits.
+ * The per-VM layout is checked on the device: a RUNNING VM that breaks one
+ * of the rules on n and mem_off is not run (its state is left unchanged)
+ * and is counted in *rejected, an optional caller-owned device uint32 that
+ * the call sets to 0 first (NULL: not reported).
  * Returns RASP_EINVAL for num_vms > RASP_STATIC_MAX_VMS, bad w/semantics,
- * NULL or misaligned buffers, RASP_ECUDA if a CUDA call fails; the message
- * goes to err_buf (if given). Asynchronous on `stream`. */
+ * NULL or misaligned buffers, mem_words = 0, RASP_ECUDA if a CUDA call
+ * fails; the message goes to err_buf (if given). Asynchronous on `stream`. */
 #define RASP_STATIC_MAX_VMS (1u << 20)
 
 typedef struct rasp_static_run {
@@ -299,6 +320,8 @@ typedef struct rasp_static_run {
     char*           err_buf;     /* optional: receives an error message */
     uint32_t        err_buf_size;
     uint32_t        reserved;
+    uint64_t        mem_words;   /* words in mem (bounds every VM's slab) */
+    uint32_t*       rejected;    /* optional device word: VMs refused for their layout */
 } rasp_static_run;
 
 int rasp_run_static(const rasp_static_run* run);

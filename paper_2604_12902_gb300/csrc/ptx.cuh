@@ -1,5 +1,6 @@
 // ptx.cuh -- inline-PTX wrappers for sm_103a: mbarrier and 1-D bulk async
-// copies (the TMA bulk path, cp.async.bulk). No multicast is used anywhere.
+// copies (the TMA bulk path, cp.async.bulk). Every copy moves data between
+// this GPU's global memory and the issuing CTA's own shared memory.
 #pragma once
 
 #include <cstdint>
@@ -15,7 +16,7 @@ __device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
 }
 
 __device__ __forceinline__ void fence_mbar_init() {
-  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");   // the only scope PTX offers
 }
 
 // Arrive once on the barrier and add `bytes` to the transaction count that
@@ -49,7 +50,7 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint32_t bar, uint32_t parity,
 // dst and src 16-byte aligned, bytes a multiple of 16.
 __device__ __forceinline__ void bulk_g2s(uint32_t dst, const void* src, uint32_t bytes, uint32_t bar) {
   asm volatile(
-      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(dst),
+      "cp.async.bulk.shared::cta.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(dst),
       "l"(src), "r"(bytes), "r"(bar)
       : "memory");
 }

@@ -2,12 +2,13 @@
 // allocating anything.
 //
 // Some callers cannot call cudaMalloc (or any allocator) at the moment they
-// want to run machines: code executing while a CUDA stream is being
-// captured into a graph, engines whose device memory is owned and accounted
-// by another framework's allocator, and hard-real-time loops where an
-// allocation (and the implicit synchronisation it can cause) is not
-// allowed. rasp_run_static serves them: the caller passes device pointers to
-// its own state store and the call allocates no device or host memory.
+// want to run machines: engines whose device memory is owned and accounted
+// by another framework's allocator (a cudaMalloc behind its back breaks its
+// accounting and can fail when that allocator holds the free memory), and
+// real-time loops where an allocation, and the device-wide synchronisation
+// cudaMalloc/cudaFree can cause, is not allowed. rasp_run_static serves
+// them: the caller passes device pointers to its own state store and the
+// call allocates no device or host memory.
 //
 // The only memory it needs beyond the caller's buffers is a work queue of
 // VM ids plus a few counters. That scratch is the file-scope array
@@ -16,6 +17,13 @@
 // code the array's name is only a host-side stand-in, so the first call on
 // each device looks up its device address with cudaGetSymbolAddress (with
 // that device current) and passes that address to the kernels.
+//
+// The caller's per-VM layout (n, mem_off) lives in device memory, where the
+// host cannot check it without a copy. The queueing kernel checks it per VM
+// instead: a VM whose n is outside 1..2^31-1, whose mem_off is odd, or whose
+// slab does not lie inside mem[0, mem_words) is not queued (so no kernel
+// ever reads or writes outside the caller's buffers for it) and is counted
+// in the caller's optional `rejected` word.
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
@@ -27,7 +35,7 @@
 namespace rasp {
 namespace {
 
-constexpr uint32_t kHeader = 64;   // words before the id queue: [0] queued VMs, [1] queue head, [2] error flag
+constexpr uint32_t kHeader = 64;   // words before the id queue: [0] queued VMs, [1] queue head
 constexpr uint32_t kMaxDevices = 64;
 
 static __device__ __align__(256) uint32_t g_static_scratch[kHeader + RASP_STATIC_MAX_VMS];
@@ -51,17 +59,33 @@ int report(const rasp_static_run* r, int code, const char* fmt, ...) {
   return code;
 }
 
-// Queue the ids of the machines that are still RUNNING (warp-aggregated).
-__global__ void __launch_bounds__(256) k_static_compact(const uint8_t* __restrict__ status, uint32_t num_vms,
-                                                        uint32_t* __restrict__ scratch) {
+// Queue the ids of the machines that are still RUNNING and whose memory
+// layout is valid (warp-aggregated); count the RUNNING machines refused for
+// their layout in *rejected (if given).
+__global__ void __launch_bounds__(256) k_static_compact(const uint8_t* __restrict__ status,
+                                                        const uint32_t* __restrict__ n,
+                                                        const uint64_t* __restrict__ mem_off, uint32_t num_vms,
+                                                        uint64_t mem_words, uint32_t* __restrict__ scratch,
+                                                        uint32_t* __restrict__ rejected) {
   const uint32_t lane = threadIdx.x & 31u;
   const uint32_t stride = gridDim.x * blockDim.x;
   for (uint32_t base = blockIdx.x * blockDim.x; base < num_vms; base += stride) {
     const uint32_t v = base + threadIdx.x;
-    const bool run = v < num_vms && status[v] == ST_RUNNING;
+    bool run = v < num_vms && status[v] == ST_RUNNING;
+    bool bad = false;
+    if (run) {
+      // the slab is read in aligned 16-byte pairs, so its even-padded length
+      // must fit: mem_off even, 1 <= n < 2^31, mem_off + even(n) <= mem_words
+      const uint64_t nn = n[v], off = mem_off[v];
+      const uint64_t npad = (nn + 1ull) & ~1ull;
+      bad = nn == 0ull || nn >= (1ull << 31) || (off & 1ull) || off > mem_words || npad > mem_words - off;
+      run = !bad;
+    }
     const uint32_t m = __ballot_sync(0xffffffffu, run);
+    const uint32_t mb = __ballot_sync(0xffffffffu, bad);
     uint32_t first = 0;
     if (lane == 0 && m) first = atomicAdd(&scratch[0], (uint32_t)__popc(m));
+    if (lane == 0 && mb && rejected) atomicAdd(rejected, (uint32_t)__popc(mb));
     first = __shfl_sync(0xffffffffu, first, 0);
     if (run) scratch[kHeader + first + __popc(m & ((1u << lane) - 1u))] = v;
   }
@@ -150,6 +174,8 @@ extern "C" int rasp_run_static(const rasp_static_run* r) {
   if (!r->i || !r->a || !r->steps || !r->cap || !r->status || !r->uhead || !r->ylen || !r->n || !r->mem_off ||
       !r->mem || (r->in_cap && !r->tape) || (r->out_cap && !r->y))
     return report(r, RASP_EINVAL, "a state-store pointer is NULL");
+  if (r->mem_words == 0) return report(r, RASP_EINVAL, "mem_words (the size of mem) must be given");
+  if (reinterpret_cast<uintptr_t>(r->rejected) & 3u) return report(r, RASP_EINVAL, "rejected must be 4-byte aligned");
   if ((reinterpret_cast<uintptr_t>(r->mem) & 15u) || (reinterpret_cast<uintptr_t>(r->tape) & 15u) ||
       (reinterpret_cast<uintptr_t>(r->y) & 15u))
     return report(r, RASP_EINVAL, "mem, tape and y must be 16-byte aligned");
@@ -174,6 +200,14 @@ extern "C" int rasp_run_static(const rasp_static_run* r) {
       int sms = 0;
       e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
       if (e != cudaSuccess) return report(r, RASP_ECUDA, "cudaDeviceGetAttribute: %s", cudaGetErrorString(e));
+      // load every kernel of this file now, so that no later call loads code
+      cudaFuncAttributes fa;
+      const void* fns[] = {(const void*)k_static_compact, (const void*)pick(false, false),
+                           (const void*)pick(true, false), (const void*)pick(false, true)};
+      for (const void* f : fns) {
+        e = cudaFuncGetAttributes(&fa, f);
+        if (e != cudaSuccess) return report(r, RASP_ECUDA, "cudaFuncGetAttributes: %s", cudaGetErrorString(e));
+      }
       s.scratch = static_cast<uint32_t*>(ptr);
       s.sms = sms;
       s.done = true;
@@ -204,17 +238,19 @@ extern "C" int rasp_run_static(const rasp_static_run* r) {
   P.s = r->out_cap;
   P.ellp = (r->in_cap + 1u) & ~1u;
   P.sp = (r->out_cap + 1u) & ~1u;
-  P.err = reinterpret_cast<int*>(setup.scratch + 2);
+  P.err = nullptr;     // the static kernels have no bounded wait to report
   P.hist = nullptr;
   cudaStream_t stream = static_cast<cudaStream_t>(r->stream);
 
   // the queue counters start at zero on every call (the ids need no clearing)
   e = cudaMemsetAsync(setup.scratch, 0, kHeader * sizeof(uint32_t), stream);
+  if (e == cudaSuccess && r->rejected) e = cudaMemsetAsync(r->rejected, 0, sizeof(uint32_t), stream);
   if (e != cudaSuccess) return report(r, RASP_ECUDA, "cudaMemsetAsync: %s", cudaGetErrorString(e));
   const uint32_t V = (uint32_t)r->num_vms;
   uint32_t cblocks = (V + 255u) / 256u;
   if (cblocks > (uint32_t)setup.sms * 8u) cblocks = (uint32_t)setup.sms * 8u;
-  k_static_compact<<<cblocks, 256, 0, stream>>>(r->status, V, setup.scratch);
+  k_static_compact<<<cblocks, 256, 0, stream>>>(r->status, r->n, r->mem_off, V, r->mem_words, setup.scratch,
+                                                 r->rejected);
   uint32_t grid = (uint32_t)(per_sm * setup.sms);
   const uint32_t useful = (V + 127u) / 128u;
   if (grid > useful) grid = useful;

@@ -346,7 +346,8 @@ class rasp_static_run(ctypes.Structure):
                 ("num_vms", ctypes.c_uint64), ("word_bits", ctypes.c_uint32),
                 ("semantics", ctypes.c_uint32), ("in_cap", ctypes.c_uint32), ("out_cap", ctypes.c_uint32),
                 ("max_steps", ctypes.c_uint64), ("stream", ctypes.c_void_p), ("err_buf", ctypes.c_char_p),
-                ("err_buf_size", ctypes.c_uint32), ("reserved", ctypes.c_uint32)]
+                ("err_buf_size", ctypes.c_uint32), ("reserved", ctypes.c_uint32),
+                ("mem_words", ctypes.c_uint64), ("rejected", ctypes.c_void_p)]
 
 
 RASP_STATIC_MAX_VMS = 1 << 20

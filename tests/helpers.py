@@ -82,3 +82,25 @@ def assert_same_state(got, st, ell, s, ids=None, what=""):
         if not np.array_equal(gm, st.mem[:gm.shape[0]]):
             bad = np.nonzero(gm != st.mem[:gm.shape[0]])[0]
             raise AssertionError("%s: memory differs at %d words, first word %d" % (what, bad.size, bad[0]))
+
+
+def checked_workload(V=4096, seed=11):
+    """Random programs whose operands straddle [0, n) and whose data are large,
+    so that address and overflow faults both occur under CHECKED semantics
+    (n = 48, 20 instructions, 4 RDs of values near +-2^63 first, cap 500)."""
+    from paper_2604_12902_gb300 import workloads as W
+    ids = np.arange(V, dtype=np.uint64)
+    n = 48
+    ops = np.array([1, 2, 2, 2, 3, 3, 3, 4, 5, 7, 0, 8])[W.uniform_int(W.draws(seed, 1, ids, 20), 0, 11)]
+    arg = W.uniform_int(W.draws(seed, 2, ids, 20), 30, n + 3)
+    arg[:, ::5] -= 36                                           # some negative operands
+    ops[:, :4] = RD                                             # read the large inputs first
+    arg[:, :4] = np.arange(40, 44)
+    prog = np.empty((V, 40), np.int64)
+    prog[:, 0::2] = ops
+    prog[:, 1::2] = arg
+    big = W.uniform_int(W.draws(seed, 3, ids, 4), -(1 << 31), (1 << 31) - 1).astype(np.int64)
+    tape = big * np.int64(1 << 32)
+    return W.Workload("checked", prog.reshape(-1), np.arange(V + 1, dtype=np.uint64) * 40,
+                      np.full(V, n, np.uint32), tape.reshape(-1), np.arange(V + 1, dtype=np.uint64) * 4,
+                      np.full(V, 500, np.uint64), 4, 3)

@@ -6,7 +6,7 @@ import pytest
 
 from paper_2604_12902_gb300 import dsl, workloads as W
 from tests.helpers import (ADD, BNZ, LOD, MUL, PRI, RD, STO, U64, asm, assert_same_state,
-                           batch, busy_beavers, oracle_state)
+                           batch, busy_beavers, checked_workload, oracle_state)
 
 pytestmark = pytest.mark.gpu
 
@@ -123,28 +123,8 @@ def test_busy_beavers_on_gpu(rasp, w):
             assert [int(x) for x in got["steps"]] == [tau for _, tau, _ in bbs]
 
 
-def _checked_workload(V=4096, seed=11):
-    """Random programs whose operands straddle [0, n) and whose data are large,
-    so that address and overflow faults both occur."""
-    ids = np.arange(V, dtype=np.uint64)
-    n = 48
-    ops = np.array([1, 2, 2, 2, 3, 3, 3, 4, 5, 7, 0, 8])[W.uniform_int(W.draws(seed, 1, ids, 20), 0, 11)]
-    arg = W.uniform_int(W.draws(seed, 2, ids, 20), 30, n + 3)
-    arg[:, ::5] -= 36                                           # some negative operands
-    ops[:, :4] = RD                                             # read the large inputs first
-    arg[:, :4] = np.arange(40, 44)
-    prog = np.empty((V, 40), np.int64)
-    prog[:, 0::2] = ops
-    prog[:, 1::2] = arg
-    big = W.uniform_int(W.draws(seed, 3, ids, 4), -(1 << 31), (1 << 31) - 1).astype(np.int64)
-    tape = big * np.int64(1 << 32)
-    return W.Workload("checked", prog.reshape(-1), np.arange(V + 1, dtype=np.uint64) * 40,
-                      np.full(V, n, np.uint32), tape.reshape(-1), np.arange(V + 1, dtype=np.uint64) * 4,
-                      np.full(V, 500, np.uint64), 4, 3)
-
-
 def test_checked_semantics_faults(rasp):
-    wl = _checked_workload()
+    wl = checked_workload()
     st, _ = oracle_state(wl, checked=True)
     counts = np.bincount(st.status, minlength=5)
     assert counts[3] > 50 and counts[4] > 500, counts          # both fault kinds occur
@@ -156,7 +136,7 @@ def test_checked_semantics_faults(rasp):
 
 
 def test_wrap_semantics_never_faults(rasp):
-    wl = _checked_workload()
+    wl = checked_workload()
     st, _ = oracle_state(wl)
     got, stats = run_gpu(rasp, wl, 0)
     assert_same_state(got, st, wl.ell, wl.s, what="wrap")

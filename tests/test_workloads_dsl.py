@@ -119,18 +119,12 @@ def test_parser_rejects_bad_programs():
             dsl.parse(bad)
 
 
-def test_readme_example_results():
-    """The README's quick-start program gives the results printed there
-    (status HALTED, 6 steps, first outputs 12 and 2), by the oracle."""
-    import os
-    import re
+def test_quick_start_example_results():
+    """The Python quick-start example program (RD 14; LOD 5; ADD 14; STO 15;
+    PRI 15; LOD 1; BNZ 12, n = 16, l = s = 2) halts after 6 steps with first
+    output x + 5, on the example's inputs (7 -> 12, -3 -> 2), by the oracle."""
     from oracle import spec
-    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
-    text = open(os.path.join(root, "README.md")).read()
-    m = re.search(r"^prog = (\[[-0-9, ]+\])$", text, flags=re.M)
-    assert m, "README example program not found"
-    prog = [int(v) for v in m.group(1).strip("[]").split(",")]
-    assert "# [1 1] [6 6] [12  2]" in text
+    prog = [6, 14, 1, 5, 2, 14, 4, 15, 7, 15, 1, 1, 5, 12]
     for x, y1 in (([7], 12), ([-3], 2)):
         c = spec.initial(prog, [v % (1 << 64) for v in x], 16, 2, 2, 64)
         (i, a, M, u, y), steps, status = spec.run(c, 2, 2, 64, 10 ** 6)

@@ -88,6 +88,10 @@ enum rasp_semantics {
                                           between rounds; by default only
                                           batches larger than the resident
                                           lanes do                             */
+#define RASP_STEP_BLOCK        0x20000u /* HBM-slab persistent schedule: evaluate
+                                          every step as one predicated block
+                                          (the earlier form) instead of the
+                                          epoch loop that leaves by warp vote */
 #define RASP_ISA_CLASSIC       0x8000u /* the classic RASP opcode set (Sec. 1.1)
                                           on the same words: opcode 3 is SUB
                                           (a - M_j mod 2^w), opcode 5 is BPA
@@ -106,7 +110,8 @@ typedef struct rasp_config {
     uint32_t warps_per_cta; /* persistent kernels: warps per CTA (SMEM-staged
                             up to 8, HBM-slab up to 4); 0 = default           */
     uint32_t refill_min; /* persistent kernels: idle lanes that trigger a
-                            refill; 0 = default                               */
+                            refill (SMEM-staged), or stopped lanes that end
+                            an epoch early (HBM-slab); 0 = default            */
     uint32_t ctas_per_sm;/* persistent kernels: resident CTAs per SM (fewer
                             resident VMs keep their memory in L1/L2);
                             0 = as many as fit                                */

@@ -205,6 +205,7 @@ StepVariant variant_of(const rasp_batch* b) {
   v.hist = (b->cfg.flags & RASP_COLLECT_STATS) != 0;
   v.vote = (b->cfg.flags & RASP_DISPATCH_VOTE) != 0;
   v.classic = (b->cfg.flags & RASP_ISA_CLASSIC) != 0;
+  v.block = (b->cfg.flags & RASP_STEP_BLOCK) != 0;
   return v;
 }
 
@@ -244,6 +245,7 @@ void plan_buckets(rasp_batch* b) {
       sh.warps = 4;
       sh.refill_min = 1;
       sh.epoch = b->cfg.epoch ? b->cfg.epoch : 128u;
+      sh.idle_exit = std::min<uint32_t>(b->cfg.refill_min, 32u);   // epoch loop: end an epoch after this many stops
     }
     if (b->cfg.warps_per_cta) sh.warps = std::min<uint32_t>(b->cfg.warps_per_cta, 8u);
     if (!sh.staged) sh.warps = std::min<uint32_t>(sh.warps, 4u);   // k_persist_gl: at most 128 threads

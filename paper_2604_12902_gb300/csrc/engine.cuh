@@ -468,6 +468,146 @@ __device__ __forceinline__ uint32_t fast_step_ptx(uint64_t* M, const uint64_t* T
   return rare;
 }
 
+// A whole epoch of fast steps as one PTX loop, run together by the lanes of
+// `mask` (every lane of the mask executes it; the exits are warp-uniform).
+// Each iteration is the guarded-sum step of fast_step_ptx, reorganised so
+// that a step costs as few instructions as the case equation allows:
+//  - the guards of every case that needs the general path (no loaded pair,
+//    invalid opcode, countdown at its stop, an address or jump target outside
+//    [0, n), RD at the end of the tape, BNZ to itself, i (+) 2 reaching
+//    ilim) are evaluated first, from registers only, and one warp vote leaves
+//    the loop, before anything is applied, if any lane has such a step;
+//  - otherwise every lane applies its step: the next instruction pair (at
+//    the jump target or at i + 2) is loaded straight into <co, cj>, the
+//    operand M[j] of ADD/MUL/PRI and the tape word of RD are loaded beside
+//    it, and the opcode guards select a, the store, the output and u_0/y_0;
+//  - the countdown toward the step stop is not kept per step: the lane is
+//    stopped when the loop counter reaches `stopk` (= k - left, 0: never).
+// In: kk = steps to run (the same in every lane of mask). Out: kk = steps
+// not run; rare = 1 in the lanes whose current step needs the general path
+// (nothing of it applied); have = 0 when the pair in <co, cj> is not the next
+// instruction (odd or out-of-range target, or overwritten by the step's own
+// store). Precondition for every lane: have != 0 or the lane is rare at the
+// first step; i = ip < n.
+#define RASP_LOOP_A \
+      "{\n\t" \
+      ".reg .pred px, pq, pv, pj, pjl, pz, pt, pe, pop, p6, pad, p1, p2, p3, pw, p7, pp, pst, pany, pc;\n\t" \
+      ".reg .b32 ol, oh, jl, jh, m, t0, t1, nip, tip;\n\t" \
+      ".reg .b64 v, tv, sm, pd, wv, jj, ado, adn, adt, ady, am;\n\t" \
+      "RASP_LOOP:\n\t" \
+      "mov.b64 {ol, oh}, %1;\n\t" \
+      "mov.b64 {jl, jh}, %2;\n\t" \
+      "add.u32 t0, ol, -1;\n\t" \
+      "setp.lt.u32 pv, t0, 7;\n\t" \
+      "setp.eq.and.u32 pv, oh, 0, pv;\n\t" \
+      "setp.lt.u32 pjl, jl, %12;\n\t" \
+      "setp.eq.and.u32 pj, jh, 0, pjl;\n\t" \
+      "shl.b32 m, 1, ol;\n\t"
+// opcode 5's condition pz: BNZ a != 0 (word machine); BPA 1 <= a <= 2^(w-1) - 1 (classic, %20 = 2^(w-1) - 1)
+#define RASP_LOOP_PZ_WORD "setp.ne.u64 pz, %0, 0;\n\t"
+#define RASP_LOOP_PZ_CLASSIC "add.u64 am, %0, -1;\n\tsetp.lt.u64 pz, am, %20;\n\t"
+#define RASP_LOOP_B \
+      "and.b32 t0, m, 0x20;\n\t" \
+      "setp.ne.and.u32 pt, t0, 0, pz;\n\t" \
+      "add.u32 nip, %3, 2;\n\t" \
+      "selp.b32 tip, jl, nip, pt;\n\t" \
+      "setp.eq.u32 px, %6, 0;\n\t" \
+      "setp.eq.or.u32 px, %7, %17, px;\n\t" \
+      "not.pred pq, pv;\n\t" \
+      "or.pred px, px, pq;\n\t" \
+      "and.b32 t0, m, 0xDC;\n\t" \
+      "setp.ne.or.u32 pad, t0, 0, pt;\n\t" \
+      "not.pred pq, pj;\n\t" \
+      "and.pred pq, pq, pad;\n\t" \
+      "or.pred px, px, pq;\n\t" \
+      "and.b32 t0, m, 0x40;\n\t" \
+      "setp.ne.u32 p6, t0, 0;\n\t" \
+      "setp.ge.and.u32 pq, %4, %14, p6;\n\t" \
+      "or.pred px, px, pq;\n\t" \
+      "setp.eq.and.u32 pq, jl, %3, pt;\n\t" \
+      "or.pred px, px, pq;\n\t" \
+      "setp.ge.and.u32 pq, nip, %16, !pt;\n\t" \
+      "or.pred px, px, pq;\n\t" \
+      "vote.sync.any.pred pany, px, %18;\n\t" \
+      "@pany bra.uni RASP_DONE;\n\t" \
+      "and.b32 t0, tip, 1;\n\t" \
+      "setp.eq.u32 pe, t0, 0;\n\t" \
+      "setp.lt.and.u32 pe, tip, %13, pe;\n\t" \
+      "mad.wide.u32 adn, tip, 8, %9;\n\t" \
+      "mov.b64 jj, {jl, jh};\n\t" \
+      "@pe ld.global.v2.u64 {%1, %2}, [adn];\n\t" \
+      "and.b32 t0, m, 0x8C;\n\t" \
+      "setp.ne.u32 pop, t0, 0;\n\t" \
+      "mad.wide.u32 ado, jl, 8, %9;\n\t" \
+      "@pop ld.global.u64 v, [ado];\n\t" \
+      "mad.wide.u32 adt, %4, 8, %10;\n\t" \
+      "@p6 ld.global.u64 tv, [adt];\n\t" \
+      "add.u64 sm, %0, v;\n\t"
+// opcode 3's result pd: MUL a * v (word machine); SUB a - v (classic)
+#define RASP_LOOP_PD_WORD "mul.lo.u64 pd, %0, v;\n\t"
+#define RASP_LOOP_PD_CLASSIC "sub.u64 pd, %0, v;\n\t"
+#define RASP_LOOP_C \
+      "and.b32 t0, m, 0x50;\n\t" \
+      "setp.ne.u32 pw, t0, 0;\n\t" \
+      "selp.b64 wv, tv, %0, p6;\n\t" \
+      "@pw st.global.u64 [ado], wv;\n\t" \
+      "setp.eq.u32 p1, ol, 1;\n\t" \
+      "setp.eq.u32 p2, ol, 2;\n\t" \
+      "setp.eq.u32 p3, ol, 3;\n\t" \
+      "@p1 mov.b64 %0, jj;\n\t" \
+      "@p2 mov.b64 %0, sm;\n\t" \
+      "@p3 mov.b64 %0, pd;\n\t"
+#define RASP_LOOP_D \
+      "and.b32 t0, m, 0x80;\n\t" \
+      "setp.ne.u32 p7, t0, 0;\n\t" \
+      "setp.lt.and.u32 pp, %5, %15, p7;\n\t" \
+      "mad.wide.u32 ady, %5, 8, %11;\n\t" \
+      "@pp st.global.u64 [ady], v;\n\t" \
+      "@pp add.u32 %5, %5, 1;\n\t" \
+      "@p6 add.u32 %4, %4, 1;\n\t" \
+      "mov.b32 %3, tip;\n\t" \
+      "or.b32 t0, jl, 1;\n\t" \
+      "or.b32 t1, tip, 1;\n\t" \
+      "setp.eq.and.u32 pst, t0, t1, pw;\n\t" \
+      "not.pred pq, pst;\n\t" \
+      "and.pred pe, pe, pq;\n\t" \
+      "selp.u32 %6, 1, 0, pe;\n\t" \
+      "add.u32 %7, %7, -1;\n\t" \
+      "setp.ne.u32 pc, %7, 0;\n\t" \
+      "@pc bra.uni RASP_LOOP;\n\t" \
+      "RASP_DONE:\n\t" \
+      "selp.u32 %8, 1, 0, px;\n\t" \
+      "}"
+#define RASP_LOOP_OPERANDS                                                                                 \
+  : "+l"(a), "+l"(co), "+l"(cj), "+r"(ip), "+r"(u0), "+r"(y0), "+r"(have), "+r"(kk), "=r"(rare)             \
+  : "l"(M), "l"(T), "l"(Y), "r"(n), "r"(n - 1u), "r"(ell), "r"(s), "r"(ilim), "r"(stopk), "r"(mask),         \
+    "l"(wmask), "l"(wmask >> 1)                                                                              \
+  : "memory"
+
+template <bool MASKED, bool CLASSIC>
+__device__ __forceinline__ uint32_t fast_loop_ptx(uint64_t* M, const uint64_t* T, uint64_t* Y, uint32_t n,
+                                                  uint32_t ell, uint32_t s, uint32_t ilim, uint64_t wmask,
+                                                  uint32_t stopk, uint32_t mask, uint64_t& a, uint64_t& co,
+                                                  uint64_t& cj, uint32_t& ip, uint32_t& u0, uint32_t& y0,
+                                                  uint32_t& have, uint32_t& kk) {
+  uint32_t rare;
+  // w < 64: the new accumulator is reduced to w bits (%19 = 2^w - 1)
+  if constexpr (MASKED && CLASSIC) {
+    asm volatile(RASP_LOOP_A RASP_LOOP_PZ_CLASSIC RASP_LOOP_B RASP_LOOP_PD_CLASSIC RASP_LOOP_C
+                 "and.b64 %0, %0, %19;\n\t" RASP_LOOP_D RASP_LOOP_OPERANDS);
+  } else if constexpr (MASKED) {
+    asm volatile(RASP_LOOP_A RASP_LOOP_PZ_WORD RASP_LOOP_B RASP_LOOP_PD_WORD RASP_LOOP_C
+                 "and.b64 %0, %0, %19;\n\t" RASP_LOOP_D RASP_LOOP_OPERANDS);
+  } else if constexpr (CLASSIC) {
+    asm volatile(RASP_LOOP_A RASP_LOOP_PZ_CLASSIC RASP_LOOP_B RASP_LOOP_PD_CLASSIC RASP_LOOP_C RASP_LOOP_D
+                 RASP_LOOP_OPERANDS);
+  } else {
+    asm volatile(RASP_LOOP_A RASP_LOOP_PZ_WORD RASP_LOOP_B RASP_LOOP_PD_WORD RASP_LOOP_C RASP_LOOP_D
+                 RASP_LOOP_OPERANDS);
+  }
+  return rare;
+}
+
 template <bool MASKED, bool CHECKED, bool HIST, bool PIPE, bool SHARED = false, bool CLASSIC = false>
 __device__ __forceinline__ uint32_t one_step(uint64_t* __restrict__ M, const uint64_t* __restrict__ T,
                                              uint64_t* __restrict__ Y, const Params& P, Regs& r, Hist& h,

@@ -15,6 +15,7 @@ struct StepVariant {
   bool hist;     // collect per-opcode counters
   bool vote;     // warp opcode voting instead of guarded selects
   bool classic;  // classic opcode set (Sec. 1.1: SUB, BPA); plain and HBM-slab persistent, select only
+  bool block;    // HBM-slab persistent: one predicated block per step instead of the epoch loop
 };
 
 // Persistent-kernel launch shape for one bucket of VMs.
@@ -24,7 +25,8 @@ struct PersistShape {
   uint32_t slot_words;  // words per lane slot (M + tape + y, padded)
   uint32_t warps;       // warps per CTA
   uint32_t epoch;       // steps between warp scheduling points
-  uint32_t refill_min;  // idle lanes that trigger a refill
+  uint32_t refill_min;  // idle lanes that trigger a refill (staged schedule)
+  uint32_t idle_exit;   // HBM-slab epoch loop: stopped lanes that end an epoch early (0: never)
   uint32_t grid;        // CTAs
   uint32_t ctas_per_sm; // resident CTAs per SM (occupancy)
   size_t smem;          // dynamic shared memory per CTA

@@ -211,6 +211,51 @@ __device__ __forceinline__ void run_epoch(uint64_t* M, const uint64_t* T, uint64
   }
 }
 
+// Run up to `epoch` steps of every active lane with the epoch loop of
+// fast_loop_ptx (WRAP, no counters, select dispatch). The lanes whose step
+// needs the general path (the loop left by a warp vote, nothing applied)
+// take that one step here with step_general, then every active lane
+// re-enters the loop together; a round with general steps counts as one
+// step of the epoch, so the epoch always ends. With idle_exit > 0 the epoch
+// also ends once that many lanes that were running at its start have
+// stopped, so that they are refilled sooner.
+template <bool MASKED, bool CLASSIC>
+__device__ __forceinline__ void run_epoch_loop(uint64_t* M, const uint64_t* T, uint64_t* Y, const Params& P,
+                                               Regs& r, Hist& h, bool& active, uint32_t& final_st, uint32_t epoch,
+                                               uint32_t idle_exit) {
+  const uint32_t mask0 = __ballot_sync(FULL, active);
+  uint32_t mask = mask0;
+  uint32_t k = epoch;
+  while (k && mask) {
+    uint32_t kk = k, rare = 0;
+    if (active) {
+      const uint32_t stopk = r.left < k ? k - r.left : 0u;   // loop counter at which the countdown ends
+      uint32_t hv = r.have ? 1u : 0u;
+      uint64_t co = r.cur.x, cj = r.cur.y;
+      rare = fast_loop_ptx<MASKED, CLASSIC>(M, T, Y, r.n, P.ell, P.s, r.ilim, P.wmask, stopk, mask, r.a, co, cj,
+                                            r.ip, r.u0, r.y0, hv, kk);
+      r.cur.x = co;
+      r.cur.y = cj;
+      r.have = hv != 0u;
+      r.left -= k - kk;
+      if (rare) {
+        r.have = false;
+        const uint32_t st = step_general<MASKED, false, false, false, CLASSIC>(M, T, Y, P, r, h);
+        if (st == CONT) {
+          prime(M, r);
+        } else {
+          active = false;
+          final_st = st;
+        }
+      }
+    }
+    kk = __shfl_sync(FULL, kk, __ffs(mask) - 1);             // the same in every lane of the mask
+    k = __any_sync(FULL, rare != 0u) ? kk - 1u : kk;
+    mask = __ballot_sync(FULL, active);
+    if (idle_exit && (uint32_t)__popc(mask0 & ~mask) >= idle_exit) break;
+  }
+}
+
 // ------------------------------------------------------------------ persistent, staged in SMEM
 template <bool MASKED, bool CHECKED, bool HIST, bool VOTE>
 __global__ void __launch_bounds__(256) k_persist(DevState S, Params P, Queue Q, uint32_t ncap,
@@ -330,8 +375,10 @@ __global__ void __launch_bounds__(256) k_persist(DevState S, Params P, Queue Q, 
 // end no VM waits in a busy lane's prefetch slot while other lanes idle.
 enum : uint32_t { PF_EMPTY = 0, PF_ID = 1, PF_REGS = 2, PF_NONE = 3 };   // PF_REGS: entries warmed in L2
 
-template <bool MASKED, bool CHECKED, bool HIST, bool VOTE, bool CLASSIC = false>
-__global__ void __launch_bounds__(128, 7) k_persist_gl(DevState S, Params P, Queue Q, uint32_t epoch) {
+template <bool MASKED, bool CHECKED, bool HIST, bool VOTE, bool CLASSIC = false, bool LOOP = false>
+__global__ void __launch_bounds__(128, 7) k_persist_gl(DevState S, Params P, Queue Q, uint32_t epoch,
+                                                       uint32_t idle_exit) {
+  static_assert(!LOOP || (!CHECKED && !HIST && !VOTE), "the epoch loop serves WRAP select steps without counters");
   const uint32_t lane = threadIdx.x & 31u;
   const uint32_t lt = (1u << lane) - 1u;
   Hist h;
@@ -474,7 +521,8 @@ __global__ void __launch_bounds__(128, 7) k_persist_gl(DevState S, Params P, Que
     if (__all_sync(FULL, vm < 0 && pf == PF_NONE)) break;
 
     // ---- run
-    run_epoch<MASKED, CHECKED, HIST, VOTE, true, CLASSIC>(M, T, Y, P, r, h, active, final_st, epoch);
+    if constexpr (LOOP) run_epoch_loop<MASKED, CLASSIC>(M, T, Y, P, r, h, active, final_st, epoch, idle_exit);
+    else run_epoch<MASKED, CHECKED, HIST, VOTE, true, CLASSIC>(M, T, Y, P, r, h, active, final_st, epoch);
   }
   flush_hist<HIST>(P, h);
 }
@@ -711,7 +759,7 @@ int num_sms() {
 
 using PlainFn = void (*)(DevState, Params, const uint32_t*, uint32_t);
 using StagedFn = void (*)(DevState, Params, Queue, uint32_t, uint32_t, uint32_t, uint32_t);
-using GlobalFn = void (*)(DevState, Params, Queue, uint32_t);
+using GlobalFn = void (*)(DevState, Params, Queue, uint32_t, uint32_t);
 
 template <bool M_, bool C_, bool H_>
 PlainFn plain_fn(bool vote) {
@@ -731,8 +779,10 @@ GlobalFn global_select(const StepVariant& v) {
   if (v.checked)
     return v.hist ? k_persist_gl<false, true, true, false, CL> : k_persist_gl<false, true, false, false, CL>;
   if (v.masked)
-    return v.hist ? k_persist_gl<true, false, true, false, CL> : k_persist_gl<true, false, false, false, CL>;
-  return v.hist ? k_persist_gl<false, false, true, false, CL> : k_persist_gl<false, false, false, false, CL>;
+    return v.hist ? k_persist_gl<true, false, true, false, CL>
+                  : (v.block ? k_persist_gl<true, false, false, false, CL> : k_persist_gl<true, false, false, false, CL, true>);
+  return v.hist ? k_persist_gl<false, false, true, false, CL>
+                : (v.block ? k_persist_gl<false, false, false, false, CL> : k_persist_gl<false, false, false, false, CL, true>);
 }
 
 PlainFn pick_plain(const StepVariant& v) {
@@ -760,6 +810,7 @@ GlobalFn global_fn(bool vote) {
 
 GlobalFn pick_global(const StepVariant& v) {
   if (v.classic) return global_select<true>(v);
+  if (!v.vote) return global_select<false>(v);
   if (v.checked) return v.hist ? global_fn<false, true, true>(v.vote) : global_fn<false, true, false>(v.vote);
   if (v.masked) return v.hist ? global_fn<true, false, true>(v.vote) : global_fn<true, false, false>(v.vote);
   return v.hist ? global_fn<false, false, true>(v.vote) : global_fn<false, false, false>(v.vote);
@@ -862,7 +913,7 @@ cudaError_t launch_persist(const StepVariant& var, const DevState& S, const Para
     pick_staged(var)<<<grid, 32u * sh.warps, sh.smem, stream>>>(S, P, q, sh.ncap, sh.slot_words, sh.epoch,
                                                                  sh.refill_min);
   else
-    pick_global(var)<<<grid, 32u * sh.warps, 0, stream>>>(S, P, q, sh.epoch);
+    pick_global(var)<<<grid, 32u * sh.warps, 0, stream>>>(S, P, q, sh.epoch, sh.idle_exit);
   return cudaGetLastError();
 }
 

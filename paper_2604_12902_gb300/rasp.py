@@ -25,6 +25,7 @@ DISPATCH_SELECT, DISPATCH_VOTE = 0x000, 0x100
 COLLECT_STATS = 0x1000
 ISA_CLASSIC = 0x8000
 BUDGET_ROUNDS = 0x10000
+STEP_BLOCK = 0x20000
 SHARED_PROGRAM = 0x2000
 CUDA_GRAPH = 0x4000
 U64_MAX = (1 << 64) - 1

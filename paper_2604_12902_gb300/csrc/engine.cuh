@@ -471,48 +471,52 @@ __device__ __forceinline__ uint32_t fast_step_ptx(uint64_t* M, const uint64_t* T
 // A whole epoch of fast steps as one PTX loop, run together by the lanes of
 // `mask` (every lane of the mask executes it; the exits are warp-uniform).
 // Each iteration is the guarded-sum step of fast_step_ptx, reorganised so
-// that a step costs as few instructions as the case equation allows:
-//  - the guards of every case that needs the general path (no loaded pair,
-//    invalid opcode, countdown at its stop, an address or jump target outside
-//    [0, n), RD at the end of the tape, BNZ to itself, i (+) 2 reaching
-//    ilim) are evaluated first, from registers only, and one warp vote leaves
-//    the loop, before anything is applied, if any lane has such a step;
+// that a step costs as few integer instructions as the case equation
+// allows:
+//  - the guards of every case that needs the general path (no loaded
+//    instruction pair, invalid opcode, an address or jump target outside
+//    [0, n), RD at the end of the tape, BNZ to itself) are evaluated first,
+//    from registers only, and one warp vote leaves the loop, before anything
+//    is applied, if any lane has such a step;
 //  - otherwise every lane applies its step: the next instruction pair (at
 //    the jump target or at i + 2) is loaded straight into <co, cj>, the
 //    operand M[j] of ADD/MUL/PRI and the tape word of RD are loaded beside
 //    it, and the opcode guards select a, the store, the output and u_0/y_0;
-//  - the countdown toward the step stop is not kept per step: the lane is
-//    stopped when the loop counter reaches `stopk` (= k - left, 0: never).
-// In: kk = steps to run (the same in every lane of mask). Out: kk = steps
-// not run; rare = 1 in the lanes whose current step needs the general path
-// (nothing of it applied); have = 0 when the pair in <co, cj> is not the next
-// instruction (odd or out-of-range target, or overwritten by the step's own
-// store). Precondition for every lane: have != 0 or the lane is rare at the
-// first step; i = ip < n.
+//  - the step countdown is not kept per step: the caller runs at most as
+//    many steps as the smallest countdown of the warp;
+//  - i (+) 2 is taken as ip + 2 without reduction; when that reaches ilim
+//    (n, or 2^w when smaller) the next pair is not loaded, so the lane leaves
+//    at its next step and the caller reduces ip.
+// In: kk = steps to run (>= 1, the same in every lane of mask). Out: kk =
+// steps not run; rare = 1 in the lanes whose current step needs the general
+// path (nothing of it applied); have = 0 when <co, cj> is not the next
+// instruction (odd or out-of-range target, i (+) 2 at ilim, or overwritten by
+// the step's own store). Precondition: ibase = 0, i = ip < ilim, and have = 1
+// only with ip even, ip + 1 < ilim and <co, cj> = <M[ip], M[ip+1]>.
 #define RASP_LOOP_A \
       "{\n\t" \
-      ".reg .pred px, pq, pv, pj, pjl, pz, pt, pe, pop, p6, pad, p1, p2, p3, pw, p7, pp, pst, pany, pc;\n\t" \
-      ".reg .b32 ol, oh, jl, jh, m, t0, t1, nip, tip;\n\t" \
+      ".reg .pred px, pq, pv, pj, pz, pt, pe, ph, pop, p6, pad, p1, p2, p3, pw, p7, pp, pst, pany, pc;\n\t" \
+      ".reg .b32 ol, oh, jl, jh, m, t0, nip, tip;\n\t" \
       ".reg .b64 v, tv, sm, pd, wv, jj, ado, adn, adt, ady, am;\n\t" \
+      "setp.ne.u32 ph, %6, 0;\n\t" \
       "RASP_LOOP:\n\t" \
       "mov.b64 {ol, oh}, %1;\n\t" \
       "mov.b64 {jl, jh}, %2;\n\t" \
       "add.u32 t0, ol, -1;\n\t" \
       "setp.lt.u32 pv, t0, 7;\n\t" \
       "setp.eq.and.u32 pv, oh, 0, pv;\n\t" \
-      "setp.lt.u32 pjl, jl, %12;\n\t" \
-      "setp.eq.and.u32 pj, jh, 0, pjl;\n\t" \
+      "setp.lt.u32 pj, jl, %12;\n\t" \
+      "setp.eq.and.u32 pj, jh, 0, pj;\n\t" \
       "shl.b32 m, 1, ol;\n\t"
-// opcode 5's condition pz: BNZ a != 0 (word machine); BPA 1 <= a <= 2^(w-1) - 1 (classic, %20 = 2^(w-1) - 1)
+// opcode 5's condition pz: BNZ a != 0 (word machine); BPA 1 <= a <= 2^(w-1) - 1 (classic, %17 = 2^(w-1) - 1)
 #define RASP_LOOP_PZ_WORD "setp.ne.u64 pz, %0, 0;\n\t"
-#define RASP_LOOP_PZ_CLASSIC "add.u64 am, %0, -1;\n\tsetp.lt.u64 pz, am, %20;\n\t"
+#define RASP_LOOP_PZ_CLASSIC "add.u64 am, %0, -1;\n\tsetp.lt.u64 pz, am, %17;\n\t"
 #define RASP_LOOP_B \
       "and.b32 t0, m, 0x20;\n\t" \
       "setp.ne.and.u32 pt, t0, 0, pz;\n\t" \
       "add.u32 nip, %3, 2;\n\t" \
       "selp.b32 tip, jl, nip, pt;\n\t" \
-      "setp.eq.u32 px, %6, 0;\n\t" \
-      "setp.eq.or.u32 px, %7, %17, px;\n\t" \
+      "not.pred px, ph;\n\t" \
       "not.pred pq, pv;\n\t" \
       "or.pred px, px, pq;\n\t" \
       "and.b32 t0, m, 0xDC;\n\t" \
@@ -526,9 +530,7 @@ __device__ __forceinline__ uint32_t fast_step_ptx(uint64_t* M, const uint64_t* T
       "or.pred px, px, pq;\n\t" \
       "setp.eq.and.u32 pq, jl, %3, pt;\n\t" \
       "or.pred px, px, pq;\n\t" \
-      "setp.ge.and.u32 pq, nip, %16, !pt;\n\t" \
-      "or.pred px, px, pq;\n\t" \
-      "vote.sync.any.pred pany, px, %18;\n\t" \
+      "vote.sync.any.pred pany, px, %16;\n\t" \
       "@pany bra.uni RASP_DONE;\n\t" \
       "and.b32 t0, tip, 1;\n\t" \
       "setp.eq.u32 pe, t0, 0;\n\t" \
@@ -566,38 +568,37 @@ __device__ __forceinline__ uint32_t fast_step_ptx(uint64_t* M, const uint64_t* T
       "@pp add.u32 %5, %5, 1;\n\t" \
       "@p6 add.u32 %4, %4, 1;\n\t" \
       "mov.b32 %3, tip;\n\t" \
-      "or.b32 t0, jl, 1;\n\t" \
-      "or.b32 t1, tip, 1;\n\t" \
-      "setp.eq.and.u32 pst, t0, t1, pw;\n\t" \
+      "xor.b32 t0, jl, tip;\n\t" \
+      "setp.lt.and.u32 pst, t0, 2, pw;\n\t" \
       "not.pred pq, pst;\n\t" \
-      "and.pred pe, pe, pq;\n\t" \
-      "selp.u32 %6, 1, 0, pe;\n\t" \
+      "and.pred ph, pe, pq;\n\t" \
       "add.u32 %7, %7, -1;\n\t" \
       "setp.ne.u32 pc, %7, 0;\n\t" \
       "@pc bra.uni RASP_LOOP;\n\t" \
       "RASP_DONE:\n\t" \
       "selp.u32 %8, 1, 0, px;\n\t" \
+      "selp.u32 %6, 1, 0, ph;\n\t" \
       "}"
 #define RASP_LOOP_OPERANDS                                                                                 \
   : "+l"(a), "+l"(co), "+l"(cj), "+r"(ip), "+r"(u0), "+r"(y0), "+r"(have), "+r"(kk), "=r"(rare)             \
-  : "l"(M), "l"(T), "l"(Y), "r"(n), "r"(n - 1u), "r"(ell), "r"(s), "r"(ilim), "r"(stopk), "r"(mask),         \
-    "l"(wmask), "l"(wmask >> 1)                                                                              \
+  : "l"(M), "l"(T), "l"(Y), "r"(n), "r"(ilim - 1u), "r"(ell), "r"(s), "r"(mask), "l"(wmask >> 1),           \
+    "l"(wmask)                                                                                               \
   : "memory"
 
 template <bool MASKED, bool CLASSIC>
 __device__ __forceinline__ uint32_t fast_loop_ptx(uint64_t* M, const uint64_t* T, uint64_t* Y, uint32_t n,
                                                   uint32_t ell, uint32_t s, uint32_t ilim, uint64_t wmask,
-                                                  uint32_t stopk, uint32_t mask, uint64_t& a, uint64_t& co,
-                                                  uint64_t& cj, uint32_t& ip, uint32_t& u0, uint32_t& y0,
-                                                  uint32_t& have, uint32_t& kk) {
+                                                  uint32_t mask, uint64_t& a, uint64_t& co, uint64_t& cj,
+                                                  uint32_t& ip, uint32_t& u0, uint32_t& y0, uint32_t& have,
+                                                  uint32_t& kk) {
   uint32_t rare;
-  // w < 64: the new accumulator is reduced to w bits (%19 = 2^w - 1)
+  // w < 64: the new accumulator is reduced to w bits (%18 = 2^w - 1)
   if constexpr (MASKED && CLASSIC) {
     asm volatile(RASP_LOOP_A RASP_LOOP_PZ_CLASSIC RASP_LOOP_B RASP_LOOP_PD_CLASSIC RASP_LOOP_C
-                 "and.b64 %0, %0, %19;\n\t" RASP_LOOP_D RASP_LOOP_OPERANDS);
+                 "and.b64 %0, %0, %18;\n\t" RASP_LOOP_D RASP_LOOP_OPERANDS);
   } else if constexpr (MASKED) {
     asm volatile(RASP_LOOP_A RASP_LOOP_PZ_WORD RASP_LOOP_B RASP_LOOP_PD_WORD RASP_LOOP_C
-                 "and.b64 %0, %0, %19;\n\t" RASP_LOOP_D RASP_LOOP_OPERANDS);
+                 "and.b64 %0, %0, %18;\n\t" RASP_LOOP_D RASP_LOOP_OPERANDS);
   } else if constexpr (CLASSIC) {
     asm volatile(RASP_LOOP_A RASP_LOOP_PZ_CLASSIC RASP_LOOP_B RASP_LOOP_PD_CLASSIC RASP_LOOP_C RASP_LOOP_D
                  RASP_LOOP_OPERANDS);

@@ -212,13 +212,14 @@ __device__ __forceinline__ void run_epoch(uint64_t* M, const uint64_t* T, uint64
 }
 
 // Run up to `epoch` steps of every active lane with the epoch loop of
-// fast_loop_ptx (WRAP, no counters, select dispatch). The lanes whose step
-// needs the general path (the loop left by a warp vote, nothing applied)
-// take that one step here with step_general, then every active lane
-// re-enters the loop together; a round with general steps counts as one
-// step of the epoch, so the epoch always ends. With idle_exit > 0 the epoch
-// also ends once that many lanes that were running at its start have
-// stopped, so that they are refilled sooner.
+// fast_loop_ptx (WRAP, no counters, select dispatch). Each round runs the
+// loop for at most the smallest step countdown of the warp; then the lanes
+// whose step needs the general path (the loop left by a warp vote, nothing
+// of that step applied) or whose countdown ended take one step with
+// step_general, and every active lane re-enters the loop together. A round
+// with general steps counts one more step of the epoch, so the epoch always
+// ends. With idle_exit > 0 the epoch also ends once that many lanes that were
+// running at its start have stopped, so that they are refilled sooner.
 template <bool MASKED, bool CLASSIC>
 __device__ __forceinline__ void run_epoch_loop(uint64_t* M, const uint64_t* T, uint64_t* Y, const Params& P,
                                                Regs& r, Hist& h, bool& active, uint32_t& final_st, uint32_t epoch,
@@ -227,18 +228,31 @@ __device__ __forceinline__ void run_epoch_loop(uint64_t* M, const uint64_t* T, u
   uint32_t mask = mask0;
   uint32_t k = epoch;
   while (k && mask) {
-    uint32_t kk = k, rare = 0;
+    uint32_t done = 0;
+    bool general = false;
     if (active) {
-      const uint32_t stopk = r.left < k ? k - r.left : 0u;   // loop counter at which the countdown ends
-      uint32_t hv = r.have ? 1u : 0u;
-      uint64_t co = r.cur.x, cj = r.cur.y;
-      rare = fast_loop_ptx<MASKED, CLASSIC>(M, T, Y, r.n, P.ell, P.s, r.ilim, P.wmask, stopk, mask, r.a, co, cj,
-                                            r.ip, r.u0, r.y0, hv, kk);
-      r.cur.x = co;
-      r.cur.y = cj;
-      r.have = hv != 0u;
-      r.left -= k - kk;
-      if (rare) {
+      uint32_t kk = min(k, __reduce_min_sync(mask, r.left));
+      uint32_t rare = 0;
+      if (kk) {
+        const uint32_t k0 = kk;
+        uint32_t hv = r.have ? 1u : 0u;
+        uint64_t co = r.cur.x, cj = r.cur.y;
+        rare = fast_loop_ptx<MASKED, CLASSIC>(M, T, Y, r.n, P.ell, P.s, r.ilim, P.wmask, mask, r.a, co, cj, r.ip,
+                                              r.u0, r.y0, hv, kk);
+        r.cur.x = co;
+        r.cur.y = cj;
+        r.have = hv != 0u;
+        done = k0 - kk;
+        r.left -= done;
+      }
+      general = rare || r.left == 0u;
+      if (general) {
+        if (r.ip >= r.ilim) {
+          // the loop took i (+) 2 = ip + 2 unreduced (ibase = 0): reduce it
+          const uint64_t i = (uint64_t)r.ip & P.wmask;
+          r.ip = mod_n(i, r.n);
+          r.ibase = i - r.ip;
+        }
         r.have = false;
         const uint32_t st = step_general<MASKED, false, false, false, CLASSIC>(M, T, Y, P, r, h);
         if (st == CONT) {
@@ -249,8 +263,9 @@ __device__ __forceinline__ void run_epoch_loop(uint64_t* M, const uint64_t* T, u
         }
       }
     }
-    kk = __shfl_sync(FULL, kk, __ffs(mask) - 1);             // the same in every lane of the mask
-    k = __any_sync(FULL, rare != 0u) ? kk - 1u : kk;
+    done = __shfl_sync(FULL, done, __ffs(mask) - 1);        // the same in every lane of the mask
+    k -= done;
+    if (__any_sync(FULL, general) && k) k -= 1u;
     mask = __ballot_sync(FULL, active);
     if (idle_exit && (uint32_t)__popc(mask0 & ~mask) >= idle_exit) break;
   }

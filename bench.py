@@ -178,11 +178,97 @@ def outcomes(stats) -> dict:
     return out
 
 
-def algorithmic_bytes(stats) -> float:
+def algorithmic_bytes(stats, fetch_from_smem: bool = False) -> float:
+    """Opcode-weighted bytes of VM state touched by the executed steps; with
+    fetch_from_smem the 16-byte instruction fetch is left out (the
+    shared-program kernel reads the program words from shared memory)."""
     ops = stats["op_steps"]
     b = sum(BYTES_PER_OP[k] * ops[k] for k in range(1, 8))
     b -= (BYTES_PER_OP[7] - PRI_FULL_BYTES) * stats["pri_full"]
+    if fetch_from_smem:
+        b -= 16 * sum(ops[k] for k in range(1, 8))
     return float(b)
+
+
+KERNEL_OF = {"persist_gl": "k_persist_gl", "plain": "k_plain", "persist_smem": "k_persist", "shared": "k_shared"}
+
+
+def time_config(R, torch, wl, desc, flags, steps, warmup, flush_l2=False):
+    """Times one workload the way the headline is timed (re-pack c_0 + run to
+    completion per step, CUDA events on the batch stream, generation and
+    tuning untimed): run-kernel ms, whole-step VM-steps/s, roofline of the
+    run kernel against the measured HBM bandwidth, and the final statuses."""
+    stream = torch.cuda.current_stream()
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda") if flush_l2 else None
+    with R.Batch(wl.mem_words, wl.ell, wl.s, word_bits=wl.w, flags=flags) as b:
+        b.load_workload(wl)
+        tuned = b.autotune(reps=2) if (flags & 0xF0) == 0 else None
+        with R.Batch(wl.mem_words, wl.ell, wl.s, word_bits=wl.w, flags=flags | R.COLLECT_STATS) as bs:
+            bs.load_workload(wl)
+            bs.run()
+            stats = bs.stats()
+        chosen = tuned["chosen"] if tuned else "flags %#x" % flags
+        kernel = KERNEL_OF.get(chosen.split()[0], chosen)
+        alg = algorithmic_bytes(stats, fetch_from_smem=kernel == "k_shared")
+        for _ in range(warmup):
+            b.reset()
+            b.run()
+        torch.cuda.synchronize()
+        run_ms, pack_ms, step_ms = [], [], []
+        for _ in range(steps):
+            if flush is not None:
+                flush.zero_()
+            ev = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+            ev[0].record(stream)
+            b.reset()
+            ev[1].record(stream)
+            b.run()
+            ev[2].record(stream)
+            torch.cuda.synchronize()
+            pack_ms.append(ev[0].elapsed_time(ev[1]))
+            run_ms.append(ev[1].elapsed_time(ev[2]))
+            step_ms.append(ev[0].elapsed_time(ev[2]))
+        b.sync()
+        st = b.stats()
+    assert st["vm_steps"] == stats["vm_steps"], "timed runs disagree with the counting run"
+    hbm, peak_kind = peaks()
+    run_avg = float(np.mean(run_ms))
+    achieved = alg / (run_avg * 1e-3) / 1e9
+    m_bytes = float(wl.mem_words.astype(np.uint64).sum()) * 8.0
+    return {"workload": desc, "vms": wl.num_vms, "vm_steps": int(stats["vm_steps"]), "steps": steps,
+            "warmup": warmup, "ms_per_step": float(np.mean(step_ms)),
+            "value": stats["vm_steps"] / (float(np.mean(step_ms)) * 1e-3), "unit": UNIT,
+            "schedule": chosen, "cuda_graph": bool(flags & R.CUDA_GRAPH),
+            "l2": ("inputs larger than L2 (M = %.2f GiB)" % (m_bytes / 2 ** 30)) if m_bytes > 129e6
+            else ("M = %.2f MB fits in L2: 256 MB written between timed steps" % (m_bytes / 1e6)),
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
+                         "traffic": None, "kernel": kernel, "peak_kind": peak_kind,
+                         "bytes_per_step": alg / max(stats["vm_steps"], 1),
+                         "fetch_from_smem_excluded": kernel == "k_shared",
+                         "kernel_ms": run_avg, "pack_ms": float(np.mean(pack_ms))},
+            "outcomes": outcomes(st)}
+
+
+def other_configs(R, torch, steps, warmup):
+    """The benchmark's other single-GPU configurations, each timed like the
+    headline after it: 1,024 random programs (config 1), the uneven batch of
+    4,194,304 programs in its CUDA-graph form (config 3) and the
+    shared-program rollout of 16,384 programs x 256 tapes (config 4)."""
+    out = {}
+    for name in ("random", "shared", "uneven"):
+        t0 = time.perf_counter()
+        wl, desc = make_workload(name, 0)
+        gen_s = time.perf_counter() - t0
+        flags = R.CUDA_GRAPH if name == "uneven" else 0
+        clk = ClockSampler(torch.cuda.current_device())
+        clk.start()
+        rec = time_config(R, torch, wl, desc, flags, steps, warmup, flush_l2=name == "random")
+        rec["clocks"] = clk.stop()
+        rec["generation_s"] = gen_s
+        out[{"random": "config1_random", "uneven": "config3_uneven", "shared": "config4_shared"}[name]] = rec
+        del wl
+        torch.cuda.empty_cache()
+    return out
 
 
 def cpu_baseline(wl, budget_s: float = 15.0, threads: int = 1, classic: bool = False):
@@ -331,6 +417,8 @@ def main():
     ap.add_argument("--lam-sweep", default="", help="serving: further arrival rates to run, comma separated")
     ap.add_argument("--rounds", type=int, default=4, help="search: rounds")
     ap.add_argument("--tau-max", type=int, default=10 ** 5, help="search: step cap")
+    ap.add_argument("--no-other", action="store_true",
+                    help="skip the other configurations (random, uneven, shared) after the headline")
     ap.add_argument("--out-arity", type=int, default=0,
                     help="halting: output arity of the sampled programs (0 = drawn from 1..s, as the grammar allows)")
     args = ap.parse_args()
@@ -499,12 +587,21 @@ def main():
     if rank == 0 and ws == 1 and not args.no_cpu:
         cpu = cpu_baseline(wl, args.cpu_seconds, classic=args.isa == "classic")
     b.close()
+    num_vms = wl.num_vms
+    del wl
+    torch.cuda.empty_cache()
+
+    # the other configurations, after the headline has been timed
+    others = None
+    if rank == 0 and ws == 1 and args.workload == "templates" and args.vms == 1 << 20 and args.flags == 0 \
+            and not args.no_other:
+        others = other_configs(R, torch, args.steps, args.warmup)
 
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True,
                 "scaling": "weak", "vs_baseline": None, "dtype": "int64", "data": "synthetic",
-                "config": {"workload": desc, "vms_per_gpu": wl.num_vms, "vm_steps_per_gpu": total_steps,
+                "config": {"workload": desc, "vms_per_gpu": num_vms, "vm_steps_per_gpu": total_steps,
                            "l2": "inputs larger than L2 (M = %.2f GiB)" % (m_bytes / 2 ** 30)
                                  if m_bytes > 129e6 else "M below L2 size (%.1f MB); no flush" % (m_bytes / 1e6),
                            "schedule_flags": args.flags, "isa": args.isa, "parallelism": "vm shards x%d" % ws,
@@ -512,11 +609,13 @@ def main():
                 "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "plain": plain,
                 "gpu_launches": (1 + run_launches + (1 if hist else 0)) * args.steps, "clocks": clocks,
                 "outcomes": outcomes(st)}
+        if others:
+            line["other_configs"] = others
         if hist:
             c, o = hist["counts"], hist["other"]
             halted = int(c.sum() + o[3])
             line["halting"] = {
-                "programs": wl.num_vms, "halted": halted, "halted_frac": halted / wl.num_vms,
+                "programs": num_vms, "halted": halted, "halted_frac": halted / num_vms,
                 "tau_h_lt_100": int(c[:100].sum()), "tau_h_100_to_1e6": int(c[100]), "timeout_1e6": int(o[1]),
                 "mean_tau_h_lt_100": float((c[:100] * np.arange(100)).sum() / max(c[:100].sum(), 1)),
                 "min_tau_h": int(np.nonzero(c)[0][0]) if c.any() else None,

@@ -495,9 +495,9 @@ __device__ __forceinline__ uint32_t fast_step_ptx(uint64_t* M, const uint64_t* T
 // only with ip even, ip + 1 < ilim and <co, cj> = <M[ip], M[ip+1]>.
 #define RASP_LOOP_A \
       "{\n\t" \
-      ".reg .pred px, pq, pv, pj, pz, pt, pe, ph, pop, p6, pad, p1, p2, p3, pw, p7, pp, pst, pany, pc;\n\t" \
+      ".reg .pred px, pq, pv, pj, pz, pt, pe, ph, pop, p4, p6, pad, p1, p2, p3, pw, p7, pp, pst, pany, pc;\n\t" \
       ".reg .b32 ol, oh, jl, jh, m, t0, nip, tip;\n\t" \
-      ".reg .b64 v, tv, sm, pd, wv, jj, ado, adn, adt, ady, am;\n\t" \
+      ".reg .b64 v, tv, jj, ado, adn, adt, ady, am;\n\t" \
       "setp.ne.u32 ph, %6, 0;\n\t" \
       "RASP_LOOP:\n\t" \
       "mov.b64 {ol, oh}, %1;\n\t" \
@@ -544,21 +544,20 @@ __device__ __forceinline__ uint32_t fast_step_ptx(uint64_t* M, const uint64_t* T
       "@pop ld.global.u64 v, [ado];\n\t" \
       "mad.wide.u32 adt, %4, 8, %10;\n\t" \
       "@p6 ld.global.u64 tv, [adt];\n\t" \
-      "add.u64 sm, %0, v;\n\t"
-// opcode 3's result pd: MUL a * v (word machine); SUB a - v (classic)
-#define RASP_LOOP_PD_WORD "mul.lo.u64 pd, %0, v;\n\t"
-#define RASP_LOOP_PD_CLASSIC "sub.u64 pd, %0, v;\n\t"
-#define RASP_LOOP_C \
-      "and.b32 t0, m, 0x50;\n\t" \
-      "setp.ne.u32 pw, t0, 0;\n\t" \
-      "selp.b64 wv, tv, %0, p6;\n\t" \
-      "@pw st.global.u64 [ado], wv;\n\t" \
+      "and.b32 t0, m, 0x10;\n\t" \
+      "setp.ne.u32 p4, t0, 0;\n\t" \
+      "@p4 st.global.u64 [ado], %0;\n\t" \
+      "@p6 st.global.u64 [ado], tv;\n\t" \
+      "or.pred pw, p4, p6;\n\t" \
       "setp.eq.u32 p1, ol, 1;\n\t" \
       "setp.eq.u32 p2, ol, 2;\n\t" \
       "setp.eq.u32 p3, ol, 3;\n\t" \
       "@p1 mov.b64 %0, jj;\n\t" \
-      "@p2 mov.b64 %0, sm;\n\t" \
-      "@p3 mov.b64 %0, pd;\n\t"
+      "@p2 add.u64 %0, %0, v;\n\t"
+// opcode 3 (the guards are exclusive, so each lane updates a at most once):
+// MUL a * v (word machine); SUB a - v (classic)
+#define RASP_LOOP_PD_WORD "@p3 mul.lo.u64 %0, %0, v;\n\t"
+#define RASP_LOOP_PD_CLASSIC "@p3 sub.u64 %0, %0, v;\n\t"
 #define RASP_LOOP_D \
       "and.b32 t0, m, 0x80;\n\t" \
       "setp.ne.u32 p7, t0, 0;\n\t" \
@@ -594,16 +593,16 @@ __device__ __forceinline__ uint32_t fast_loop_ptx(uint64_t* M, const uint64_t* T
   uint32_t rare;
   // w < 64: the new accumulator is reduced to w bits (%18 = 2^w - 1)
   if constexpr (MASKED && CLASSIC) {
-    asm volatile(RASP_LOOP_A RASP_LOOP_PZ_CLASSIC RASP_LOOP_B RASP_LOOP_PD_CLASSIC RASP_LOOP_C
+    asm volatile(RASP_LOOP_A RASP_LOOP_PZ_CLASSIC RASP_LOOP_B RASP_LOOP_PD_CLASSIC
                  "and.b64 %0, %0, %18;\n\t" RASP_LOOP_D RASP_LOOP_OPERANDS);
   } else if constexpr (MASKED) {
-    asm volatile(RASP_LOOP_A RASP_LOOP_PZ_WORD RASP_LOOP_B RASP_LOOP_PD_WORD RASP_LOOP_C
+    asm volatile(RASP_LOOP_A RASP_LOOP_PZ_WORD RASP_LOOP_B RASP_LOOP_PD_WORD
                  "and.b64 %0, %0, %18;\n\t" RASP_LOOP_D RASP_LOOP_OPERANDS);
   } else if constexpr (CLASSIC) {
-    asm volatile(RASP_LOOP_A RASP_LOOP_PZ_CLASSIC RASP_LOOP_B RASP_LOOP_PD_CLASSIC RASP_LOOP_C RASP_LOOP_D
+    asm volatile(RASP_LOOP_A RASP_LOOP_PZ_CLASSIC RASP_LOOP_B RASP_LOOP_PD_CLASSIC RASP_LOOP_D
                  RASP_LOOP_OPERANDS);
   } else {
-    asm volatile(RASP_LOOP_A RASP_LOOP_PZ_WORD RASP_LOOP_B RASP_LOOP_PD_WORD RASP_LOOP_C RASP_LOOP_D
+    asm volatile(RASP_LOOP_A RASP_LOOP_PZ_WORD RASP_LOOP_B RASP_LOOP_PD_WORD RASP_LOOP_D
                  RASP_LOOP_OPERANDS);
   }
   return rare;

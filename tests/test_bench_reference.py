@@ -40,3 +40,16 @@ def test_clock_summary_from_nvidia_smi_lines():
     assert bench.summarize_clocks([]) is None
     hot = bench.summarize_clocks(["0, 1500, 2070, 1400, 0x48, Active, Not Active, Active, Not Active"])
     assert hot["reasons"] == ["hw_slowdown", "sw_thermal_slowdown"]
+
+
+def test_algorithmic_bytes_per_opcode():
+    """Bytes of VM state per executed step: 16 for the instruction fetch, 8
+    more for an M operand read or write, 16 more for RD (tape read and M
+    write) and PRI with room in y (M read and y write), 8 for PRI on a full
+    y; the shared-program kernel fetches instructions from shared memory."""
+    import bench
+    ops = [0, 10, 20, 30, 40, 50, 60, 70]                 # LOD ADD MUL STO BNZ RD PRI
+    st = dict(op_steps=ops, pri_full=5)
+    want = 16 * 10 + 24 * 20 + 24 * 30 + 24 * 40 + 16 * 50 + 32 * 60 + 32 * 65 + 24 * 5
+    assert bench.algorithmic_bytes(st) == want
+    assert bench.algorithmic_bytes(st, fetch_from_smem=True) == want - 16 * sum(ops)

@@ -335,14 +335,25 @@ int rasp_run_static(const rasp_static_run* run);
  * (The paper evaluates fixed batches only; this is the request loop around
  * the same machine.) A pool owns one device arena of `arena_bytes`. Each
  * submitted request is a batch of its own (programs, tapes, caps, memory
- * sizes; all VMs of the pool share cfg's w, semantics, l, s and schedule).
+ * sizes; all VMs of the pool share cfg's w, semantics, l, s and opcode set).
  * A request is admitted as soon as a first-fit block of the arena can hold
- * its batch (rasp_batch_bytes), otherwise it waits first-in-first-out.
- * Admitted requests run on their own streams, concurrently with the ones
- * already on the device. rasp_pool_read copies a finished request's state out
- * and frees its block, which admits waiting requests. The pool's calls are
- * serialised by an internal mutex; errors are reported by
- * rasp_pool_last_error (thread-local). */
+ * its batch (rasp_batch_bytes), one of the pool's 1024 request slots is free
+ * and the pool's ring has room for its VMs (2^24 VMs admitted and unread at
+ * most); otherwise it waits first-in-first-out. Admission loads the request
+ * on its own stream and appends its VMs to a ring in device memory that all
+ * admitted requests share; one persistent serving kernel drains that ring,
+ * so the lanes that one request's finished VMs free are taken by the VMs of
+ * whatever request comes next (continuous batching of lanes, not only of
+ * memory). A request is DONE when its last VM has stopped (the kernel writes
+ * a completion word in host-mapped memory; polling reads it without a CUDA
+ * call). rasp_pool_read copies a finished request's state out and frees its
+ * block and slot, which admits waiting requests. The serving kernel returns
+ * by itself once the ring is empty (after a wait of about 3 ms, or at once
+ * when a newer instance is queued); admission launches a new instance, so
+ * nothing on the device waits on the host without a limit. The pool's calls
+ * are serialised by an internal mutex; errors are reported by
+ * rasp_pool_last_error (thread-local). cfg's schedule, dispatch and stats
+ * flags do not apply to pools. */
 typedef struct rasp_pool rasp_pool;
 
 enum rasp_request_state { RASP_REQ_QUEUED = 0, RASP_REQ_RUNNING = 1, RASP_REQ_DONE = 2 };
@@ -379,7 +390,9 @@ int rasp_pool_poll(rasp_pool* p, uint64_t ticket, int* state);
 int rasp_pool_next_done(rasp_pool* p, uint64_t* ticket);
 /* Copy out a RUNNING or DONE request's final state (waits for it; out may be
  * NULL to discard), free its memory and forget the ticket. ESTATE while
- * still QUEUED. */
+ * still QUEUED. EDEVICE if every serving kernel has returned without
+ * finishing the request, or the kernel flagged a ring entry outside the
+ * slot table (the wait is bounded by the kernels, not by a clock). */
 int rasp_pool_read(rasp_pool* p, uint64_t ticket, rasp_state_view* out);
 /* Withdraw a request that is still waiting for admission (QUEUED): it is
  * forgotten and its ticket becomes unknown. ESTATE once it was admitted (read
@@ -387,6 +400,20 @@ int rasp_pool_read(rasp_pool* p, uint64_t ticket, rasp_state_view* out);
 int rasp_pool_cancel(rasp_pool* p, uint64_t ticket);
 /* Bytes of the arena in use, requests waiting, requests running. */
 int rasp_pool_info(rasp_pool* p, uint64_t* in_use, uint64_t* waiting, uint64_t* running);
+
+typedef struct rasp_pool_counters {
+    uint64_t admitted;        /* requests put on the ring                     */
+    uint64_t completed;       /* requests read back (or failed) and freed     */
+    uint64_t kernel_launches; /* serving kernel instances launched            */
+    uint64_t kernel_returns;  /* instances all of whose CTAs have returned    */
+    uint64_t ring_published;  /* VMs ever put on the ring                     */
+    uint64_t vms_in_flight;   /* VMs admitted and not yet read back           */
+    uint64_t kernel_ctas;     /* CTAs per serving kernel instance             */
+} rasp_pool_counters;
+
+/* Counters of the pool (non-blocking). kernel_returns reaching
+ * kernel_launches means no serving kernel is on the device. */
+int rasp_pool_stats(rasp_pool* p, rasp_pool_counters* out);
 /* Wait for the requests still running, discard every request (running,
  * done or waiting; their results are lost), free the arena and the pool.
  * NULL is a no-op. */

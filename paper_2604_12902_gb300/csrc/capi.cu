@@ -22,6 +22,11 @@ bool rasp::inject_alloc_failure() {
   return v && strcmp(v, "alloc") == 0;
 }
 
+bool rasp::inject_wait_expiry() {
+  const char* v = getenv("RASP_FAULT_INJECT");
+  return v && strcmp(v, "wait") == 0;
+}
+
 namespace {
 
 thread_local std::string g_err;
@@ -324,11 +329,29 @@ int check_device_error(rasp_batch* b) {
   CK(cudaMemcpyAsync(&err, b->d_err, sizeof(int), cudaMemcpyDeviceToHost, b->stream));
   CK(cudaStreamSynchronize(b->stream));
   if (err) return fail(RASP_EDEVICE, "a kernel reported internal error %d (%s)", err,
-                       err == ERR_SLOT ? "VM larger than its bucket's slot" : "bounded wait expired");
+                       err == ERR_SLOT ? "VM larger than its bucket's slot"
+                                       : (err == ERR_RING ? "ring entry outside the slot table" : "bounded wait expired"));
   return RASP_OK;
 }
 
 }  // namespace
+
+const DevState& rasp::batch_dev_state(const rasp_batch* b) { return b->S; }
+
+Params rasp::batch_params(const rasp_batch* b) {
+  Params P{};
+  P.wmask = b->wmask;
+  P.budget = ~0ull;
+  P.ell = b->ell;
+  P.s = b->s;
+  P.ellp = b->ellp;
+  P.sp = b->sp;
+  P.err = b->d_err;
+  P.hist = b->d_hist;
+  return P;
+}
+
+const uint32_t* rasp::batch_queue(const rasp_batch* b) { return b->d_ids; }
 
 extern "C" {
 
@@ -476,10 +499,10 @@ int rasp_batch_create(const rasp_config* cfg, uint64_t num_vms, const uint32_t* 
   CKC(cudaMemcpyAsync((void*)S.mem_off, b->h_memoff.data(), 8 * num_vms, cudaMemcpyHostToDevice, st));
   CKC(cudaMemcpyAsync(b->d_ids, b->h_ids.data(), 4 * num_vms, cudaMemcpyHostToDevice, st));
   b->ids_uploaded = true;
-  CKC(cudaMemsetAsync(b->base + L.off_status, RASP_RUNNING, num_vms, st));
-  CKC(cudaMemsetAsync(b->d_err, 0, 16, st));
-  CKC(cudaMemsetAsync(b->d_hist, 0, 8 * 10, st));
-  CKC(cudaMemsetAsync(b->d_cap, 0xff, 8 * num_vms, st));
+  CKC(fill_bytes(b->base + L.off_status, RASP_RUNNING, num_vms, st));
+  CKC(fill_bytes(b->d_err, 0, 16, st));
+  CKC(fill_bytes(b->d_hist, 0, 8 * 10, st));
+  CKC(fill_bytes(b->d_cap, 0xff, 8 * num_vms, st));
   CKC(cudaStreamSynchronize(st));
 #undef CKC
   *out = b;
@@ -536,7 +559,7 @@ int rasp_load_programs(rasp_batch* b, const int64_t* words, const uint64_t* offs
   }
   if (prog_of_vm) CK(cudaMemcpyAsync(b->d_progvm, prog_of_vm, 4ull * b->V, cudaMemcpyHostToDevice, st));
   CK(cudaStreamSynchronize(st));   // the caller's buffers are read before the call returns
-  CK(cudaMemsetAsync(b->d_hist, 0, 8 * 10, st));
+  CK(fill_bytes(b->d_hist, 0, 8 * 10, st));
   CK(launch_pack(b->S, b->d_prog, b->d_progoff, b->shared_programs ? b->d_progvm : nullptr, b->V, b->wmask, b->sp, st));
   b->programs_loaded = true;
   b->dirty_valid = true;
@@ -580,7 +603,7 @@ int rasp_load_inputs(rasp_batch* b, const int64_t* tape, const uint64_t* offsets
     if (uniform) b->h_caps.clear();
     else b->h_caps.assign(caps, caps + b->V);
   } else {
-    CK(cudaMemsetAsync(b->d_cap, 0xff, 8ull * b->V, st));
+    CK(fill_bytes(b->d_cap, 0xff, 8ull * b->V, st));
     b->h_caps.clear();
   }
   CK(cudaStreamSynchronize(st));   // the caller's buffers are read before the call returns
@@ -588,7 +611,7 @@ int rasp_load_inputs(rasp_batch* b, const int64_t* tape, const uint64_t* offsets
     const int rc = order_ids(b);
     if (rc) return rc;
   }
-  CK(cudaMemsetAsync(b->S.uhead, 0, 4ull * b->V, st));
+  CK(fill_bytes(b->S.uhead, 0, 4ull * b->V, st));
   b->inputs_loaded = true;
   g_err.clear();
   return RASP_OK;

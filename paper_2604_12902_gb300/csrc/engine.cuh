@@ -22,7 +22,7 @@ enum : uint32_t {
   CONT = 0xFFu  // step applied, machine continues
 };
 
-enum : int { ERR_NONE = 0, ERR_WAIT_TIMEOUT = 1, ERR_SLOT = 2 };
+enum : int { ERR_NONE = 0, ERR_WAIT_TIMEOUT = 1, ERR_SLOT = 2, ERR_RING = 3 };
 
 // Structure-of-arrays state store in HBM (one entry per VM).
 struct DevState {

@@ -7,6 +7,8 @@
 
 #include "engine.cuh"
 
+struct rasp_batch;
+
 namespace rasp {
 
 struct StepVariant {
@@ -79,11 +81,70 @@ constexpr uint32_t kMaxTopBlocks = 256;
 cudaError_t launch_topk(const DevState& S, uint32_t num_vms, uint32_t k, TopCand* cand, TopCand* best,
                         cudaStream_t stream);
 
+// memset of device memory by a kernel of this library (falls back to
+// cudaMemsetAsync for a pointer that is not 16-byte aligned).
+cudaError_t fill_bytes(void* p, uint8_t value, uint64_t bytes, cudaStream_t stream);
+
 // Host-side fault injection for tests: true when the environment variable
 // RASP_FAULT_INJECT is "alloc", in which case every device allocation the
 // library would make (a batch, the autotuner's snapshot, a pool arena)
 // fails as if cudaMalloc had, with RASP_ENOMEM. Nothing reaches the GPU.
 bool inject_alloc_failure();
+
+// Host-side test hook: with RASP_FAULT_INJECT=wait the SMEM-staged kernel is
+// launched with a bounded-wait limit of 0 polls, so its wait for each bulk
+// copy gives up at once: the kernel flags ERR_WAIT_TIMEOUT (rasp_sync and
+// rasp_read_state return RASP_EDEVICE), lets the copies it issued land
+// (a wait with the default limit) and returns. No fault, no trap, no hang.
+bool inject_wait_expiry();
+
+// ---- serving: one persistent kernel over a ring of VMs shared by requests
+// Device descriptor of one admitted request (a "slot"): its batch's state
+// store, the budget of its run and the word written to its completion flag.
+struct ServeSlot {
+  DevState S;
+  uint64_t budget;       // max_steps of the request's run
+  uint32_t num_vms;      // entries with this slot index name VMs below this
+  uint32_t gen;          // written to done[slot] when its last VM stops (nonzero)
+};
+
+struct ServeArgs {
+  const ServeSlot* slots;
+  uint32_t num_slots;
+  uint32_t* pending;                 // [num_slots] VMs of the request not yet stopped
+  const uint64_t* ring;              // entries (slot << 32 | vm), position p at ring[p & ring_mask]
+  uint64_t ring_mask;
+  unsigned long long* head;          // positions claimed by the kernel
+  unsigned long long* credits;       // published entries not yet claimed (signed; may dip while a shortfall is returned)
+  unsigned long long* state;         // warps holding work, | 1 << 63 once the instance closes (0 at launch)
+  uint32_t* done;                    // host-mapped [num_slots] completion words
+  const volatile uint32_t* launched; // host-mapped: instances the host has launched
+  uint32_t* exited;                  // host-mapped: instances that have returned
+  uint32_t instance;                 // this launch's number (1, 2, ...)
+  uint32_t epoch;
+  uint32_t idle_polls;               // empty-ring polls (1 to 16 us apart) before the newest instance returns
+  int* err;                          // ERR_RING: a ring entry outside the slot table
+};
+
+// Serving kernel shape for the device: grid (leaving one CTA slot per SM
+// free for the requests' pack and ring-fill kernels) and threads per CTA.
+struct ServeShape {
+  uint32_t grid;
+  uint32_t threads;
+};
+int serve_configure(const StepVariant& var, ServeShape& sh);
+cudaError_t launch_serve(const StepVariant& var, const ServeArgs& A, const Params& P, const ServeShape& sh,
+                         cudaStream_t stream);
+// ring[(start + k) & mask] = slot << 32 | ids[k] for k < count, then *credits += count
+// (two launches on `stream`, so every entry is written before it can be claimed).
+cudaError_t launch_ring_append(uint64_t* ring, uint64_t mask, unsigned long long start, uint32_t slot,
+                               const uint32_t* ids, uint32_t count, unsigned long long* credits,
+                               cudaStream_t stream);
+
+// The state store and step parameters of a batch (for the serving pool).
+const DevState& batch_dev_state(const rasp_batch* b);
+Params batch_params(const rasp_batch* b);
+const uint32_t* batch_queue(const rasp_batch* b);   // VM ids in the batch's queue order (device)
 
 // Aggregate: out[0] = sum steps, out[1..5] = count per status.
 cudaError_t launch_stats(const DevState& S, uint32_t num_vms, unsigned long long* out, cudaStream_t stream);

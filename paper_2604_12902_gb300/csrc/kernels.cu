@@ -25,7 +25,8 @@
 namespace rasp {
 
 constexpr uint32_t FULL = 0xffffffffu;
-constexpr uint32_t WAIT_LIMIT = 1u << 22;   // mbarrier polls before giving up
+constexpr uint32_t WAIT_LIMIT = 1u << 22;   // mbarrier polls before giving up (default; the
+                                           // staged kernel takes its limit as an argument)
 
 // ------------------------------------------------------------------ pack
 __global__ void __launch_bounds__(256) k_pack(DevState S, const uint64_t* __restrict__ prog,
@@ -274,7 +275,8 @@ __device__ __forceinline__ void run_epoch_loop(uint64_t* M, const uint64_t* T, u
 // ------------------------------------------------------------------ persistent, staged in SMEM
 template <bool MASKED, bool CHECKED, bool HIST, bool VOTE>
 __global__ void __launch_bounds__(256) k_persist(DevState S, Params P, Queue Q, uint32_t ncap,
-                                                 uint32_t slot_words, uint32_t epoch, uint32_t refill_min) {
+                                                 uint32_t slot_words, uint32_t epoch, uint32_t refill_min,
+                                                 uint32_t wait_limit) {
   extern __shared__ __align__(16) uint64_t smem[];
   const uint32_t lane = threadIdx.x & 31u;
   const uint32_t warp = threadIdx.x >> 5;
@@ -338,7 +340,7 @@ __global__ void __launch_bounds__(256) k_persist(DevState S, Params P, Queue Q, 
         bulk_g2s(slot_s, S.mem + moff, mbytes, bar);
         if (tbytes) bulk_g2s(slot_s + ncap * 8u, S.tape + (uint64_t)vm * P.ellp, tbytes, bar);
         if (ybytes) bulk_g2s(slot_s + (ncap + P.ellp) * 8u, S.y + (uint64_t)vm * P.sp, ybytes, bar);
-        if (!mbar_wait_bounded(bar, phase, WAIT_LIMIT)) {
+        if (!mbar_wait_bounded(bar, phase, wait_limit)) {
           atomicExch(P.err, ERR_WAIT_TIMEOUT);
           dead = true;          // copies may still land: never touch the slot again
           exhausted = true;
@@ -540,6 +542,182 @@ __global__ void __launch_bounds__(128, 7) k_persist_gl(DevState S, Params P, Que
     else run_epoch<MASKED, CHECKED, HIST, VOTE, true, CLASSIC>(M, T, Y, P, r, h, active, final_st, epoch);
   }
   flush_hist<HIST>(P, h);
+}
+
+// ------------------------------------------------------------------ serving: one kernel over a shared ring
+// Persistent warps over the ring of VMs of every admitted request (continuous
+// batching). Each ring entry names a request slot and a VM of that request's
+// batch; lanes claim entries for themselves (two or three atomic adds per
+// warp, never past the entries the host has published, so no lane waits for
+// work that is not there and nobody retries), run the VM with the same step as the batch kernels, store it
+// back and count it off its request. The lane that stops a request's last VM
+// writes the request's completion word in host-mapped memory.
+//
+// The instance lives as a whole: *state counts the warps that hold or are
+// claiming work. A warp with nothing to run and an empty ring leaves that
+// count and polls; to take work again it rejoins first. When the count is
+// zero, an idle warp may close the instance (compare-and-swap 0 -> CLOSING)
+// -- at once when the host has launched a newer instance (ordered after every
+// later publish), else after idle_polls polls of an empty ring, up to 16 us
+// apart --
+// and every warp that sees CLOSING returns. So warps never leave while others
+// of the instance still run work (the next instance cannot start until this
+// one has returned), and nothing waits on the host without a limit.
+constexpr unsigned long long SERVE_CLOSING = 1ull << 63;
+constexpr uint32_t kServeIdleCeiling = 1u << 16;   // about 1 s of idle polls: the warp leaves, whatever the count says
+
+__device__ __forceinline__ unsigned long long ld_acquire_u64(const unsigned long long* p) {
+  unsigned long long v;
+  asm volatile("ld.acquire.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+  return v;
+}
+
+// A VM of request `slot` has stopped and its state is stored: count it off.
+__device__ __forceinline__ void serve_finish(const ServeArgs& A, uint32_t slot) {
+  __threadfence();                                  // the VM's state before the count
+  if (atomicSub(&A.pending[slot], 1u) == 1u) {
+    __threadfence_system();                         // every VM's state before the completion word
+    *reinterpret_cast<volatile uint32_t*>(&A.done[slot]) = A.slots[slot].gen;
+  }
+}
+
+template <bool MASKED, bool CHECKED, bool CLASSIC>
+__global__ void __launch_bounds__(128, 6) k_serve(ServeArgs A, Params P0) {
+  const uint32_t lane = threadIdx.x & 31u;
+  const uint32_t lt = (1u << lane) - 1u;
+  Hist h;
+  h.zero();
+  Params P = P0;                 // per lane: P.budget is the running request's
+  Regs r{};
+  r.n = 1;
+  int32_t slot = -1;
+  uint32_t vm = 0;
+  bool active = false;
+  uint32_t final_st = ST_RUNNING;
+  uint64_t* M = nullptr;
+  const uint64_t* T = nullptr;
+  uint64_t* Y = nullptr;
+  uint32_t idle = 0;
+  bool busy = false;             // warp-uniform: this warp is counted in *A.state
+  for (;;) {
+    // ---- retire a stopped VM
+    if (slot >= 0 && !active) {
+      store_regs(A.slots[slot].S, vm, r, final_st);
+      serve_finish(A, (uint32_t)slot);
+      slot = -1;
+    }
+    // ---- claim ring positions for the idle lanes: take credits (published,
+    // unclaimed entries; a shortfall is given back, so nobody retries), then
+    // positions below the published ones with one add on the head
+    const uint32_t need = __ballot_sync(FULL, slot < 0);
+    uint32_t got = 0;
+    if (need) {
+      const int leader = __ffs(need) - 1;
+      unsigned long long base = 0;
+      int closing = 0;
+      if ((int)lane == leader) {
+        const long long c = *reinterpret_cast<volatile long long*>(A.credits);
+        if (c > 0) {
+          if (!busy) {                            // rejoin before taking work
+            if (atomicAdd(A.state, 1ull) & SERVE_CLOSING) closing = 1;
+            else busy = true;                     // counted: leaves the count only through the idle path
+          }
+          if (!closing) {
+            const long long want = __popc(need);
+            const long long old = (long long)atomicAdd(A.credits, (unsigned long long)(-want));
+            const long long g = old >= want ? want : (old > 0 ? old : 0);
+            if (g < want) atomicAdd(A.credits, (unsigned long long)(want - g));
+            if (g > 0) {
+              base = atomicAdd(A.head, (unsigned long long)g);
+              got = (uint32_t)g;
+            }
+            __threadfence();                      // the entries published before the credits, then read
+          }
+        }
+      }
+      if (__shfl_sync(FULL, closing, leader)) break;
+      busy = __shfl_sync(FULL, busy ? 1 : 0, leader) != 0;
+      __syncwarp();
+      got = __shfl_sync(FULL, got, leader);
+      base = __shfl_sync(FULL, base, leader);
+      const uint32_t rank = (uint32_t)__popc(need & lt);
+      if (((need >> lane) & 1u) && rank < got) {
+        const uint64_t e = A.ring[(base + rank) & A.ring_mask];
+        const uint32_t sl = (uint32_t)(e >> 32), v = (uint32_t)e;
+        if (sl >= A.num_slots || v >= A.slots[sl].num_vms) {
+          atomicExch(A.err, ERR_RING);          // never touch memory an entry does not own
+        } else {
+          const ServeSlot& sd = A.slots[sl];
+          slot = (int32_t)sl;
+          vm = v;
+          if (sd.S.status[v] == ST_RUNNING) {
+            P.budget = sd.budget;
+            load_regs(sd.S, P, v, r);
+            const uint64_t moff = sd.S.mem_off[v];
+            arm_regs(P, r);
+            M = sd.S.mem + moff;
+            T = sd.S.tape + (uint64_t)v * P.ellp;
+            Y = sd.S.y + (uint64_t)v * P.sp;
+            if (!CHECKED) prime(M, r);
+            active = true;
+          } else {
+            serve_finish(A, sl);                // already stopped: nothing to run
+            slot = -1;
+          }
+        }
+      }
+    }
+    if (!__any_sync(FULL, active)) {
+      if (got == 0 && __all_sync(FULL, slot < 0)) {
+        // nothing to run: leave the busy count; close the instance when no
+        // warp is busy and (a newer instance exists or the idle polls ran out)
+        // (host-mapped words are read only when the count is empty; idle
+        // warps back off from 1 to 16 us so that they do not crowd the
+        // counters the working warps use)
+        int leave = 0;
+        if (lane == 0) {
+          if (busy) atomicAdd(A.state, ~0ull);       // minus one
+          const unsigned long long st = *reinterpret_cast<volatile unsigned long long*>(A.state);
+          if (st & SERVE_CLOSING) {
+            leave = 1;
+          } else if (st == 0ull && (idle + 1u > A.idle_polls || *A.launched > A.instance)) {
+            const unsigned long long prev = atomicCAS(A.state, 0ull, SERVE_CLOSING);
+            leave = (prev == 0ull || (prev & SERVE_CLOSING)) ? 1 : 0;
+          } else if (idle > kServeIdleCeiling) {
+            leave = 1;                            // idle this long: this warp leaves (the rest still serve)
+          }
+        }
+        busy = false;
+        if (__shfl_sync(FULL, leave, 0)) break;
+        __nanosleep(1000u << min(idle, 4u));
+        ++idle;
+      }
+      continue;
+    }
+    idle = 0;
+    // ---- run an epoch
+    if constexpr (CHECKED) {
+      run_epoch<MASKED, true, false, false, false, CLASSIC>(M, T, Y, P, r, h, active, final_st, A.epoch);
+    } else {
+      run_epoch_loop<MASKED, CLASSIC>(M, T, Y, P, r, h, active, final_st, A.epoch, 0u);
+    }
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    __threadfence_system();
+    atomicAdd(A.exited, 1u);     // host-mapped: this instance's blocks are done when all have added
+  }
+}
+
+__global__ void k_ring_fill(uint64_t* __restrict__ ring, uint64_t mask, unsigned long long start, uint32_t slot,
+                            const uint32_t* __restrict__ ids, uint32_t count) {
+  for (uint32_t k = blockIdx.x * blockDim.x + threadIdx.x; k < count; k += gridDim.x * blockDim.x)
+    ring[(start + k) & mask] = ((uint64_t)slot << 32) | (uint64_t)(ids ? ids[k] : k);
+}
+
+__global__ void k_ring_publish(unsigned long long* credits, unsigned long long count) {
+  __threadfence();
+  atomicAdd(credits, count);
 }
 
 // ------------------------------------------------------------------ shared programs
@@ -773,7 +951,7 @@ int num_sms() {
 }
 
 using PlainFn = void (*)(DevState, Params, const uint32_t*, uint32_t);
-using StagedFn = void (*)(DevState, Params, Queue, uint32_t, uint32_t, uint32_t, uint32_t);
+using StagedFn = void (*)(DevState, Params, Queue, uint32_t, uint32_t, uint32_t, uint32_t, uint32_t);
 using GlobalFn = void (*)(DevState, Params, Queue, uint32_t, uint32_t);
 
 template <bool M_, bool C_, bool H_>
@@ -926,7 +1104,8 @@ cudaError_t launch_persist(const StepVariant& var, const DevState& S, const Para
   q.soft_end = Q.count > lanes ? (uint32_t)(Q.count - lanes) : 0u;
   if (sh.staged)
     pick_staged(var)<<<grid, 32u * sh.warps, sh.smem, stream>>>(S, P, q, sh.ncap, sh.slot_words, sh.epoch,
-                                                                 sh.refill_min);
+                                                                 sh.refill_min,
+                                                                 inject_wait_expiry() ? 0u : WAIT_LIMIT);
   else
     pick_global(var)<<<grid, 32u * sh.warps, 0, stream>>>(S, P, q, sh.epoch, sh.idle_exit);
   return cudaGetLastError();
@@ -970,6 +1149,81 @@ cudaError_t launch_topk(const DevState& S, uint32_t num_vms, uint32_t k, TopCand
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   k_topk<<<1, 1024, 0, stream>>>(nullptr, nullptr, cand, blocks * k, k, best);
+  return cudaGetLastError();
+}
+
+// Byte fill of device memory with 16-byte stores (p 16-byte aligned): the
+// state-store resets of a batch, as a kernel of this library so that it asks
+// for the same L1/shared split as the kernels that may be resident beside it.
+__global__ void __launch_bounds__(256) k_fill(uint8_t* __restrict__ p, uint32_t word, uint64_t bytes) {
+  const uint64_t n16 = bytes >> 4;
+  const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+  const uint4 w = make_uint4(word, word, word, word);
+  for (uint64_t k = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; k < n16; k += stride)
+    reinterpret_cast<uint4*>(p)[k] = w;
+  const uint64_t rest = bytes & 15u;
+  if (blockIdx.x == 0 && threadIdx.x < rest) p[(n16 << 4) + threadIdx.x] = (uint8_t)word;
+}
+
+cudaError_t fill_bytes(void* p, uint8_t value, uint64_t bytes, cudaStream_t stream) {
+  if (!bytes) return cudaSuccess;
+  if (reinterpret_cast<uintptr_t>(p) & 15u) return cudaMemsetAsync(p, value, bytes, stream);
+  uint64_t blocks = ((bytes >> 4) + 255u) / 256u;
+  if (blocks > (uint64_t)num_sms() * 4u) blocks = (uint64_t)num_sms() * 4u;
+  if (blocks == 0) blocks = 1;
+  k_fill<<<(uint32_t)blocks, 256, 0, stream>>>((uint8_t*)p, 0x01010101u * value, bytes);
+  return cudaGetLastError();
+}
+
+namespace {
+
+using ServeFn = void (*)(ServeArgs, Params);
+
+ServeFn pick_serve(const StepVariant& v) {
+  if (v.checked) return k_serve<false, true, false>;
+  if (v.classic) return v.masked ? k_serve<true, false, true> : k_serve<false, false, true>;
+  return v.masked ? k_serve<true, false, false> : k_serve<false, false, false>;
+}
+
+}  // namespace
+
+int serve_configure(const StepVariant& var, ServeShape& sh) {
+  const ServeFn fn = pick_serve(var);
+  // the kernels a request's admission launches while the serving kernel is
+  // resident (state resets, pack, ring fill and publish) ask for the same L1/shared split,
+  // so that an SM can host them beside it
+  const void* beside[] = {(const void*)fn, (const void*)k_pack, (const void*)k_ring_fill, (const void*)k_ring_publish,
+                          (const void*)k_fill};
+  for (const void* f : beside)
+    cudaFuncSetAttribute(f, cudaFuncAttributePreferredSharedMemoryCarveout, (int)cudaSharedmemCarveoutMaxL1);
+  cudaGetLastError();
+  int per_sm = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, 128, 0) != cudaSuccess || per_sm <= 0) {
+    cudaGetLastError();
+    return 0;
+  }
+  sh.threads = 128;
+  sh.grid = (uint32_t)(per_sm > 1 ? per_sm - 1 : 1) * (uint32_t)num_sms();
+  return per_sm;
+}
+
+cudaError_t launch_serve(const StepVariant& var, const ServeArgs& A, const Params& P, const ServeShape& sh,
+                         cudaStream_t stream) {
+  pick_serve(var)<<<sh.grid, sh.threads, 0, stream>>>(A, P);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_ring_append(uint64_t* ring, uint64_t mask, unsigned long long start, uint32_t slot,
+                               const uint32_t* ids, uint32_t count, unsigned long long* credits,
+                               cudaStream_t stream) {
+  if (count) {
+    uint32_t blocks = (count + 255u) / 256u;
+    if (blocks > (uint32_t)num_sms() * 4u) blocks = (uint32_t)num_sms() * 4u;
+    k_ring_fill<<<blocks, 256, 0, stream>>>(ring, mask, start, slot, ids, count);
+    const cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+  }
+  k_ring_publish<<<1, 1, 0, stream>>>(credits, count);
   return cudaGetLastError();
 }
 

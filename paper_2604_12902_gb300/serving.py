@@ -27,6 +27,11 @@ class rasp_request(ctypes.Structure):
                 ("max_steps", ctypes.c_uint64)]
 
 
+class rasp_pool_counters(ctypes.Structure):
+    _fields_ = [(name, ctypes.c_uint64) for name in ("admitted", "completed", "kernel_launches", "kernel_returns",
+                                                     "ring_published", "vms_in_flight", "kernel_ctas")]
+
+
 _typed = False
 
 
@@ -42,11 +47,12 @@ def _lib():
         L.rasp_pool_info.argtypes = [P, ctypes.POINTER(U64), ctypes.POINTER(U64), ctypes.POINTER(U64)]
         L.rasp_pool_cancel.argtypes = [P, U64]
         L.rasp_pool_next_done.argtypes = [P, ctypes.POINTER(U64)]
+        L.rasp_pool_stats.argtypes = [P, ctypes.POINTER(rasp_pool_counters)]
         L.rasp_pool_destroy.argtypes = [P]
         L.rasp_pool_destroy.restype = None
         L.rasp_pool_last_error.restype = ctypes.c_char_p
         for name in ("rasp_pool_create", "rasp_pool_submit", "rasp_pool_poll", "rasp_pool_read", "rasp_pool_info",
-                     "rasp_pool_cancel", "rasp_pool_next_done"):
+                     "rasp_pool_cancel", "rasp_pool_next_done", "rasp_pool_stats"):
             getattr(L, name).restype = ctypes.c_int
         _typed = True
     return L
@@ -119,6 +125,13 @@ class Pool:
         a, b, c = ctypes.c_uint64(), ctypes.c_uint64(), ctypes.c_uint64()
         _check(_lib().rasp_pool_info(self.h, ctypes.byref(a), ctypes.byref(b), ctypes.byref(c)))
         return dict(in_use=a.value, waiting=b.value, running=c.value)
+
+    def stats(self) -> dict:
+        """Pool counters: requests admitted and completed, serving kernel
+        instances launched and returned, VMs published and in flight."""
+        st = rasp_pool_counters()
+        _check(_lib().rasp_pool_stats(self.h, ctypes.byref(st)))
+        return {name: int(getattr(st, name)) for name, _ in rasp_pool_counters._fields_}
 
     def close(self):
         if getattr(self, "h", None):

@@ -14,7 +14,8 @@ ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 def _structs():
     from paper_2604_12902_gb300 import rasp as R, serving as S
     return {"rasp_config": R.rasp_config, "rasp_state_view": R.rasp_state_view, "rasp_stats": R.rasp_stats,
-            "rasp_static_run": R.rasp_static_run, "rasp_request": S.rasp_request}
+            "rasp_static_run": R.rasp_static_run, "rasp_request": S.rasp_request,
+            "rasp_pool_counters": S.rasp_pool_counters}
 
 
 def _c_layout(tmp_path, structs):

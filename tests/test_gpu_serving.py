@@ -175,3 +175,32 @@ def test_submit_refuses_null_buffers(serving):
         assert_same_state(pool.read(k), st, wl.ell, wl.s, what="after refused submits")
     finally:
         pool.close()
+
+
+def test_serving_kernel_returns_when_idle_and_relaunches(serving):
+    """The serving kernel waits for new ring entries only a bounded time: once
+    every request is read, every instance returns by itself; a request that
+    arrives later is served by a new instance, with the oracle's result."""
+    import time
+    R, S = serving
+    reqs = [request(2000 + 1000 * k, k, seed=12) for k in range(3)]
+    with S.Pool(4 << 30, reqs[0].ell, reqs[0].s) as pool:
+        for r in reqs[:2]:
+            t = pool.submit(r)
+            wait(pool, t)
+            pool.read(t)
+        t0 = time.time()
+        while True:
+            st = pool.stats()
+            if st["kernel_returns"] == st["kernel_launches"]:
+                break
+            assert time.time() - t0 < 10, st
+            time.sleep(0.01)
+        assert st["admitted"] == 2 and st["completed"] == 2 and st["vms_in_flight"] == 0
+        assert st["ring_published"] == reqs[0].num_vms + reqs[1].num_vms
+        t = pool.submit(reqs[2])
+        wait(pool, t)
+        got = pool.read(t, mem=True)
+        assert pool.stats()["kernel_launches"] == st["kernel_launches"] + 1
+    ref, _ = oracle_state(reqs[2], threads=THREADS)
+    assert_same_state(got, ref, reqs[2].ell, reqs[2].s, what="after the kernel returned")

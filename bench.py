@@ -346,9 +346,10 @@ def run_serving(args, ws, rank):
         clk.start()
         out = SV.poisson_run(pool, reqs, lam=args.lam, duration=args.duration, seed=1)
         clocks = clk.stop()
+        pool_counters = pool.stats()
         # higher arrival rates on the same requests: where does latency grow?
         for lam in [float(x) for x in args.lam_sweep.split(",") if x]:
-            o = SV.poisson_run(pool, reqs, lam=lam, duration=args.duration, seed=2, max_waiting=32)
+            o = SV.poisson_run(pool, reqs, lam=lam, duration=args.sweep_duration, seed=2, max_waiting=32)
             sweep.append({"lambda": lam, "p50_ms": o["p50_ms"], "p99_ms": o["p99_ms"],
                           "vm_steps_per_s": o["vm_steps_per_s"], "requests_done": o["requests"],
                           "rejected": o["rejected"],
@@ -362,7 +363,9 @@ def run_serving(args, ws, rank):
                                    "memory; %d distinct requests cycled; arena %.1f GiB" % (args.lam, args.duration, len(reqs), arena / 2 ** 30)},
             "serving": {"requests_done": out["requests"], "p50_ms": out["p50_ms"], "p99_ms": out["p99_ms"],
                         "wall_s": out["wall_s"], "vm_steps": out["vm_steps"], "mean_vms_per_request": out["mean_vms"],
-                        "offered_vms_per_s": offered, "request_gen_s": gen_s, "lambda_sweep": sweep},
+                        "offered_vms_per_s": offered, "request_gen_s": gen_s, "lambda_sweep": sweep,
+                        "sweep_duration_s": args.sweep_duration, "pool": pool_counters,
+                        "design": "one persistent serving kernel over a device ring shared by all admitted requests"},
             "clocks": clocks}
     print(json.dumps(line), flush=True)
 
@@ -413,8 +416,9 @@ def main():
     ap.add_argument("--lam", type=float, default=200.0, help="serving: arrival rate (requests/s)")
     ap.add_argument("--duration", type=float, default=60.0, help="serving: seconds of arrivals")
     ap.add_argument("--requests", type=int, default=64, help="serving: distinct requests (cycled)")
-    ap.add_argument("--arena-gb", type=float, default=64.0, help="serving: device arena size")
+    ap.add_argument("--arena-gb", type=float, default=192.0, help="serving: device arena size (at most 80%% of free memory)")
     ap.add_argument("--lam-sweep", default="", help="serving: further arrival rates to run, comma separated")
+    ap.add_argument("--sweep-duration", type=float, default=10.0, help="serving: seconds of arrivals per swept rate")
     ap.add_argument("--rounds", type=int, default=4, help="search: rounds")
     ap.add_argument("--tau-max", type=int, default=10 ** 5, help="search: step cap")
     ap.add_argument("--no-other", action="store_true",

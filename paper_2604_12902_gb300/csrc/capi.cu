@@ -124,6 +124,7 @@ struct rasp_batch {
   uint64_t max_cap = ~0ull;    // largest step cap of the batch (no VM runs further)
   uint32_t* d_ids2 = nullptr;  // compacted queue between budget rounds
   uint32_t* d_rcount = nullptr;
+  bool planned = true;         // buckets have schedules and launch groups
 };
 
 namespace {
@@ -281,7 +282,12 @@ int order_ids(rasp_batch* b) {
   if (!b->h_caps.empty()) {
     const std::vector<uint64_t>& caps = b->h_caps;
     std::vector<uint32_t> tmp;
-    for (const Group& k : b->groups) {
+    std::vector<Group> whole;
+    if (b->groups.empty()) {                   // not planned: one range, the whole queue
+      whole.resize(1);
+      whole[0].count = b->V;
+    }
+    for (const Group& k : b->groups.empty() ? whole : b->groups) {
       if (k.count < 2) continue;
       uint32_t cnt[66] = {0};
       for (uint32_t q = k.first; q < k.first + k.count; ++q) cnt[64u - cap_class(caps[ids[q]]) + 1u]++;
@@ -323,6 +329,8 @@ void build_groups(rasp_batch* b) {
     b->groups.push_back(g);
   }
 }
+
+int replan(rasp_batch* b);
 
 int check_device_error(rasp_batch* b) {
   int err = 0;
@@ -370,6 +378,16 @@ int rasp_batch_bytes(const rasp_config* cfg, uint64_t num_vms, const uint32_t* m
 }
 
 int rasp_batch_create(const rasp_config* cfg, uint64_t num_vms, const uint32_t* mem_words, rasp_batch** out) {
+  return rasp::create_batch(cfg, num_vms, mem_words, true, out);
+}
+
+}  // extern "C"
+
+// With plan = false the launch plan (schedules per bucket) is made by the
+// first rasp_run instead (the serving pool's batches are never run by
+// rasp_run: its kernel schedules their VMs).
+int rasp::create_batch(const rasp_config* cfg, uint64_t num_vms, const uint32_t* mem_words, bool plan,
+                       rasp_batch** out) {
   if (!out) return fail(RASP_EINVAL, "out is NULL");
   *out = nullptr;
   int rc = validate_config(cfg, num_vms, mem_words);
@@ -473,8 +491,11 @@ int rasp_batch_create(const rasp_config* cfg, uint64_t num_vms, const uint32_t* 
     b->h_ids[b->buckets[k].first + fill[k]++] = (uint32_t)v;
   }
   b->h_ids_base = b->h_ids;
-  plan_buckets(b);
-  build_groups(b);
+  if (plan) {
+    plan_buckets(b);
+    build_groups(b);
+  }
+  b->planned = plan;
   if (cfg->flags & RASP_CUDA_GRAPH) {
     if (cudaStreamCreateWithFlags(&b->cap_stream, cudaStreamNonBlocking) != cudaSuccess) {
       cudaGetLastError();
@@ -509,6 +530,8 @@ int rasp_batch_create(const rasp_config* cfg, uint64_t num_vms, const uint32_t* 
   g_err.clear();
   return RASP_OK;
 }
+
+extern "C" {
 
 int rasp_load_programs(rasp_batch* b, const int64_t* words, const uint64_t* offsets, uint64_t num_programs,
                        const uint32_t* prog_of_vm) {
@@ -724,6 +747,11 @@ extern "C" {
 int rasp_run(rasp_batch* b, uint64_t max_steps) {
   if (!b) return fail(RASP_EINVAL, "batch is NULL");
   if (!b->programs_loaded || !b->inputs_loaded) return fail(RASP_ESTATE, "load programs and inputs before rasp_run");
+  if (!b->planned) {
+    b->planned = true;
+    const int rc = replan(b);
+    if (rc) return rc;
+  }
   if (!b->cap_stream) return enqueue_run(b, b->stream, max_steps);
   // CUDA graph: capture the run once per budget on a private stream, replay it on the batch stream
   cudaGraphExec_t exec = nullptr;

@@ -8,6 +8,7 @@
 #include "engine.cuh"
 
 struct rasp_batch;
+struct rasp_config;
 
 namespace rasp {
 
@@ -140,6 +141,11 @@ cudaError_t launch_serve(const StepVariant& var, const ServeArgs& A, const Param
 cudaError_t launch_ring_append(uint64_t* ring, uint64_t mask, unsigned long long start, uint32_t slot,
                                const uint32_t* ids, uint32_t count, unsigned long long* credits,
                                cudaStream_t stream);
+
+// rasp_batch_create; with plan = false the launch plan is left to the first
+// rasp_run (the serving pool's batches are never run by rasp_run).
+int create_batch(const rasp_config* cfg, uint64_t num_vms, const uint32_t* mem_words, bool plan,
+                 rasp_batch** out);
 
 // The state store and step parameters of a batch (for the serving pool).
 const DevState& batch_dev_state(const rasp_batch* b);

@@ -108,6 +108,7 @@ struct rasp_pool {
   uint32_t* mapped = nullptr;                 // host-mapped: done[kMaxSlots] | launched | exited | err
   uint32_t* d_mapped = nullptr;
   std::vector<uint32_t> free_slots;
+  std::vector<std::pair<cudaStream_t, cudaEvent_t>> spare;   // of retired requests
   unsigned long long tail = 0;                // published positions
   uint64_t ring_used = 0;                     // VMs admitted and not yet read
   uint32_t launches = 0;
@@ -237,8 +238,12 @@ void start(rasp_pool* p, Request& r, const rasp_request& q) {
   c.arena = p->base + r.offset;
   c.arena_bytes = r.bytes;
   c.flags &= ~RASP_CUDA_GRAPH;
-  if (cudaStreamCreateWithFlags(&r.stream, cudaStreamNonBlocking) != cudaSuccess ||
-      cudaEventCreateWithFlags(&r.loaded, cudaEventDisableTiming) != cudaSuccess) {
+  if (!p->spare.empty()) {                    // streams and events are reused across requests
+    r.stream = p->spare.back().first;
+    r.loaded = p->spare.back().second;
+    p->spare.pop_back();
+  } else if (cudaStreamCreateWithFlags(&r.stream, cudaStreamNonBlocking) != cudaSuccess ||
+             cudaEventCreateWithFlags(&r.loaded, cudaEventDisableTiming) != cudaSuccess) {
     cudaGetLastError();
     r.state = RASP_REQ_DONE;
     r.error = RASP_ECUDA;
@@ -246,7 +251,7 @@ void start(rasp_pool* p, Request& r, const rasp_request& q) {
     return;
   }
   c.stream = r.stream;
-  int rc = rasp_batch_create(&c, q.num_vms, q.mem_words, &r.batch);
+  int rc = create_batch(&c, q.num_vms, q.mem_words, false, &r.batch);
   if (rc) return fail_request(r, rc, "create");
   // inputs first: each load waits until it has read the caller's buffers,
   // and the program load ends by launching the c_0 pack without waiting for
@@ -342,9 +347,14 @@ int device_error(rasp_pool* p) { return *err_word(p) ? RASP_EDEVICE : RASP_OK; }
 
 // Free an admitted request's resources (its VMs are no longer on the ring).
 void retire(rasp_pool* p, Request& r) {
-  if (r.batch) rasp_batch_destroy(r.batch);
-  if (r.loaded) cudaEventDestroy(r.loaded);
-  if (r.stream) cudaStreamDestroy(r.stream);
+  if (r.batch) rasp_batch_destroy(r.batch);      // waits for the request's stream
+  else if (r.stream) cudaStreamSynchronize(r.stream);
+  if (r.stream && r.loaded) {
+    p->spare.emplace_back(r.stream, r.loaded);
+  } else {
+    if (r.loaded) cudaEventDestroy(r.loaded);
+    if (r.stream) cudaStreamDestroy(r.stream);
+  }
   r.batch = nullptr;
   r.loaded = nullptr;
   r.stream = nullptr;
@@ -363,6 +373,10 @@ void free_pool(rasp_pool* p) {
   if (p->run_stream) cudaStreamSynchronize(p->run_stream);
   if (p->ring_stream) cudaStreamSynchronize(p->ring_stream);
   if (p->published) cudaEventDestroy(p->published);
+  for (auto& se : p->spare) {
+    cudaEventDestroy(se.second);
+    cudaStreamDestroy(se.first);
+  }
   if (p->run_stream) cudaStreamDestroy(p->run_stream);
   if (p->ring_stream) cudaStreamDestroy(p->ring_stream);
   if (p->dev) cudaFree(p->dev);

@@ -157,10 +157,9 @@ def test_budget_and_resume(rasp, sched):
 
 @pytest.mark.parametrize("sched", list(SCHEDS))
 def test_reset_repacks_c0_in_the_run(rasp, sched):
-    """rasp_reset re-packs c_0 (Sec. 2.1). On the HBM-slab persistent schedule
-    the run kernel packs each VM itself just before running it: in chunks of
-    32 queue positions while the queue lasts, one VM at a time in the tail.
-    300,000 VMs is more than the resident lanes, so both paths run. Reading
+    """rasp_reset re-packs c_0 (Sec. 2.1) on the device from the loaded
+    programs and tapes. 300,000 VMs is more than the resident lanes of the
+    persistent schedules, so their queue and tail phases both run. Reading
     the state between reset and run shows c_0."""
     wl = W.random_programs(num_vms=300_000, seed=12)
     full, _ = oracle_state(wl, threads=THREADS)
@@ -187,6 +186,23 @@ def test_reset_repacks_c0_in_the_run(rasp, sched):
         b.run()
         st = b.stats()
     assert st["vm_steps"] == int(full.steps.sum())
+
+
+@pytest.mark.parametrize("flags,w", [(0x30 | 0x10000, 64), (0x30 | 0x100, 64), (0x30, 13), (0x30 | 0x20000, 64)])
+def test_reset_then_run_matches_the_oracle(rasp, flags, w):
+    """rasp_reset re-packs c_0 after a partial run; a run from there matches
+    the oracle in every field, twice in a row: with budget rounds, with warp
+    opcode voting, at w = 13 and with the per-step block."""
+    wl = W.uneven_programs(num_vms=20000, seed=31, n_hi=1024, cap_hi=20000)
+    wl.w = w
+    full, _ = oracle_state(wl, threads=THREADS)
+    with rasp.Batch(wl.mem_words, wl.ell, wl.s, word_bits=w, flags=flags) as b:
+        b.load_workload(wl)
+        b.run(50)
+        for k in range(2):
+            b.reset()
+            b.run()
+            assert_same_state(b.read_state(), full, wl.ell, wl.s, what="reset+run %d flags %#x w %d" % (k, flags, w))
 
 
 def test_reset_repacks_shared_programs(rasp):

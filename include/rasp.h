@@ -174,14 +174,19 @@ int rasp_batch_create(const rasp_config* cfg, uint64_t num_vms,
  * program v) or [num_vms] program index per VM (one program shared by many
  * VMs, e.g. a rollout of one candidate over many inputs).
  * Resets i = a = 0, steps = 0, status = RUNNING, u_0 = y_0 = 0, y = 0.
- * EINVAL: odd program length, 2m > n of a VM using it, bad index. */
+ * EINVAL: odd program length, 2m > n of a VM using it, bad index. The copy
+ * to the device is issued before the per-program checks run (so that they
+ * overlap it); after a failed check the batch holds no programs and
+ * rasp_reset / rasp_run return ESTATE until programs are loaded again. */
 int rasp_load_programs(rasp_batch* b, const int64_t* words,
                        const uint64_t* offsets, uint64_t num_programs,
                        const uint32_t* prog_of_vm);
 
 /* Load input tapes x (u = [0, x, 0^(l-|x|)], Sec. 2.1) and per-VM step
  * caps. tape/offsets[num_vms+1] as for programs; caps NULL = no cap
- * (UINT64_MAX). Resets u_0 = 0. EINVAL: |x| > l. */
+ * (UINT64_MAX). Resets u_0 = 0. EINVAL: |x| > l, offsets not increasing;
+ * as for programs, after a failed check the batch holds no inputs until
+ * they are loaded again. */
 int rasp_load_inputs(rasp_batch* b, const int64_t* tape,
                      const uint64_t* offsets, const uint64_t* caps);
 

@@ -121,6 +121,7 @@ struct rasp_batch {
   uint32_t max_plen = 0;
   bool dirty_valid = false;    // codedirty is up to date (only the shared kernel tracks it)
   bool ids_uploaded = false;   // d_ids holds h_ids
+  bool ids_base = true;        // h_ids is h_ids_base (bucket order, no cap-class sort)
   uint64_t max_cap = ~0ull;    // largest step cap of the batch (no VM runs further)
   uint32_t* d_ids2 = nullptr;  // compacted queue between budget rounds
   uint32_t* d_rcount = nullptr;
@@ -278,6 +279,7 @@ inline uint32_t cap_class(uint64_t c) { return c ? 64u - (uint32_t)__builtin_clz
 // class -- a stable counting sort, linear in the batch. Uploads the order
 // only when it changed.
 int order_ids(rasp_batch* b) {
+  if (b->h_caps.empty() && b->ids_base && b->ids_uploaded) return RASP_OK;   // uniform caps: bucket order
   std::vector<uint32_t> ids = b->h_ids_base;
   if (!b->h_caps.empty()) {
     const std::vector<uint64_t>& caps = b->h_caps;
@@ -298,6 +300,7 @@ int order_ids(rasp_batch* b) {
   }
   if (ids == b->h_ids && b->ids_uploaded) return RASP_OK;
   b->h_ids.swap(ids);
+  b->ids_base = b->h_caps.empty();
   CK(cudaMemcpyAsync(b->d_ids, b->h_ids.data(), 4ull * b->V, cudaMemcpyHostToDevice, b->stream));
   CK(cudaStreamSynchronize(b->stream));
   b->ids_uploaded = true;
@@ -543,28 +546,46 @@ int rasp_load_programs(rasp_batch* b, const int64_t* words, const uint64_t* offs
   if (num_programs > b->V) return fail(RASP_EINVAL, "more programs (%llu) than VMs (%u)",
                                        (unsigned long long)num_programs, b->V);
   if (offsets[0] != 0) return fail(RASP_EINVAL, "offsets[0] must be 0");
-  for (uint64_t p = 0; p < num_programs; ++p) {
-    if (offsets[p + 1] < offsets[p]) return fail(RASP_EINVAL, "offsets decrease at program %llu", (unsigned long long)p);
-    if ((offsets[p + 1] - offsets[p]) & 1ull)
-      return fail(RASP_EINVAL, "program %llu has odd length (instructions are word pairs)", (unsigned long long)p);
-  }
   const uint64_t total = offsets[num_programs];
   if (total > b->mem_words) return fail(RASP_EINVAL, "programs (%llu words) exceed the batch memory", (unsigned long long)total);
   if (total && !words) return fail(RASP_EINVAL, "words is NULL");
-  for (uint32_t v = 0; v < b->V; ++v) {
-    const uint64_t p = prog_of_vm ? prog_of_vm[v] : v;
-    if (p >= num_programs) return fail(RASP_EINVAL, "prog_of_vm[%u] = %llu out of range", v, (unsigned long long)p);
-    if (offsets[p + 1] - offsets[p] > b->h_n[v])
-      return fail(RASP_EINVAL, "program of VM %u has %llu words > n = %u (need 2m <= n)", v,
-                  (unsigned long long)(offsets[p + 1] - offsets[p]), b->h_n[v]);
-  }
+  // The copies go out first and the per-program checks run on the host while
+  // they are in flight (the copies stay inside the batch's program area
+  // whatever the offsets say). A failed check discards the programs: the
+  // copy has already replaced the earlier ones.
   cudaStream_t st = b->stream;
   if (total) CK(cudaMemcpyAsync(b->d_prog, words, 8 * total, cudaMemcpyHostToDevice, st));
   CK(cudaMemcpyAsync(b->d_progoff, offsets, 8 * (num_programs + 1), cudaMemcpyHostToDevice, st));
+  if (prog_of_vm) CK(cudaMemcpyAsync(b->d_progvm, prog_of_vm, 4ull * b->V, cudaMemcpyHostToDevice, st));
+  b->programs_loaded = false;
+  uint32_t max_plen = 0;
+  int bad = RASP_OK;
+  for (uint64_t p = 0; p < num_programs && !bad; ++p) {
+    const uint64_t len = offsets[p + 1] - offsets[p];
+    if (offsets[p + 1] < offsets[p])
+      bad = fail(RASP_EINVAL, "offsets decrease at program %llu", (unsigned long long)p);
+    else if (len & 1ull)
+      bad = fail(RASP_EINVAL, "program %llu has odd length (instructions are word pairs)", (unsigned long long)p);
+    else if (!prog_of_vm && len > b->h_n[p])
+      bad = fail(RASP_EINVAL, "program of VM %llu has %llu words > n = %u (need 2m <= n)", (unsigned long long)p,
+                 (unsigned long long)len, b->h_n[p]);
+    else if (len > max_plen)
+      max_plen = (uint32_t)len;
+  }
+  for (uint32_t v = 0; prog_of_vm && v < b->V && !bad; ++v) {
+    const uint64_t p = prog_of_vm[v];
+    if (p >= num_programs)
+      bad = fail(RASP_EINVAL, "prog_of_vm[%u] = %llu out of range", v, (unsigned long long)p);
+    else if (offsets[p + 1] - offsets[p] > b->h_n[v])
+      bad = fail(RASP_EINVAL, "program of VM %u has %llu words > n = %u (need 2m <= n)", v,
+                 (unsigned long long)(offsets[p + 1] - offsets[p]), b->h_n[v]);
+  }
+  if (bad) {
+    cudaStreamSynchronize(st);   // the caller's buffers are read before the call returns
+    return bad;
+  }
   b->shared_programs = prog_of_vm != nullptr;
-  b->max_plen = 0;
-  for (uint64_t p = 0; p < num_programs; ++p)
-    b->max_plen = std::max<uint32_t>(b->max_plen, (uint32_t)(offsets[p + 1] - offsets[p]));
+  b->max_plen = max_plen;
   b->num_programs = (uint32_t)num_programs;
   if (prog_of_vm || (b->cfg.flags & RASP_SCHED_MASK) == RASP_SCHED_SHARED) {
     // VMs grouped by program (counting sort), for the shared-program schedule
@@ -573,14 +594,15 @@ int rasp_load_programs(rasp_batch* b, const int64_t* words, const uint64_t* offs
     for (uint64_t p = 0; p < num_programs; ++p) pvoff[p + 1] += pvoff[p];
     std::vector<uint32_t> fillp(pvoff.begin(), pvoff.end() - 1);
     for (uint32_t v = 0; v < b->V; ++v) pvids[fillp[prog_of_vm ? prog_of_vm[v] : v]++] = v;
-    if (b->max_plen * 8ull > 200ull * 1024ull && (b->cfg.flags & RASP_SCHED_MASK) == RASP_SCHED_SHARED)
+    if (b->max_plen * 8ull > 200ull * 1024ull && (b->cfg.flags & RASP_SCHED_MASK) == RASP_SCHED_SHARED) {
+      cudaStreamSynchronize(st);
       return fail(RASP_EINVAL, "shared-program schedule: a program of %u words does not fit in shared memory",
                   b->max_plen);
+    }
     CK(cudaMemcpyAsync(b->d_pvoff, pvoff.data(), 4 * pvoff.size(), cudaMemcpyHostToDevice, st));
     CK(cudaMemcpyAsync(b->d_pvids, pvids.data(), 4ull * b->V, cudaMemcpyHostToDevice, st));
     CK(cudaStreamSynchronize(st));
   }
-  if (prog_of_vm) CK(cudaMemcpyAsync(b->d_progvm, prog_of_vm, 4ull * b->V, cudaMemcpyHostToDevice, st));
   CK(cudaStreamSynchronize(st));   // the caller's buffers are read before the call returns
   CK(fill_bytes(b->d_hist, 0, 8 * 10, st));
   CK(launch_pack(b->S, b->d_prog, b->d_progoff, b->shared_programs ? b->d_progvm : nullptr, b->V, b->wmask, b->sp, st));
@@ -594,35 +616,46 @@ int rasp_load_inputs(rasp_batch* b, const int64_t* tape, const uint64_t* offsets
   if (!b) return fail(RASP_EINVAL, "batch is NULL");
   if (!offsets) return fail(RASP_EINVAL, "offsets is NULL");
   if (offsets[0] != 0) return fail(RASP_EINVAL, "offsets[0] must be 0");
-  bool regular = true;
-  for (uint32_t v = 0; v < b->V; ++v) {
-    if (offsets[v + 1] < offsets[v]) return fail(RASP_EINVAL, "offsets decrease at VM %u", v);
-    const uint64_t len = offsets[v + 1] - offsets[v];
-    if (len > b->ell) return fail(RASP_EINVAL, "input of VM %u has %llu words > l = %u", v, (unsigned long long)len, b->ell);
-    regular = regular && (len == b->ellp);
-  }
   if (offsets[b->V] && !tape) return fail(RASP_EINVAL, "tape is NULL");
   cudaStream_t st = b->stream;
   uint64_t* d_tape = (uint64_t*)b->S.tape;
   const bool masked = b->wmask != ~0ull;
-  if (b->ellp) {
-    if (regular && !masked) {
-      CK(cudaMemcpyAsync(d_tape, tape, 8ull * b->V * b->ellp, cudaMemcpyHostToDevice, st));
-    } else {
-      std::vector<uint64_t> buf((size_t)b->V * b->ellp, 0);
-      for (uint32_t v = 0; v < b->V; ++v)
-        for (uint64_t k = offsets[v]; k < offsets[v + 1]; ++k)
-          buf[(size_t)v * b->ellp + (k - offsets[v])] = (uint64_t)tape[k] & b->wmask;
-      CK(cudaMemcpyAsync(d_tape, buf.data(), 8 * buf.size(), cudaMemcpyHostToDevice, st));
-      CK(cudaStreamSynchronize(st));
-    }
+  // Every tape exactly l words long (l even, w = 64): one copy of the caller's
+  // array, sent before the per-VM checks (which then also prove that every
+  // length is l: none exceeds l and they sum to V l). A failed check discards
+  // the inputs: the copy has already replaced the earlier ones.
+  const bool regular = b->ellp && !masked && b->ell == b->ellp && offsets[b->V] == (uint64_t)b->V * b->ellp;
+  if (regular) CK(cudaMemcpyAsync(d_tape, tape, 8ull * b->V * b->ellp, cudaMemcpyHostToDevice, st));
+  if (caps) CK(cudaMemcpyAsync(b->d_cap, caps, 8ull * b->V, cudaMemcpyHostToDevice, st));
+  b->inputs_loaded = false;
+  int bad = RASP_OK;
+  for (uint32_t v = 0; v < b->V && !bad; ++v) {
+    if (offsets[v + 1] < offsets[v]) bad = fail(RASP_EINVAL, "offsets decrease at VM %u", v);
+    else if (offsets[v + 1] - offsets[v] > b->ell)
+      bad = fail(RASP_EINVAL, "input of VM %u has %llu words > l = %u", v,
+                 (unsigned long long)(offsets[v + 1] - offsets[v]), b->ell);
+  }
+  if (bad) {
+    cudaStreamSynchronize(st);   // the caller's buffers are read before the call returns
+    return bad;
+  }
+  if (b->ellp && !regular) {
+    std::vector<uint64_t> buf((size_t)b->V * b->ellp, 0);
+    for (uint32_t v = 0; v < b->V; ++v)
+      for (uint64_t k = offsets[v]; k < offsets[v + 1]; ++k)
+        buf[(size_t)v * b->ellp + (k - offsets[v])] = (uint64_t)tape[k] & b->wmask;
+    CK(cudaMemcpyAsync(d_tape, buf.data(), 8 * buf.size(), cudaMemcpyHostToDevice, st));
+    CK(cudaStreamSynchronize(st));
   }
   b->max_cap = ~0ull;
   if (caps) {
-    CK(cudaMemcpyAsync(b->d_cap, caps, 8ull * b->V, cudaMemcpyHostToDevice, st));
-    b->max_cap = *std::max_element(caps, caps + b->V);
+    uint64_t mx = caps[0];
     bool uniform = true;
-    for (uint32_t v = 1; v < b->V && uniform; ++v) uniform = caps[v] == caps[0];
+    for (uint32_t v = 1; v < b->V; ++v) {
+      mx = std::max(mx, caps[v]);
+      uniform = uniform && caps[v] == caps[0];
+    }
+    b->max_cap = mx;
     if (uniform) b->h_caps.clear();
     else b->h_caps.assign(caps, caps + b->V);
   } else {

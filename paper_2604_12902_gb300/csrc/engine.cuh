@@ -476,8 +476,10 @@ __device__ __forceinline__ uint32_t fast_step_ptx(uint64_t* M, const uint64_t* T
 //  - the guards of every case that needs the general path (no loaded
 //    instruction pair, invalid opcode, an address or jump target outside
 //    [0, n), RD at the end of the tape, BNZ to itself) are evaluated first,
-//    from registers only, and one warp vote leaves the loop, before anything
-//    is applied, if any lane has such a step;
+//    from registers only, each folded into one "leave" predicate by a
+//    compare-and-combine; the end of the step count is folded into the same
+//    predicate, and one warp vote leaves the loop, before anything is
+//    applied, if any lane has such a step or the count is used up;
 //  - otherwise every lane applies its step: the next instruction pair (at
 //    the jump target or at i + 2) is loaded straight into <co, cj>, the
 //    operand M[j] of ADD/MUL/PRI and the tape word of RD are loaded beside
@@ -486,101 +488,94 @@ __device__ __forceinline__ uint32_t fast_step_ptx(uint64_t* M, const uint64_t* T
 //    many steps as the smallest countdown of the warp;
 //  - i (+) 2 is taken as ip + 2 without reduction; when that reaches ilim
 //    (n, or 2^w when smaller) the next pair is not loaded, so the lane leaves
-//    at its next step and the caller reduces ip.
+//    at its next step and the caller reduces ip. Whether the pair at the new
+//    ip can be loaded (ip even and ip + 1 < ilim) is one unsigned compare of
+//    ip rotated right by one bit (an odd ip sets the top bit) against
+//    floor(ilim / 2).
 // In: kk = steps to run (>= 1, the same in every lane of mask). Out: kk =
 // steps not run; rare = 1 in the lanes whose current step needs the general
-// path (nothing of it applied); have = 0 when <co, cj> is not the next
-// instruction (odd or out-of-range target, i (+) 2 at ilim, or overwritten by
-// the step's own store). Precondition: ibase = 0, i = ip < ilim, and have = 1
-// only with ip even, ip + 1 < ilim and <co, cj> = <M[ip], M[ip+1]>.
+// path (nothing of it applied; 0 when the loop ended because kk reached 0);
+// have = 0 when <co, cj> is not the next instruction (odd or out-of-range
+// target, i (+) 2 at ilim, or overwritten by the step's own store).
+// Precondition: ibase = 0, i = ip < ilim, and have = 1 only with ip even,
+// ip + 1 < ilim and <co, cj> = <M[ip], M[ip+1]>.
 #define RASP_LOOP_A \
       "{\n\t" \
-      ".reg .pred px, pq, pv, pj, pz, pt, pe, ph, pop, p4, p6, pad, p1, p2, p3, pw, p7, pp, pst, pany, pc;\n\t" \
-      ".reg .b32 ol, oh, jl, jh, m, t0, nip, tip;\n\t" \
-      ".reg .b64 v, tv, jj, ado, adn, adt, ady, am;\n\t" \
+      ".reg .pred px, pq, po, pz, pt, pe, ph, pop, p4, p6, pad, p1, p2, p3, pw, pp, pany;\n\t" \
+      ".reg .b32 ol, oh, jl, jh, m, t0, t1, nip;\n\t" \
+      ".reg .b64 v, tv, ado, adn, adt, ady, am;\n\t" \
       "setp.ne.u32 ph, %6, 0;\n\t" \
       "RASP_LOOP:\n\t" \
       "mov.b64 {ol, oh}, %1;\n\t" \
       "mov.b64 {jl, jh}, %2;\n\t" \
+      "setp.eq.or.u32 px, %7, 0, !ph;\n\t" \
       "add.u32 t0, ol, -1;\n\t" \
-      "setp.lt.u32 pv, t0, 7;\n\t" \
-      "setp.eq.and.u32 pv, oh, 0, pv;\n\t" \
-      "setp.lt.u32 pj, jl, %12;\n\t" \
-      "setp.eq.and.u32 pj, jh, 0, pj;\n\t" \
+      "setp.ge.or.u32 px, t0, 7, px;\n\t" \
+      "setp.ne.or.u32 px, oh, 0, px;\n\t" \
       "shl.b32 m, 1, ol;\n\t"
 // opcode 5's condition pz: BNZ a != 0 (word machine); BPA 1 <= a <= 2^(w-1) - 1 (classic, %17 = 2^(w-1) - 1)
 #define RASP_LOOP_PZ_WORD "setp.ne.u64 pz, %0, 0;\n\t"
 #define RASP_LOOP_PZ_CLASSIC "add.u64 am, %0, -1;\n\tsetp.lt.u64 pz, am, %17;\n\t"
 #define RASP_LOOP_B \
-      "and.b32 t0, m, 0x20;\n\t" \
-      "setp.ne.and.u32 pt, t0, 0, pz;\n\t" \
-      "add.u32 nip, %3, 2;\n\t" \
-      "selp.b32 tip, jl, nip, pt;\n\t" \
-      "not.pred px, ph;\n\t" \
-      "not.pred pq, pv;\n\t" \
-      "or.pred px, px, pq;\n\t" \
+      "setp.eq.and.u32 pt, ol, 5, pz;\n\t" \
+      "setp.ge.u32 po, jl, %12;\n\t" \
+      "setp.ne.or.u32 po, jh, 0, po;\n\t" \
       "and.b32 t0, m, 0xDC;\n\t" \
       "setp.ne.or.u32 pad, t0, 0, pt;\n\t" \
-      "not.pred pq, pj;\n\t" \
-      "and.pred pq, pq, pad;\n\t" \
+      "and.pred pq, po, pad;\n\t" \
       "or.pred px, px, pq;\n\t" \
-      "and.b32 t0, m, 0x40;\n\t" \
-      "setp.ne.u32 p6, t0, 0;\n\t" \
+      "setp.eq.u32 p6, ol, 6;\n\t" \
       "setp.ge.and.u32 pq, %4, %14, p6;\n\t" \
       "or.pred px, px, pq;\n\t" \
       "setp.eq.and.u32 pq, jl, %3, pt;\n\t" \
       "or.pred px, px, pq;\n\t" \
       "vote.sync.any.pred pany, px, %16;\n\t" \
       "@pany bra.uni RASP_DONE;\n\t" \
-      "and.b32 t0, tip, 1;\n\t" \
-      "setp.eq.u32 pe, t0, 0;\n\t" \
-      "setp.lt.and.u32 pe, tip, %13, pe;\n\t" \
-      "mad.wide.u32 adn, tip, 8, %9;\n\t" \
-      "mov.b64 jj, {jl, jh};\n\t" \
+      "add.u32 nip, %3, 2;\n\t" \
+      "selp.b32 %3, jl, nip, pt;\n\t" \
+      "shf.l.wrap.b32 t1, %3, %3, 31;\n\t" \
+      "setp.lt.u32 pe, t1, %13;\n\t" \
+      "mad.wide.u32 adn, %3, 8, %9;\n\t" \
+      "mad.wide.u32 ado, jl, 8, %9;\n\t" \
+      "xor.b32 t1, jl, %3;\n\t" \
+      "setp.eq.u32 p1, ol, 1;\n\t" \
+      "@p1 mov.b64 %0, %2;\n\t" \
       "@pe ld.global.v2.u64 {%1, %2}, [adn];\n\t" \
       "and.b32 t0, m, 0x8C;\n\t" \
       "setp.ne.u32 pop, t0, 0;\n\t" \
-      "mad.wide.u32 ado, jl, 8, %9;\n\t" \
       "@pop ld.global.u64 v, [ado];\n\t" \
       "mad.wide.u32 adt, %4, 8, %10;\n\t" \
       "@p6 ld.global.u64 tv, [adt];\n\t" \
-      "and.b32 t0, m, 0x10;\n\t" \
-      "setp.ne.u32 p4, t0, 0;\n\t" \
+      "setp.eq.u32 p4, ol, 4;\n\t" \
       "@p4 st.global.u64 [ado], %0;\n\t" \
       "@p6 st.global.u64 [ado], tv;\n\t" \
       "or.pred pw, p4, p6;\n\t" \
-      "setp.eq.u32 p1, ol, 1;\n\t" \
       "setp.eq.u32 p2, ol, 2;\n\t" \
       "setp.eq.u32 p3, ol, 3;\n\t" \
-      "@p1 mov.b64 %0, jj;\n\t" \
       "@p2 add.u64 %0, %0, v;\n\t"
 // opcode 3 (the guards are exclusive, so each lane updates a at most once):
 // MUL a * v (word machine); SUB a - v (classic)
 #define RASP_LOOP_PD_WORD "@p3 mul.lo.u64 %0, %0, v;\n\t"
 #define RASP_LOOP_PD_CLASSIC "@p3 sub.u64 %0, %0, v;\n\t"
 #define RASP_LOOP_D \
-      "and.b32 t0, m, 0x80;\n\t" \
-      "setp.ne.u32 p7, t0, 0;\n\t" \
-      "setp.lt.and.u32 pp, %5, %15, p7;\n\t" \
+      "setp.lt.u32 pp, %5, %15;\n\t" \
+      "setp.eq.and.u32 pp, ol, 7, pp;\n\t" \
       "mad.wide.u32 ady, %5, 8, %11;\n\t" \
       "@pp st.global.u64 [ady], v;\n\t" \
       "@pp add.u32 %5, %5, 1;\n\t" \
       "@p6 add.u32 %4, %4, 1;\n\t" \
-      "mov.b32 %3, tip;\n\t" \
-      "xor.b32 t0, jl, tip;\n\t" \
-      "setp.lt.and.u32 pst, t0, 2, pw;\n\t" \
-      "not.pred pq, pst;\n\t" \
+      "setp.ge.or.u32 pq, t1, 2, !pw;\n\t" \
       "and.pred ph, pe, pq;\n\t" \
       "add.u32 %7, %7, -1;\n\t" \
-      "setp.ne.u32 pc, %7, 0;\n\t" \
-      "@pc bra.uni RASP_LOOP;\n\t" \
+      "bra.uni RASP_LOOP;\n\t" \
       "RASP_DONE:\n\t" \
+      "setp.ne.and.u32 px, %7, 0, px;\n\t" \
       "selp.u32 %8, 1, 0, px;\n\t" \
       "selp.u32 %6, 1, 0, ph;\n\t" \
       "}"
 #define RASP_LOOP_OPERANDS                                                                                 \
   : "+l"(a), "+l"(co), "+l"(cj), "+r"(ip), "+r"(u0), "+r"(y0), "+r"(have), "+r"(kk), "=r"(rare)             \
-  : "l"(M), "l"(T), "l"(Y), "r"(n), "r"(ilim - 1u), "r"(ell), "r"(s), "r"(mask), "l"(wmask >> 1),           \
+  : "l"(M), "l"(T), "l"(Y), "r"(n), "r"(ilim >> 1), "r"(ell), "r"(s), "r"(mask), "l"(wmask >> 1),           \
     "l"(wmask)                                                                                               \
   : "memory"
 

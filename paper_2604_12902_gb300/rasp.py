@@ -20,7 +20,7 @@ from .build import LIB
 RASP_OK, RASP_EINVAL, RASP_ENOMEM, RASP_ECUDA, RASP_ESTATE, RASP_EDEVICE = 0, -1, -2, -3, -4, -5
 RUNNING, HALTED, TIMEOUT, FAULT_OVERFLOW, FAULT_ADDR = 0, 1, 2, 3, 4
 WRAP, CHECKED = 0, 1
-SCHED_AUTO, SCHED_PLAIN, SCHED_PERSIST, SCHED_PERSIST_GL = 0x00, 0x10, 0x20, 0x30
+SCHED_AUTO, SCHED_PLAIN, SCHED_PERSIST, SCHED_PERSIST_GL, SCHED_SHARED = 0x00, 0x10, 0x20, 0x30, 0x40
 DISPATCH_SELECT, DISPATCH_VOTE = 0x000, 0x100
 COLLECT_STATS = 0x1000
 ISA_CLASSIC = 0x8000

@@ -73,8 +73,15 @@ enum rasp_semantics {
 #define RASP_SCHED_PERSIST     0x20u  /* persistent workers, M staged in SMEM */
 #define RASP_SCHED_PERSIST_GL  0x30u  /* persistent workers, M in HBM via L1  */
 #define RASP_SCHED_SHARED      0x40u  /* one CTA per program, program words in
-                                         SMEM (fetched while the VM has not
-                                         written into them); needs prog_of_vm */
+                                         SMEM, served from there to every VM
+                                         that has not written into them; the
+                                         c_0 pack then writes only the data
+                                         words of each slab (a VM's first
+                                         write into its program words copies
+                                         the program into its slab), and the
+                                         program words are filled in before
+                                         M is read back or another schedule
+                                         runs; needs prog_of_vm for sharing */
 #define RASP_SCHED_MASK        0xF0u
 #define RASP_DISPATCH_SELECT   0x000u /* branch-free guarded-sum step         */
 #define RASP_DISPATCH_VOTE     0x100u /* warp opcode voting, one handler/group */
@@ -91,7 +98,10 @@ enum rasp_semantics {
 #define RASP_STEP_BLOCK        0x20000u /* HBM-slab persistent schedule: evaluate
                                           every step as one predicated block
                                           (the earlier form) instead of the
-                                          epoch loop that leaves by warp vote */
+                                          epoch loop that leaves by warp vote;
+                                          shared-program schedule: one step at
+                                          a time per lane instead of the
+                                          epoch loop                           */
 #define RASP_ISA_CLASSIC       0x8000u /* the classic RASP opcode set (Sec. 1.1)
                                           on the same words: opcode 3 is SUB
                                           (a - M_j mod 2^w), opcode 5 is BPA
@@ -255,8 +265,25 @@ int rasp_top_halting(rasp_batch* b, uint32_t k, uint64_t* steps_out, uint32_t* v
  * trial, then adopts the fastest for later rasp_run calls (replacing any
  * schedule flag of the config). The machine state is left unchanged.
  * Allocates a temporary snapshot of the state (ENOMEM if it does not fit).
- * Synchronises the stream. The trial times appear in rasp_describe. */
+ * Synchronises the stream. The trial times appear in rasp_describe.
+ * With more than one memory-size bucket a second pass follows (coordinate
+ * descent over the buckets): each bucket in turn tries the other schedules
+ * and resident-CTA counts while the rest keep theirs, and keeps one only if
+ * the whole run gets more than 1 % faster. Buckets whose choices differ run
+ * as separate launches; the per-bucket trials appear in rasp_describe. */
 int rasp_autotune(rasp_batch* b, uint64_t max_steps, uint32_t reps);
+
+/* Pin the schedule of one memory-size bucket (its "index" in the "buckets"
+ * list of rasp_describe: the size class, n <= 64, 128, 256, 512, 768, 1024,
+ * 2048, 4096 and larger, counted from 0 whether or not it holds VMs):
+ * sched is RASP_SCHED_PLAIN, _PERSIST or _PERSIST_GL (RASP_SCHED_AUTO
+ * returns the bucket to the batch-wide setting); epoch, warps_per_cta and
+ * ctas_per_sm as in rasp_config (0 = default). The launch plan is the
+ * bucketing of Sec. 2.1 machines by n; results do not depend on it.
+ * EINVAL: bucket out of range, a shared-program batch, or a schedule the
+ * batch's opcode set does not run on. A later rasp_autotune replaces it. */
+int rasp_plan_bucket(rasp_batch* b, uint32_t bucket, uint32_t sched, uint32_t epoch,
+                     uint32_t warps_per_cta, uint32_t ctas_per_sm);
 
 /* Describe the launch plan as JSON into buf (NUL-terminated): per memory
  * bucket its size class, VM count, schedule, grid, warps per CTA, resident

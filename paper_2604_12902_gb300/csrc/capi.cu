@@ -71,6 +71,13 @@ struct Group {
   PersistShape shape{};
 };
 
+// A schedule and launch shape chosen for one bucket by the autotuner (in
+// place of the batch-wide rasp_config settings).
+struct BucketPlan {
+  bool set = false;
+  uint32_t sched = 0, epoch = 0, warps = 0, ctas = 0;
+};
+
 struct Layout {
   size_t off_i, off_a, off_steps, off_cap, off_status, off_uhead, off_ylen, off_n, off_memoff;
   size_t off_mem, off_prog, off_progoff, off_progvm, off_tape, off_y, off_ids, off_heads, off_err,
@@ -109,6 +116,7 @@ struct rasp_batch {
   std::vector<uint64_t> h_caps;      // per-VM caps (empty: all uncapped)
   std::vector<Bucket> buckets;
   std::vector<Group> groups;
+  std::vector<BucketPlan> over;      // per-bucket autotuned choices (empty: the batch-wide settings)
   uint64_t launches = 0;
   // CUDA graphs of rasp_run, one per budget (RASP_CUDA_GRAPH)
   cudaStream_t cap_stream = nullptr;
@@ -120,6 +128,7 @@ struct rasp_batch {
   uint32_t num_programs = 0;
   uint32_t max_plen = 0;
   bool dirty_valid = false;    // codedirty is up to date (only the shared kernel tracks it)
+  bool code_lazy = false;      // slabs of VMs with codedirty = 0 lack their program words (lazy pack)
   bool ids_uploaded = false;   // d_ids holds h_ids
   bool ids_base = true;        // h_ids is h_ids_base (bucket order, no cap-class sort)
   uint64_t max_cap = ~0ull;    // largest step cap of the batch (no VM runs further)
@@ -216,13 +225,18 @@ StepVariant variant_of(const rasp_batch* b) {
   return v;
 }
 
-// Choose a schedule and launch shape per bucket.
+// Choose a schedule and launch shape per bucket: the batch-wide settings of
+// rasp_config, or the bucket's own autotuned choice.
 void plan_buckets(rasp_batch* b) {
-  const uint32_t forced = b->cfg.flags & RASP_SCHED_MASK;
   const StepVariant var = variant_of(b);
-  for (Bucket& k : b->buckets) {
+  for (size_t bi = 0; bi < b->buckets.size(); ++bi) {
+    Bucket& k = b->buckets[bi];
     if (!k.count) continue;
-    uint32_t sched = forced;
+    const bool own = bi < b->over.size() && b->over[bi].set;
+    const uint32_t cfg_epoch = own ? b->over[bi].epoch : b->cfg.epoch;
+    const uint32_t cfg_warps = own ? b->over[bi].warps : b->cfg.warps_per_cta;
+    const uint32_t cfg_ctas = own ? b->over[bi].ctas : b->cfg.ctas_per_sm;
+    uint32_t sched = own ? b->over[bi].sched : (b->cfg.flags & RASP_SCHED_MASK);
     if (sched == RASP_SCHED_SHARED) {
       k.sched = sched;                     // one launch over programs, see build_groups
       continue;
@@ -240,9 +254,10 @@ void plan_buckets(rasp_batch* b) {
     if (sched == RASP_SCHED_PERSIST && staged_bytes > 220u * 1024u) sched = RASP_SCHED_PERSIST_GL;
     k.sched = sched;
     PersistShape& sh = k.shape;
+    sh = PersistShape{};
     sh.ncap = k.ncap;
     sh.slot_words = slot;
-    sh.epoch = b->cfg.epoch ? b->cfg.epoch : 32u;
+    sh.epoch = cfg_epoch ? cfg_epoch : 32u;
     if (sched == RASP_SCHED_PERSIST) {
       sh.staged = true;
       sh.warps = 1;
@@ -251,10 +266,10 @@ void plan_buckets(rasp_batch* b) {
       sh.staged = false;
       sh.warps = 4;
       sh.refill_min = 1;
-      sh.epoch = b->cfg.epoch ? b->cfg.epoch : 128u;
+      sh.epoch = cfg_epoch ? cfg_epoch : 128u;
       sh.idle_exit = std::min<uint32_t>(b->cfg.refill_min, 32u);   // epoch loop: end an epoch after this many stops
     }
-    if (b->cfg.warps_per_cta) sh.warps = std::min<uint32_t>(b->cfg.warps_per_cta, 8u);
+    if (cfg_warps) sh.warps = std::min<uint32_t>(cfg_warps, 8u);
     if (!sh.staged) sh.warps = std::min<uint32_t>(sh.warps, 4u);   // k_persist_gl: at most 128 threads
     if (b->cfg.refill_min) sh.refill_min = std::min<uint32_t>(b->cfg.refill_min, 32u);
     if (sched == RASP_SCHED_PLAIN) plain_configure(var);
@@ -262,9 +277,9 @@ void plan_buckets(rasp_batch* b) {
       if (persist_configure(var, sh) == 0) {
         plain_configure(var);
         k.sched = RASP_SCHED_PLAIN;        // cannot be resident: fall back to the plain form
-      } else if (b->cfg.ctas_per_sm && b->cfg.ctas_per_sm < sh.ctas_per_sm) {
-        sh.grid = sh.grid / sh.ctas_per_sm * b->cfg.ctas_per_sm;
-        sh.ctas_per_sm = b->cfg.ctas_per_sm;
+      } else if (cfg_ctas && cfg_ctas < sh.ctas_per_sm) {
+        sh.grid = sh.grid / sh.ctas_per_sm * cfg_ctas;
+        sh.ctas_per_sm = cfg_ctas;
       }
     }
   }
@@ -319,8 +334,11 @@ void build_groups(rasp_batch* b) {
   }
   for (const Bucket& k : b->buckets) {
     if (!k.count) continue;
+    const PersistShape& gs = b->groups.empty() ? k.shape : b->groups.back().shape;
+    const bool same_shape = gs.warps == k.shape.warps && gs.epoch == k.shape.epoch && gs.grid == k.shape.grid &&
+                            gs.ctas_per_sm == k.shape.ctas_per_sm && gs.idle_exit == k.shape.idle_exit;
     if (!b->groups.empty() && k.sched == RASP_SCHED_PERSIST_GL && b->groups.back().sched == RASP_SCHED_PERSIST_GL &&
-        b->groups.back().first + b->groups.back().count == k.first) {
+        same_shape && b->groups.back().first + b->groups.back().count == k.first) {
       b->groups.back().count += k.count;
       continue;
     }
@@ -331,6 +349,21 @@ void build_groups(rasp_batch* b) {
     g.shape = k.shape;
     b->groups.push_back(g);
   }
+}
+
+// The shared-program schedule reads program words from the program itself
+// until a VM writes one of them, so its c_0 writes only the data words.
+bool pack_lazy(const rasp_batch* b) {
+  return b->planned && (b->cfg.flags & RASP_SCHED_MASK) == RASP_SCHED_SHARED;
+}
+
+// Before anything but the shared-program kernel reads the slabs of a lazily
+// packed batch: the program words of every VM whose slab lacks them.
+cudaError_t materialize(rasp_batch* b, cudaStream_t st) {
+  if (!b->code_lazy) return cudaSuccess;
+  b->code_lazy = false;
+  return launch_materialize(b->S, b->d_prog, b->d_progoff, b->shared_programs ? b->d_progvm : nullptr, b->V,
+                            b->wmask, st);
 }
 
 int replan(rasp_batch* b);
@@ -605,7 +638,9 @@ int rasp_load_programs(rasp_batch* b, const int64_t* words, const uint64_t* offs
   }
   CK(cudaStreamSynchronize(st));   // the caller's buffers are read before the call returns
   CK(fill_bytes(b->d_hist, 0, 8 * 10, st));
-  CK(launch_pack(b->S, b->d_prog, b->d_progoff, b->shared_programs ? b->d_progvm : nullptr, b->V, b->wmask, b->sp, st));
+  b->code_lazy = pack_lazy(b);
+  CK(launch_pack(b->S, b->d_prog, b->d_progoff, b->shared_programs ? b->d_progvm : nullptr, b->V, b->wmask, b->sp,
+                 b->code_lazy, st));
   b->programs_loaded = true;
   b->dirty_valid = true;
   g_err.clear();
@@ -677,8 +712,9 @@ int rasp_reset(rasp_batch* b) {
   if (!b) return fail(RASP_EINVAL, "batch is NULL");
   if (!b->programs_loaded || !b->inputs_loaded) return fail(RASP_ESTATE, "load programs and inputs first");
   CK(cudaMemsetAsync(b->d_hist, 0, 8 * 10, b->stream));
+  b->code_lazy = pack_lazy(b);
   CK(launch_pack(b->S, b->d_prog, b->d_progoff, b->shared_programs ? b->d_progvm : nullptr, b->V, b->wmask, b->sp,
-                 b->stream));
+                 b->code_lazy, b->stream));
   b->dirty_valid = true;
   return RASP_OK;
 }
@@ -721,6 +757,10 @@ int enqueue_run(rasp_batch* b, cudaStream_t st, uint64_t max_steps) {
   for (size_t k = 0; k < b->groups.size(); ++k) {
     const Group& g = b->groups[k];
     const uint32_t* ids = b->d_ids + g.first;
+    if (g.sched != RASP_SCHED_SHARED && b->code_lazy) {
+      CK(materialize(b, st));                // these kernels read every word from the slabs
+      launches++;
+    }
     if (g.sched == RASP_SCHED_SHARED) {
       if (!b->dirty_valid) {
         // another schedule ran since c_0 and did not track code writes: every
@@ -729,7 +769,7 @@ int enqueue_run(rasp_batch* b, cudaStream_t st, uint64_t max_steps) {
         b->dirty_valid = true;
       }
       CK(launch_shared(var, b->S, P, b->d_prog, b->d_progoff, b->d_pvoff, b->d_pvids, b->num_programs,
-                       b->max_plen, st));
+                       b->max_plen, b->cfg.epoch, st));
     } else if (g.sched == RASP_SCHED_PLAIN) {
       b->dirty_valid = false;
       CK(launch_plain(var, b->S, P, ids, g.count, st));
@@ -843,6 +883,7 @@ int rasp_read_state(rasp_batch* b, uint64_t first, uint64_t count, rasp_state_vi
     }
   }
   uint64_t need = 0;
+  if (out->mem) CK(materialize(b, st));      // a lazily packed batch: program words into the slabs first
   if (out->mem) {
     for (uint64_t v = first; v < first + count; ++v) need += b->h_n[v];
     if (out->mem_words < need) return fail(RASP_EINVAL, "mem holds %llu words, the range needs %llu",
@@ -1014,7 +1055,7 @@ int rasp_autotune(rasp_batch* b, uint64_t max_steps, uint32_t reps) {
   // mutable state: i, a, steps | status, uhead, ylen | M | y | counters
   const size_t spans[][2] = {{L.off_i, L.off_cap}, {L.off_status, L.off_n}, {L.off_mem, L.off_prog},
                              {L.off_y, L.off_ids}, {L.off_hist, L.off_stats}, {L.off_dirty, L.off_dirty + b->V}};
-  const bool dirty_valid0 = b->dirty_valid;
+  const bool dirty_valid0 = b->dirty_valid, code_lazy0 = b->code_lazy;
   size_t total = 0;
   for (auto& sp : spans) total += sp[1] - sp[0];
   char* snap = nullptr;
@@ -1049,34 +1090,46 @@ int rasp_autotune(rasp_batch* b, uint64_t max_steps, uint32_t reps) {
   const bool classic = (b->cfg.flags & RASP_ISA_CLASSIC) != 0;
   const int ncand = classic ? 7 : (int)(sizeof(cands) / sizeof(cands[0])) - (b->shared_programs ? 0 : 1);
   const rasp_config saved = b->cfg;
+  b->over.clear();                         // the global pass tunes the batch-wide settings
   cudaEvent_t e0, e1;
   cudaEventCreate(&e0);
   cudaEventCreate(&e1);
-  float best = 1e30f;
-  int best_k = -1;
-  std::string rep = "{\"budget\": " + std::to_string(max_steps) + ", \"trials\": [";
   cudaError_t ce = copy_state(true);
-  for (int k = 0; ce == cudaSuccess && k < ncand; ++k) {
-    b->cfg.flags = (saved.flags & ~RASP_SCHED_MASK) | cands[k].sched;
-    b->cfg.epoch = cands[k].epoch;
-    b->cfg.warps_per_cta = cands[k].warps;
-    b->cfg.ctas_per_sm = cands[k].ctas;
-    rc = replan(b);
-    if (rc) break;
-    float tmin = 1e30f;
+  // one timed rasp_run of the current plan (the state put back before each
+  // repetition); the fastest repetition
+  auto trial = [&](float& tmin) -> int {
+    int r2 = replan(b);
+    if (r2) return r2;
+    tmin = 1e30f;
     for (uint32_t r = 0; r < reps && ce == cudaSuccess; ++r) {
       ce = copy_state(false);
       b->dirty_valid = dirty_valid0;
+      b->code_lazy = code_lazy0;
       if (ce != cudaSuccess) break;
       cudaEventRecord(e0, st);
-      rc = enqueue_run(b, st, max_steps);
-      if (rc) break;
+      r2 = enqueue_run(b, st, max_steps);
+      if (r2) return r2;
       cudaEventRecord(e1, st);
       ce = cudaEventSynchronize(e1);
       float ms = 0;
       cudaEventElapsedTime(&ms, e0, e1);
       tmin = std::min(tmin, ms);
     }
+    return RASP_OK;
+  };
+  auto adopt = [&](rasp_config& c, const Cand& k) {
+    c.flags = (saved.flags & ~RASP_SCHED_MASK) | k.sched;
+    c.epoch = k.epoch;
+    c.warps_per_cta = k.warps;
+    c.ctas_per_sm = k.ctas;
+  };
+  float best = 1e30f;
+  int best_k = -1;
+  std::string rep = "{\"budget\": " + std::to_string(max_steps) + ", \"trials\": [";
+  for (int k = 0; ce == cudaSuccess && k < ncand; ++k) {
+    adopt(b->cfg, cands[k]);
+    float tmin = 0;
+    rc = trial(tmin);
     if (rc || ce != cudaSuccess) break;
     char tmp[128];
     snprintf(tmp, sizeof(tmp), "%s{\"schedule\": \"%s\", \"ms\": %.4f}", k ? ", " : "", cands[k].name, tmin);
@@ -1086,30 +1139,100 @@ int rasp_autotune(rasp_batch* b, uint64_t max_steps, uint32_t reps) {
       best_k = k;
     }
   }
-  // leave the state as it was and adopt the fastest plan
+  rep += "]";
+  b->cfg = saved;
+  if (best_k >= 0) adopt(b->cfg, cands[best_k]);
+  // Per-bucket pass (coordinate descent over the memory-size buckets): with
+  // every other bucket on its current choice, each bucket tries the other
+  // thread-per-VM shapes and keeps one only if the whole run gets faster by
+  // more than 1 %. Buckets that end up with different shapes launch
+  // separately.
+  std::string brep;
+  int nonempty = 0;
+  for (const Bucket& k : b->buckets) nonempty += k.count ? 1 : 0;
+  if (!rc && ce == cudaSuccess && best_k >= 0 && cands[best_k].sched != RASP_SCHED_SHARED && nonempty > 1) {
+    b->over.assign(b->buckets.size(), BucketPlan{});
+    float cur = best;
+    brep = ", \"buckets\": [";
+    bool firstb = true;
+    for (size_t bi = 0; bi < b->buckets.size() && !rc && ce == cudaSuccess; ++bi) {
+      if (!b->buckets[bi].count) continue;
+      int chosen = -1;
+      std::string tr;
+      for (int k = 0; k < ncand && !rc && ce == cudaSuccess; ++k) {
+        // other epochs are left to the global pass: per bucket, the shapes
+        // that change the schedule or the resident VMs per SM
+        if (k == best_k || cands[k].sched == RASP_SCHED_SHARED || cands[k].epoch == 64 || cands[k].epoch == 256)
+          continue;
+        const BucketPlan keep = b->over[bi];
+        b->over[bi] = BucketPlan{true, cands[k].sched, cands[k].epoch, cands[k].warps, cands[k].ctas};
+        float tmin = 0;
+        rc = trial(tmin);
+        if (rc || ce != cudaSuccess) break;
+        char tmp[128];
+        snprintf(tmp, sizeof(tmp), "%s{\"schedule\": \"%s\", \"ms\": %.4f}", tr.empty() ? "" : ", ",
+                 cands[k].name, tmin);
+        tr += tmp;
+        if (tmin < cur * 0.99f) {
+          cur = tmin;
+          chosen = k;
+        } else {
+          b->over[bi] = keep;
+        }
+      }
+      char tmp[160];
+      snprintf(tmp, sizeof(tmp), "%s{\"n_max\": %u, \"chosen\": \"%s\", \"trials\": [", firstb ? "" : ", ",
+               b->buckets[bi].ncap, chosen >= 0 ? cands[chosen].name : cands[best_k].name);
+      brep += tmp + tr + "]}";
+      firstb = false;
+    }
+    brep += "]";
+    bool any = false;
+    for (const BucketPlan& o : b->over) any = any || o.set;
+    if (!any) b->over.clear();
+    char tmp[64];
+    snprintf(tmp, sizeof(tmp), ", \"per_bucket_ms\": %.4f", cur);
+    brep += tmp;
+  }
+  // leave the state as it was, with the chosen plan
   const cudaError_t ce2 = copy_state(false);
   b->dirty_valid = dirty_valid0;
+  b->code_lazy = code_lazy0;
   cudaStreamSynchronize(st);
   cudaFree(snap);
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
-  b->cfg = saved;
-  if (best_k >= 0) {
-    b->cfg.flags = (saved.flags & ~RASP_SCHED_MASK) | cands[best_k].sched;
-    b->cfg.epoch = cands[best_k].epoch;
-    b->cfg.warps_per_cta = cands[best_k].warps;
-    b->cfg.ctas_per_sm = cands[best_k].ctas;
-  }
+  if (rc || ce != cudaSuccess) b->over.clear();
   const int rc2 = replan(b);
   if (rc) return rc;
   if (rc2) return rc2;
   if (ce != cudaSuccess || ce2 != cudaSuccess)
     return fail(RASP_ECUDA, "autotune: %s", cudaGetErrorString(ce != cudaSuccess ? ce : ce2));
-  rep += "], \"chosen\": \"";
+  rep += ", \"chosen\": \"";
   rep += best_k >= 0 ? cands[best_k].name : "none";
-  rep += "\"}";
+  rep += "\"";
+  rep += brep;
+  rep += "}";
   b->tuned = rep;
   return check_device_error(b);
+}
+
+int rasp_plan_bucket(rasp_batch* b, uint32_t bucket, uint32_t sched, uint32_t epoch, uint32_t warps_per_cta,
+                     uint32_t ctas_per_sm) {
+  if (!b) return fail(RASP_EINVAL, "batch is NULL");
+  if (bucket >= b->buckets.size()) return fail(RASP_EINVAL, "bucket %u out of range (%zu buckets)", bucket,
+                                               b->buckets.size());
+  if (sched != RASP_SCHED_AUTO && sched != RASP_SCHED_PLAIN && sched != RASP_SCHED_PERSIST &&
+      sched != RASP_SCHED_PERSIST_GL)
+    return fail(RASP_EINVAL, "per-bucket schedule must be AUTO, PLAIN, PERSIST or PERSIST_GL");
+  if ((b->cfg.flags & RASP_SCHED_MASK) == RASP_SCHED_SHARED)
+    return fail(RASP_EINVAL, "the shared-program schedule runs all buckets in one launch");
+  if ((b->cfg.flags & RASP_ISA_CLASSIC) && sched == RASP_SCHED_PERSIST)
+    return fail(RASP_EINVAL, "the classic opcode set runs on the plain and HBM-slab persistent schedules only");
+  if (b->over.size() != b->buckets.size()) b->over.assign(b->buckets.size(), BucketPlan{});
+  b->over[bucket] = BucketPlan{sched != RASP_SCHED_AUTO, sched, epoch, warps_per_cta, ctas_per_sm};
+  if (!b->planned) return RASP_OK;       // planned at the first rasp_run
+  return replan(b);
 }
 
 int rasp_describe(const rasp_batch* b, char* buf, uint64_t size) {
@@ -1117,14 +1240,17 @@ int rasp_describe(const rasp_batch* b, char* buf, uint64_t size) {
   static const char* names[] = {"auto", "plain", "persist", "persist_gl", "shared"};
   std::string s = "{\"vms\": " + std::to_string(b->V) + ", \"buckets\": [";
   bool first = true;
-  for (const Bucket& k : b->buckets) {
+  for (size_t bi = 0; bi < b->buckets.size(); ++bi) {
+    const Bucket& k = b->buckets[bi];
     if (!k.count) continue;
     char tmp[512];
     snprintf(tmp, sizeof(tmp),
-             "%s{\"n_max\": %u, \"vms\": %u, \"schedule\": \"%s\", \"grid\": %u, \"warps_per_cta\": %u, "
-             "\"ctas_per_sm\": %u, \"smem\": %zu, \"epoch\": %u, \"refill_min\": %u}",
-             first ? "" : ", ", k.ncap, k.count, names[std::min<uint32_t>(k.sched >> 4, 4u)], k.shape.grid, k.shape.warps,
-             k.shape.ctas_per_sm, k.shape.smem, k.shape.epoch, k.shape.refill_min);
+             "%s{\"index\": %zu, \"n_max\": %u, \"vms\": %u, \"schedule\": \"%s\", \"grid\": %u, "
+             "\"warps_per_cta\": %u, \"ctas_per_sm\": %u, \"smem\": %zu, \"epoch\": %u, \"refill_min\": %u, "
+             "\"pinned\": %s}",
+             first ? "" : ", ", bi, k.ncap, k.count, names[std::min<uint32_t>(k.sched >> 4, 4u)], k.shape.grid, k.shape.warps,
+             k.shape.ctas_per_sm, k.shape.smem, k.shape.epoch, k.shape.refill_min,
+             (bi < b->over.size() && b->over[bi].set) ? "true" : "false");
     s += tmp;
     first = false;
   }

@@ -13,6 +13,7 @@
 #pragma once
 
 #include <cstdint>
+#include <type_traits>
 #include <cuda_runtime.h>
 
 namespace rasp {
@@ -166,16 +167,61 @@ struct Decoded {
   bool taken;       // BNZ with a != 0
 };
 
+// ---- views of a VM's memory M
+// The steps reach M through three accessors overloaded on the view. The
+// plain view is a pointer to the VM's slab in HBM. ShView is the view of a
+// VM whose program is shared by many VMs (Sec. 2.1's stored program, held
+// once per program): words [0, plen) are served from the program's copy in
+// shared memory while the VM has not written into them (Regs::clean), so a
+// slab need not hold its program words at all (lazy pack). The VM's first
+// write into a program word copies the program into its slab before it is
+// applied (copy-on-write; harmless when the slab already holds it), after
+// which every word comes from the slab. `clean` is Regs::clean; the plain
+// view ignores it.
+struct ShView {
+  uint64_t* M;            // the VM's slab (n words)
+  const uint64_t* Pg;     // the program in shared memory (plen words, masked to w)
+  uint32_t plen;          // program words (even)
+};
+
+__device__ __forceinline__ ulonglong2 mem_pair(const uint64_t* M, bool, uint32_t k) {
+  return *reinterpret_cast<const ulonglong2*>(M + k);
+}
+__device__ __forceinline__ uint64_t mem_rd(const uint64_t* M, bool, uint32_t k) { return M[k]; }
+__device__ __forceinline__ void mem_wr(uint64_t* M, bool&, uint32_t k, uint64_t v) { M[k] = v; }
+
+// k even; plen is even, so the pair lies wholly inside or outside [0, plen)
+__device__ __forceinline__ ulonglong2 mem_pair(const ShView& V, bool clean, uint32_t k) {
+  const uint64_t* src = (clean && k < V.plen) ? V.Pg : V.M;
+  return *reinterpret_cast<const ulonglong2*>(src + k);
+}
+__device__ __forceinline__ uint64_t mem_rd(const ShView& V, bool clean, uint32_t k) {
+  return (clean && k < V.plen) ? V.Pg[k] : V.M[k];
+}
+// The program into the VM's own slab (the VM's first write into a program
+// word).
+static __device__ __noinline__ void sh_copy_program(uint64_t* M, const uint64_t* Pg, uint32_t plen) {
+  for (uint32_t k = 0; k < plen; k += 2u)
+    *reinterpret_cast<ulonglong2*>(M + k) = *reinterpret_cast<const ulonglong2*>(Pg + k);
+}
+__device__ __forceinline__ void mem_wr(const ShView& V, bool& clean, uint32_t k, uint64_t v) {
+  if (clean && k < V.plen) {
+    sh_copy_program(V.M, V.Pg, V.plen);
+    clean = false;
+  }
+  V.M[k] = v;
+}
+
 // <o, j> = <M[i mod n], M[(i (+) 1) mod n]> when the pair is not one aligned
 // 16-byte word (odd n or odd i mod n, or i = 2^w - 1 where i (+) 1 wraps to 0).
-template <class WordPtr>
-__device__ __noinline__ ulonglong2 fetch_slow(WordPtr M, uint32_t ip, uint32_t n, uint64_t i, uint64_t wm) {
-  if (!(ip & 1u) && ip + 1u < n && i != wm) return *reinterpret_cast<const ulonglong2*>(M + ip);
+template <class Mem>
+__device__ __noinline__ ulonglong2 fetch_slow(Mem M, bool clean, uint32_t ip, uint32_t n, uint64_t i, uint64_t wm) {
+  if (!(ip & 1u) && ip + 1u < n && i != wm) return mem_pair(M, clean, ip);
   ulonglong2 oj;
-  oj.x = M[ip];
+  oj.x = mem_rd(M, clean, ip);
   uint32_t k1 = (i == wm) ? 0u : ip + 1u;
   if (k1 == n) k1 = 0u;
-  oj.y = M[k1];
+  oj.y = mem_rd(M, clean, k1);
   return oj;
 }
 
@@ -183,8 +229,8 @@ __device__ __noinline__ ulonglong2 fetch_slow(WordPtr M, uint32_t ip, uint32_t n
 // if the transition applies (d filled), else the machine's final status for
 // this run: HALTED (fixed point), a CHECKED fault, or TIMEOUT / RUNNING at
 // the step stop.
-template <bool MASKED, bool CHECKED, bool CLASSIC = false>
-__device__ __forceinline__ uint32_t decode(uint64_t* __restrict__ M, const Params& P, Regs& r, Decoded& d) {
+template <bool MASKED, bool CHECKED, bool CLASSIC = false, class Mem>
+__device__ __forceinline__ uint32_t decode(Mem M, const Params& P, Regs& r, Decoded& d) {
   const uint64_t wm = MASKED ? P.wmask : ~0ull;
   const uint32_t ip = r.ip, n = r.n;
   const bool wide = r.ibase != 0ull;      // i >= n
@@ -202,9 +248,9 @@ __device__ __forceinline__ uint32_t decode(uint64_t* __restrict__ M, const Param
   if (((ip | n) & 1u) == 0u) {
     // even n and even i mod n: i is even (ibase is a multiple of n), so
     // i != 2^w - 1 and M[ip], M[ip+1] is one aligned 16-byte word
-    oj = *reinterpret_cast<const ulonglong2*>(M + ip);
+    oj = mem_pair(M, r.clean, ip);
   } else {
-    oj = fetch_slow(M, ip, n, i_of(r), wm);
+    oj = fetch_slow(M, r.clean, ip, n, i_of(r), wm);
   }
   const uint64_t o = oj.x, j = oj.y;
   d.j = j;
@@ -263,17 +309,16 @@ __device__ __forceinline__ void count_step(Hist& h, uint32_t op, bool taken) {
 // One transition, general form: every case of the Sec. 2.1 equation,
 // every guard and every wrap. Returns CONT after applying it, else the final
 // status (see decode).
-template <bool MASKED, bool CHECKED, bool HIST, bool SHARED = false, bool CLASSIC = false>
-__device__ __forceinline__ uint32_t step_general(uint64_t* __restrict__ M, const uint64_t* __restrict__ T,
-                                                 uint64_t* __restrict__ Y, const Params& P, Regs& r, Hist& h,
-                                                 uint32_t plen = 0) {
+template <bool MASKED, bool CHECKED, bool HIST, bool CLASSIC = false, class Mem>
+__device__ __forceinline__ uint32_t step_general(Mem M, const uint64_t* __restrict__ T, uint64_t* __restrict__ Y,
+                                                 const Params& P, Regs& r, Hist& h) {
   Decoded d;
   const uint32_t s = decode<MASKED, CHECKED, CLASSIC>(M, P, r, d);
   if (s != CONT) return s;
   const uint32_t op = d.op, jm = d.jm;
   const uint64_t a = r.a;
   uint64_t v = 0;
-  if ((op == 2u) | (op == 3u)) v = M[jm];
+  if ((op == 2u) | (op == 3u)) v = mem_rd(M, r.clean, jm);
   const uint64_t sum = a + v;
   const uint64_t prod = CLASSIC ? a - v : a * v;    // opcode 3: MUL, or SUB in the classic set
   if constexpr (CHECKED) {
@@ -288,14 +333,13 @@ __device__ __forceinline__ uint32_t step_general(uint64_t* __restrict__ M, const
   na = (op == 2u) ? sum : na;
   na = (op == 3u) ? prod : na;
   if (MASKED) na &= P.wmask;
-  if (op == 4u) M[jm] = a;                       // M_{j mod n} <- a
-  if (SHARED && ((op == 4u) | (op == 6u)) && jm < plen) r.clean = false;
+  if (op == 4u) mem_wr(M, r.clean, jm, a);       // M_{j mod n} <- a
   if (op >= 6u) {
     if (op == 6u) {                              // M_{j mod n} <- u-bullet; u-triangle
-      M[jm] = T[r.u0];
+      mem_wr(M, r.clean, jm, T[r.u0]);
       r.u0 += 1u;
     } else {                                     // y :: M_{j mod n}
-      const uint64_t pv = M[jm];
+      const uint64_t pv = mem_rd(M, r.clean, jm);
       if (r.y0 < P.s) {
         Y[r.y0] = pv;
         r.y0 += 1u;
@@ -330,9 +374,10 @@ __device__ __forceinline__ uint32_t step_general(uint64_t* __restrict__ M, const
 // Load the instruction pair at i into r.cur when the fast path can use it:
 // r.have is true iff i < n, i is even and i + 1 < n (i even and 2^w - 1 odd,
 // so i (+) 1 = i + 1), and then r.cur = <M[i], M[i+1]>.
-__device__ __forceinline__ void prime(const uint64_t* __restrict__ M, Regs& r) {
+template <class Mem>
+__device__ __forceinline__ void prime(Mem M, Regs& r) {
   r.have = (r.ibase == 0ull) & ((r.ip & 1u) == 0u) & (r.ip + 1u < r.n);
-  if (r.have) r.cur = *reinterpret_cast<const ulonglong2*>(M + r.ip);
+  if (r.have) r.cur = mem_pair(M, r.clean, r.ip);
 }
 
 // Fast path of the default step (WRAP, no counters; any w) as one
@@ -516,12 +561,19 @@ __device__ __forceinline__ uint32_t fast_step_ptx(uint64_t* M, const uint64_t* T
 // opcode 5's condition pz: BNZ a != 0 (word machine); BPA 1 <= a <= 2^(w-1) - 1 (classic, %17 = 2^(w-1) - 1)
 #define RASP_LOOP_PZ_WORD "setp.ne.u64 pz, %0, 0;\n\t"
 #define RASP_LOOP_PZ_CLASSIC "add.u64 am, %0, -1;\n\tsetp.lt.u64 pz, am, %17;\n\t"
-#define RASP_LOOP_B \
+#define RASP_LOOP_B1 \
       "setp.eq.and.u32 pt, ol, 5, pz;\n\t" \
       "setp.ge.u32 po, jl, %12;\n\t" \
       "setp.ne.or.u32 po, jh, 0, po;\n\t" \
       "and.b32 t0, m, 0xDC;\n\t" \
-      "setp.ne.or.u32 pad, t0, 0, pt;\n\t" \
+      "setp.ne.or.u32 pad, t0, 0, pt;\n\t"
+// shared-program view: a clean VM's data access (ADD, MUL, STO, RD, PRI;
+// t0 = their opcode bits) below %20 = plen takes the general path
+#define RASP_LOOP_SH_GUARD \
+      "setp.lt.u32 pq, jl, %20;\n\t" \
+      "setp.ne.and.u32 pq, t0, 0, pq;\n\t" \
+      "or.pred px, px, pq;\n\t"
+#define RASP_LOOP_B2 \
       "and.pred pq, po, pad;\n\t" \
       "or.pred px, px, pq;\n\t" \
       "setp.eq.u32 p6, ol, 6;\n\t" \
@@ -534,13 +586,19 @@ __device__ __forceinline__ uint32_t fast_step_ptx(uint64_t* M, const uint64_t* T
       "add.u32 nip, %3, 2;\n\t" \
       "selp.b32 %3, jl, nip, pt;\n\t" \
       "shf.l.wrap.b32 t1, %3, %3, 31;\n\t" \
-      "setp.lt.u32 pe, t1, %13;\n\t" \
-      "mad.wide.u32 adn, %3, 8, %9;\n\t" \
+      "setp.lt.u32 pe, t1, %13;\n\t"
+// the next instruction pair: from the slab (%9), or through a generic
+// address from the code base %19 (shared-program view)
+#define RASP_LOOP_ADDR_GL "mad.wide.u32 adn, %3, 8, %9;\n\t"
+#define RASP_LOOP_ADDR_SH "mad.wide.u32 adn, %3, 8, %19;\n\t"
+#define RASP_LOOP_B3 \
       "mad.wide.u32 ado, jl, 8, %9;\n\t" \
       "xor.b32 t1, jl, %3;\n\t" \
       "setp.eq.u32 p1, ol, 1;\n\t" \
-      "@p1 mov.b64 %0, %2;\n\t" \
-      "@pe ld.global.v2.u64 {%1, %2}, [adn];\n\t" \
+      "@p1 mov.b64 %0, %2;\n\t"
+#define RASP_LOOP_FETCH_GL "@pe ld.global.v2.u64 {%1, %2}, [adn];\n\t"
+#define RASP_LOOP_FETCH_SH "@pe ld.v2.u64 {%1, %2}, [adn];\n\t"
+#define RASP_LOOP_B4 \
       "and.b32 t0, m, 0x8C;\n\t" \
       "setp.ne.u32 pop, t0, 0;\n\t" \
       "@pop ld.global.u64 v, [ado];\n\t" \
@@ -553,6 +611,9 @@ __device__ __forceinline__ uint32_t fast_step_ptx(uint64_t* M, const uint64_t* T
       "setp.eq.u32 p2, ol, 2;\n\t" \
       "setp.eq.u32 p3, ol, 3;\n\t" \
       "@p2 add.u64 %0, %0, v;\n\t"
+#define RASP_LOOP_B RASP_LOOP_B1 RASP_LOOP_B2 RASP_LOOP_ADDR_GL RASP_LOOP_B3 RASP_LOOP_FETCH_GL RASP_LOOP_B4
+#define RASP_LOOP_B_SH \
+  RASP_LOOP_B1 RASP_LOOP_SH_GUARD RASP_LOOP_B2 RASP_LOOP_ADDR_SH RASP_LOOP_B3 RASP_LOOP_FETCH_SH RASP_LOOP_B4
 // opcode 3 (the guards are exclusive, so each lane updates a at most once):
 // MUL a * v (word machine); SUB a - v (classic)
 #define RASP_LOOP_PD_WORD "@p3 mul.lo.u64 %0, %0, v;\n\t"
@@ -603,12 +664,40 @@ __device__ __forceinline__ uint32_t fast_loop_ptx(uint64_t* M, const uint64_t* T
   return rare;
 }
 
-template <bool MASKED, bool CHECKED, bool HIST, bool PIPE, bool SHARED = false, bool CLASSIC = false>
-__device__ __forceinline__ uint32_t one_step(uint64_t* __restrict__ M, const uint64_t* __restrict__ T,
-                                             uint64_t* __restrict__ Y, const Params& P, Regs& r, Hist& h,
-                                             const uint64_t* Pg = nullptr, uint32_t plen = 0) {
+// The epoch loop for a VM seen through a shared-program view (word opcode
+// set): instruction pairs are loaded through a generic address from the
+// code base `code` (the program in shared memory while the VM is clean, else
+// its slab), `ilim` is the fetch limit (min(plen, ilim) while clean), and a
+// data access below `dlo` (plen while clean, else 0) takes the general path,
+// so that every data access in the loop goes to the slab.
+#define RASP_LOOP_SH_OPERANDS                                                                              \
+  : "+l"(a), "+l"(co), "+l"(cj), "+r"(ip), "+r"(u0), "+r"(y0), "+r"(have), "+r"(kk), "=r"(rare)             \
+  : "l"(M), "l"(T), "l"(Y), "r"(n), "r"(ilim >> 1), "r"(ell), "r"(s), "r"(mask), "l"(wmask >> 1),           \
+    "l"(wmask), "l"(code), "r"(dlo)                                                                          \
+  : "memory"
+
+template <bool MASKED>
+__device__ __forceinline__ uint32_t fast_loop_ptx_sh(uint64_t* M, const uint64_t* code, uint32_t dlo,
+                                                     const uint64_t* T, uint64_t* Y, uint32_t n, uint32_t ell,
+                                                     uint32_t s, uint32_t ilim, uint64_t wmask, uint32_t mask,
+                                                     uint64_t& a, uint64_t& co, uint64_t& cj, uint32_t& ip,
+                                                     uint32_t& u0, uint32_t& y0, uint32_t& have, uint32_t& kk) {
+  uint32_t rare;
+  if constexpr (MASKED) {
+    asm volatile(RASP_LOOP_A RASP_LOOP_PZ_WORD RASP_LOOP_B_SH RASP_LOOP_PD_WORD
+                 "and.b64 %0, %0, %18;\n\t" RASP_LOOP_D RASP_LOOP_SH_OPERANDS);
+  } else {
+    asm volatile(RASP_LOOP_A RASP_LOOP_PZ_WORD RASP_LOOP_B_SH RASP_LOOP_PD_WORD RASP_LOOP_D
+                 RASP_LOOP_SH_OPERANDS);
+  }
+  return rare;
+}
+
+template <bool MASKED, bool CHECKED, bool HIST, bool PIPE, bool CLASSIC = false, class Mem>
+__device__ __forceinline__ uint32_t one_step(Mem M, const uint64_t* __restrict__ T, uint64_t* __restrict__ Y,
+                                             const Params& P, Regs& r, Hist& h) {
   const uint32_t ip = r.ip, n = r.n;
-  if constexpr (PIPE && !CHECKED && !HIST && !SHARED) {
+  if constexpr (PIPE && !CHECKED && !HIST && !std::is_same<Mem, ShView>::value) {
     if (r.have) {
       uint64_t co = r.cur.x, cj = r.cur.y;
       uint32_t hv = 1;
@@ -622,7 +711,7 @@ __device__ __forceinline__ uint32_t one_step(uint64_t* __restrict__ M, const uin
       }
     }
     r.have = false;
-    const uint32_t s = step_general<MASKED, CHECKED, HIST, SHARED, CLASSIC>(M, T, Y, P, r, h, plen);
+    const uint32_t s = step_general<MASKED, CHECKED, HIST, CLASSIC>(M, T, Y, P, r, h);
     if (s == CONT) prime(M, r);
     return s;
   }
@@ -631,15 +720,13 @@ __device__ __forceinline__ uint32_t one_step(uint64_t* __restrict__ M, const uin
   // aligned 16-byte word (slabs start 16-byte aligned)
   const bool aligned = ((ip & 1u) == 0u) & (ip + 1u < n) & (r.ibase == 0ull);
   if (PIPE && aligned && !r.have) {
-    r.cur = *reinterpret_cast<const ulonglong2*>(M + ip);
+    r.cur = mem_pair(M, r.clean, ip);
     r.have = true;
   }
   if (aligned) {
-    // shared-program mode: while the VM has not written into M[0, plen), its
-    // code words equal the program, so they are fetched from the one copy
-    // of the program in shared memory
-    const uint64_t* F = (SHARED && r.clean && ip + 1u < plen) ? Pg : M;
-    const ulonglong2 oj = PIPE ? r.cur : *reinterpret_cast<const ulonglong2*>(F + ip);
+    // (a shared-program view serves a clean VM's code words from the one
+    // copy of the program in shared memory)
+    const ulonglong2 oj = PIPE ? r.cur : mem_pair(M, r.clean, ip);
     const uint64_t o = oj.x, j = oj.y, a = r.a;
     const uint32_t op = (uint32_t)o, jm = (uint32_t)j;
     const bool valid = (o - 1ull) < 7ull;
@@ -652,11 +739,11 @@ __device__ __forceinline__ uint32_t one_step(uint64_t* __restrict__ M, const uin
     ulonglong2 pr = make_ulonglong2(0ull, 0ull);
     uint64_t v = 0;
     if (PIPE) {
-      if (seq_ok) seq = *reinterpret_cast<const ulonglong2*>(M + ip + 2u);
-      if (((op == 2u) | (op == 3u) | pri | taken) & jin) pr = *reinterpret_cast<const ulonglong2*>(M + (jm & ~1u));
+      if (seq_ok) seq = mem_pair(M, r.clean, ip + 2u);
+      if (((op == 2u) | (op == 3u) | pri | taken) & jin) pr = mem_pair(M, r.clean, jm & ~1u);
       v = (jm & 1u) ? pr.y : pr.x;
     } else {
-      if (((op == 2u) | (op == 3u) | pri) & jin) v = M[jm];
+      if (((op == 2u) | (op == 3u) | pri) & jin) v = mem_rd(M, r.clean, jm);
     }
     const uint64_t sum = a + v;
     const uint64_t prod = CLASSIC ? a - v : a * v;       // opcode 3: MUL, or SUB in the classic set
@@ -678,8 +765,7 @@ __device__ __forceinline__ uint32_t one_step(uint64_t* __restrict__ M, const uin
       const bool wr = (op == 4u) | rd;
       uint64_t w = a;                            // STO writes a, RD writes u-bullet
       if (rd) w = T[r.u0];
-      if (wr) M[jm] = w;
-      if (SHARED) r.clean = r.clean & !(wr & (jm < plen));
+      if (wr) mem_wr(M, r.clean, jm, w);
       const bool put = pri & (r.y0 < P.s);       // y :: M_{j mod n}
       if (put) Y[r.y0] = v;
       r.u0 += rd ? 1u : 0u;
@@ -700,7 +786,7 @@ __device__ __forceinline__ uint32_t one_step(uint64_t* __restrict__ M, const uin
     }
   }
   if (PIPE) r.have = false;
-  return step_general<MASKED, CHECKED, HIST, SHARED, CLASSIC>(M, T, Y, P, r, h, plen);
+  return step_general<MASKED, CHECKED, HIST, CLASSIC>(M, T, Y, P, r, h);
 }
 
 template <bool HIST>

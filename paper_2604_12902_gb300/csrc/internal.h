@@ -18,7 +18,8 @@ struct StepVariant {
   bool hist;     // collect per-opcode counters
   bool vote;     // warp opcode voting instead of guarded selects
   bool classic;  // classic opcode set (Sec. 1.1: SUB, BPA); plain and HBM-slab persistent, select only
-  bool block;    // HBM-slab persistent: one predicated block per step instead of the epoch loop
+  bool block;    // HBM-slab persistent: one predicated block per step instead of the epoch loop;
+                 // shared-program schedule: one step at a time per lane instead of the epoch loop
 };
 
 // Persistent-kernel launch shape for one bucket of VMs.
@@ -35,15 +36,24 @@ struct PersistShape {
   size_t smem;          // dynamic shared memory per CTA
 };
 
+// c_0 of every VM; with `lazy` the program words M[0, plen) are left
+// unwritten (shared-program schedule: the steps read them from the program).
 cudaError_t launch_pack(const DevState& S, const uint64_t* prog, const uint64_t* prog_off,
                         const uint32_t* prog_of_vm, uint32_t num_vms, uint64_t wmask, uint32_t sp,
-                        cudaStream_t stream);
+                        bool lazy, cudaStream_t stream);
 
 // Shared-program schedule: one CTA per program (program in shared memory),
-// lanes run the program's VMs pv_ids[pv_off[p] .. pv_off[p+1]).
+// lanes run the program's VMs pv_ids[pv_off[p] .. pv_off[p+1]) (epoch loop
+// for WRAP without counters, else one step at a time). The slabs of VMs
+// with codedirty = 0 need not hold their program words.
 cudaError_t launch_shared(const StepVariant& var, const DevState& S, const Params& P, const uint64_t* prog,
                           const uint64_t* prog_off, const uint32_t* pv_off, const uint32_t* pv_ids,
-                          uint32_t num_programs, uint32_t max_plen, cudaStream_t stream);
+                          uint32_t num_programs, uint32_t max_plen, uint32_t epoch, cudaStream_t stream);
+
+// M[0, plen) = the VM's program for every VM with codedirty = 0 (after a
+// lazy pack, before anything but the shared-program kernel reads the slabs).
+cudaError_t launch_materialize(const DevState& S, const uint64_t* prog, const uint64_t* prog_off,
+                               const uint32_t* prog_of_vm, uint32_t num_vms, uint64_t wmask, cudaStream_t stream);
 
 // One-time function attributes of the plain kernel (carveout).
 void plain_configure(const StepVariant& var);

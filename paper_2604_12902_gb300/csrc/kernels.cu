@@ -29,10 +29,14 @@ constexpr uint32_t WAIT_LIMIT = 1u << 22;   // mbarrier polls before giving up (
                                            // staged kernel takes its limit as an argument)
 
 // ------------------------------------------------------------------ pack
+// With `lazy` (shared programs on the shared-program schedule) the program
+// words M[0, plen) are not written: the steps read them from the program
+// itself until the VM writes one of them (see ShView), so only the data
+// words are packed.
 __global__ void __launch_bounds__(256) k_pack(DevState S, const uint64_t* __restrict__ prog,
                                               const uint64_t* __restrict__ prog_off,
                                               const uint32_t* __restrict__ prog_of_vm, uint32_t num_vms,
-                                              uint64_t wmask, uint32_t sp) {
+                                              uint64_t wmask, uint32_t sp, uint32_t lazy) {
   const uint32_t lane = threadIdx.x & 31u;
   const uint32_t warps = (gridDim.x * blockDim.x) >> 5;
   for (uint32_t v = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; v < num_vms; v += warps) {
@@ -42,7 +46,7 @@ __global__ void __launch_bounds__(256) k_pack(DevState S, const uint64_t* __rest
     const uint64_t* src = prog + po;                   // po is even: 16-byte aligned
     uint64_t* dst = S.mem + S.mem_off[v];
     const uint32_t npad = (S.n[v] + 1u) & ~1u;
-    for (uint32_t k = 2u * lane; k < npad; k += 64u) {
+    for (uint32_t k = (lazy ? (uint32_t)plen : 0u) + 2u * lane; k < npad; k += 64u) {
       ulonglong2 w;
       if (k + 1u < plen) {
         w = *reinterpret_cast<const ulonglong2*>(src + k);
@@ -181,7 +185,7 @@ __global__ void __launch_bounds__(256) k_plain(DevState S, Params P, const uint3
     if (had) store_regs(S, v, r, st);
   } else if (active) {
     do {
-      st = one_step<MASKED, CHECKED, HIST, false, false, CLASSIC>(M, T, Y, P, r, h);
+      st = one_step<MASKED, CHECKED, HIST, false, CLASSIC>(M, T, Y, P, r, h);
     } while (st == CONT);
     store_regs(S, v, r, st);
   }
@@ -202,7 +206,7 @@ __device__ __forceinline__ void run_epoch(uint64_t* M, const uint64_t* T, uint64
     }
   } else if (active) {
     for (uint32_t t = 0; t < epoch; ++t) {
-      const uint32_t s = one_step<MASKED, CHECKED, HIST, PIPE, false, CLASSIC>(M, T, Y, P, r, h);
+      const uint32_t s = one_step<MASKED, CHECKED, HIST, PIPE, CLASSIC>(M, T, Y, P, r, h);
       if (s != CONT) {
         active = false;
         final_st = s;
@@ -221,8 +225,8 @@ __device__ __forceinline__ void run_epoch(uint64_t* M, const uint64_t* T, uint64
 // with general steps counts one more step of the epoch, so the epoch always
 // ends. With idle_exit > 0 the epoch also ends once that many lanes that were
 // running at its start have stopped, so that they are refilled sooner.
-template <bool MASKED, bool CLASSIC>
-__device__ __forceinline__ void run_epoch_loop(uint64_t* M, const uint64_t* T, uint64_t* Y, const Params& P,
+template <bool MASKED, bool CLASSIC, class Mem>
+__device__ __forceinline__ void run_epoch_loop(Mem M, const uint64_t* T, uint64_t* Y, const Params& P,
                                                Regs& r, Hist& h, bool& active, uint32_t& final_st, uint32_t epoch,
                                                uint32_t idle_exit) {
   const uint32_t mask0 = __ballot_sync(FULL, active);
@@ -238,8 +242,17 @@ __device__ __forceinline__ void run_epoch_loop(uint64_t* M, const uint64_t* T, u
         const uint32_t k0 = kk;
         uint32_t hv = r.have ? 1u : 0u;
         uint64_t co = r.cur.x, cj = r.cur.y;
-        rare = fast_loop_ptx<MASKED, CLASSIC>(M, T, Y, r.n, P.ell, P.s, r.ilim, P.wmask, mask, r.a, co, cj, r.ip,
-                                              r.u0, r.y0, hv, kk);
+        if constexpr (std::is_same<Mem, ShView>::value) {
+          // clean: code from the shared program (fetch limit min(plen, ilim)),
+          // data accesses below plen through the general step
+          const bool cl = r.clean;
+          rare = fast_loop_ptx_sh<MASKED>(M.M, cl ? M.Pg : M.M, cl ? M.plen : 0u, T, Y, r.n, P.ell, P.s,
+                                          cl ? min(M.plen, r.ilim) : r.ilim, P.wmask, mask, r.a, co, cj, r.ip,
+                                          r.u0, r.y0, hv, kk);
+        } else {
+          rare = fast_loop_ptx<MASKED, CLASSIC>(M, T, Y, r.n, P.ell, P.s, r.ilim, P.wmask, mask, r.a, co, cj, r.ip,
+                                                r.u0, r.y0, hv, kk);
+        }
         r.cur.x = co;
         r.cur.y = cj;
         r.have = hv != 0u;
@@ -255,7 +268,7 @@ __device__ __forceinline__ void run_epoch_loop(uint64_t* M, const uint64_t* T, u
           r.ibase = i - r.ip;
         }
         r.have = false;
-        const uint32_t st = step_general<MASKED, false, false, false, CLASSIC>(M, T, Y, P, r, h);
+        const uint32_t st = step_general<MASKED, false, false, CLASSIC>(M, T, Y, P, r, h);
         if (st == CONT) {
           prime(M, r);
         } else {
@@ -722,15 +735,22 @@ __global__ void k_ring_publish(unsigned long long* credits, unsigned long long c
 
 // ------------------------------------------------------------------ shared programs
 // One CTA per program (grid-stride over programs): the program's words sit
-// once in shared memory and the CTA's lanes run that program's VMs, each
-// lane taking the next VM from a shared-memory counter when its VM stops.
-// Instructions are fetched from the shared copy while the VM has not written
-// into its program words (Regs::clean); data lives in the VM's own slab.
+// once in shared memory and the CTA's lanes run that program's VMs. Each VM
+// sees its memory through a shared-program view (ShView): code and other
+// program words come from the shared copy while the VM has not written into
+// them (Regs::clean), data from the VM's own slab, whose program words
+// need not have been written at c_0 (lazy pack); a VM's first write into its
+// program words copies the program into its slab. codedirty[v] records that
+// the VM's slab holds its own program words.
+//
+// k_shared: each lane takes the next VM from a shared-memory counter when
+// its VM stops and steps it with one_step (CHECKED semantics, counters).
 template <bool MASKED, bool CHECKED, bool HIST>
 __global__ void __launch_bounds__(128) k_shared(DevState S, Params P, const uint64_t* __restrict__ prog,
                                                 const uint64_t* __restrict__ prog_off,
                                                 const uint32_t* __restrict__ pv_off,
-                                                const uint32_t* __restrict__ pv_ids, uint32_t num_programs) {
+                                                const uint32_t* __restrict__ pv_ids, uint32_t num_programs,
+                                                uint32_t epoch) {
   extern __shared__ __align__(16) uint64_t ps[];
   __shared__ uint32_t next;
   Hist h;
@@ -746,7 +766,7 @@ __global__ void __launch_bounds__(128) k_shared(DevState S, Params P, const uint
     r.n = 1;
     int32_t vm = -1;
     uint32_t st = CONT;
-    uint64_t* M = S.mem;
+    ShView V{S.mem, ps, plen};
     const uint64_t* T = S.tape;
     uint64_t* Y = S.y;
     bool more = true;
@@ -759,7 +779,7 @@ __global__ void __launch_bounds__(128) k_shared(DevState S, Params P, const uint
             load_regs(S, P, v, r);
             arm_regs(P, r);
             r.clean = S.codedirty[v] == 0;
-            M = S.mem + S.mem_off[v];
+            V.M = S.mem + S.mem_off[v];
             T = S.tape + (uint64_t)v * P.ellp;
             Y = S.y + (uint64_t)v * P.sp;
             vm = (int32_t)v;
@@ -772,7 +792,7 @@ __global__ void __launch_bounds__(128) k_shared(DevState S, Params P, const uint
         if (!more) break;
         continue;
       }
-      st = one_step<MASKED, CHECKED, HIST, false, true>(M, T, Y, P, r, h, ps, plen);
+      st = one_step<MASKED, CHECKED, HIST, false>(V, T, Y, P, r, h);
       if (st != CONT) {
         store_regs(S, (uint32_t)vm, r, st);
         if (!r.clean) S.codedirty[vm] = 1;
@@ -782,6 +802,103 @@ __global__ void __launch_bounds__(128) k_shared(DevState S, Params P, const uint
     __syncthreads();   // every lane done with this program's copy
   }
   flush_hist<HIST>(P, h);
+}
+
+// k_shared_loop (WRAP, no counters): the lanes of a warp run their VMs in
+// epochs of the PTX epoch loop (fast_loop_ptx_sh: instruction pairs of a
+// clean VM loaded from the shared copy); at each epoch boundary the lanes
+// whose VM stopped store it and take the next VMs of the program (one
+// shared-memory atomic per warp).
+template <bool MASKED>
+__global__ void __launch_bounds__(128, 7) k_shared_loop(DevState S, Params P, const uint64_t* __restrict__ prog,
+                                                        const uint64_t* __restrict__ prog_off,
+                                                        const uint32_t* __restrict__ pv_off,
+                                                        const uint32_t* __restrict__ pv_ids, uint32_t num_programs,
+                                                        uint32_t epoch) {
+  extern __shared__ __align__(16) uint64_t ps[];
+  __shared__ uint32_t next;
+  const uint32_t lane = threadIdx.x & 31u;
+  Hist h;
+  h.zero();
+  for (uint32_t p = blockIdx.x; p < num_programs; p += gridDim.x) {
+    const uint64_t po = prog_off[p];
+    const uint32_t plen = (uint32_t)(prog_off[p + 1] - po);
+    for (uint32_t k = threadIdx.x; k < plen; k += blockDim.x) ps[k] = prog[po + k] & P.wmask;
+    if (threadIdx.x == 0) next = 0;
+    __syncthreads();
+    const uint32_t first = pv_off[p], count = pv_off[p + 1] - first;
+    Regs r{};
+    r.n = 1;
+    int32_t vm = -1;
+    bool active = false, more = true;
+    uint32_t final_st = ST_RUNNING;
+    ShView V{S.mem, ps, plen};
+    const uint64_t* T = S.tape;
+    uint64_t* Y = S.y;
+    for (;;) {
+      // boundary: retire stopped VMs, then refill idle lanes
+      if (vm >= 0 && !active) {
+        store_regs(S, (uint32_t)vm, r, final_st);
+        if (!r.clean) S.codedirty[vm] = 1;
+        vm = -1;
+      }
+      const uint32_t needm = __ballot_sync(FULL, vm < 0 && more);
+      if (needm) {
+        const int leader = __ffs(needm) - 1;
+        uint32_t base = 0;
+        if ((int)lane == leader) base = atomicAdd(&next, (uint32_t)__popc(needm));
+        base = __shfl_sync(FULL, base, leader);
+        if ((needm >> lane) & 1u) {
+          const uint32_t idx = base + (uint32_t)__popc(needm & ((1u << lane) - 1u));
+          if (idx < count) {
+            const uint32_t v = pv_ids[first + idx];
+            if (S.status[v] == ST_RUNNING) {
+              load_regs(S, P, v, r);
+              arm_regs(P, r);
+              r.clean = S.codedirty[v] == 0;
+              V.M = S.mem + S.mem_off[v];
+              T = S.tape + (uint64_t)v * P.ellp;
+              Y = S.y + (uint64_t)v * P.sp;
+              vm = (int32_t)v;
+              prime(V, r);
+              active = true;
+            }
+          } else {
+            more = false;
+          }
+        }
+      }
+      if (__all_sync(FULL, vm < 0 && !more)) break;
+      if (!__any_sync(FULL, active)) continue;
+      run_epoch_loop<MASKED, false>(V, T, Y, P, r, h, active, final_st, epoch, 0u);
+    }
+    __syncthreads();   // every lane done with this program's copy
+  }
+}
+
+// The program words of every VM whose slab does not hold them yet (clean VMs
+// of a lazily packed shared-program batch): M[0, plen) = P, one warp per VM,
+// 16-byte stores.
+__global__ void __launch_bounds__(256) k_materialize(DevState S, const uint64_t* __restrict__ prog,
+                                                     const uint64_t* __restrict__ prog_off,
+                                                     const uint32_t* __restrict__ prog_of_vm, uint32_t num_vms,
+                                                     uint64_t wmask) {
+  const uint32_t lane = threadIdx.x & 31u;
+  const uint32_t warps = (gridDim.x * blockDim.x) >> 5;
+  for (uint32_t v = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; v < num_vms; v += warps) {
+    if (S.codedirty[v]) continue;
+    const uint32_t p = prog_of_vm ? prog_of_vm[v] : v;
+    const uint64_t po = prog_off[p];
+    const uint32_t plen = (uint32_t)(prog_off[p + 1] - po);
+    const uint64_t* src = prog + po;
+    uint64_t* dst = S.mem + S.mem_off[v];
+    for (uint32_t k = 2u * lane; k < plen; k += 64u) {
+      ulonglong2 w = *reinterpret_cast<const ulonglong2*>(src + k);
+      w.x &= wmask;
+      w.y &= wmask;
+      *reinterpret_cast<ulonglong2*>(dst + k) = w;
+    }
+  }
 }
 
 // ------------------------------------------------------------------ stats
@@ -1017,28 +1134,29 @@ const void* persist_symbol(const StepVariant& v, bool staged) {
 
 cudaError_t launch_pack(const DevState& S, const uint64_t* prog, const uint64_t* prog_off,
                         const uint32_t* prog_of_vm, uint32_t num_vms, uint64_t wmask, uint32_t sp,
-                        cudaStream_t stream) {
+                        bool lazy, cudaStream_t stream) {
   if (!num_vms) return cudaSuccess;
   const uint32_t warps_needed = num_vms;
   uint32_t blocks = (warps_needed + 7u) / 8u;
   const uint32_t cap = (uint32_t)num_sms() * 16u;
   if (blocks > cap) blocks = cap;
-  k_pack<<<blocks, 256, 0, stream>>>(S, prog, prog_off, prog_of_vm, num_vms, wmask, sp);
+  k_pack<<<blocks, 256, 0, stream>>>(S, prog, prog_off, prog_of_vm, num_vms, wmask, sp, lazy ? 1u : 0u);
   return cudaGetLastError();
 }
 
 using SharedFn = void (*)(DevState, Params, const uint64_t*, const uint64_t*, const uint32_t*, const uint32_t*,
-                         uint32_t);
+                         uint32_t, uint32_t);
 
 SharedFn pick_shared(const StepVariant& v) {
   if (v.checked) return v.hist ? k_shared<false, true, true> : k_shared<false, true, false>;
-  if (v.masked) return v.hist ? k_shared<true, false, true> : k_shared<true, false, false>;
-  return v.hist ? k_shared<false, false, true> : k_shared<false, false, false>;
+  if (v.hist) return v.masked ? k_shared<true, false, true> : k_shared<false, false, true>;
+  if (v.block) return v.masked ? k_shared<true, false, false> : k_shared<false, false, false>;
+  return v.masked ? k_shared_loop<true> : k_shared_loop<false>;
 }
 
 cudaError_t launch_shared(const StepVariant& var, const DevState& S, const Params& P, const uint64_t* prog,
                           const uint64_t* prog_off, const uint32_t* pv_off, const uint32_t* pv_ids,
-                          uint32_t num_programs, uint32_t max_plen, cudaStream_t stream) {
+                          uint32_t num_programs, uint32_t max_plen, uint32_t epoch, cudaStream_t stream) {
   if (!num_programs) return cudaSuccess;
   const size_t smem = (size_t)((max_plen + 1u) & ~1u) * 8u;
   SharedFn fn = pick_shared(var);
@@ -1049,7 +1167,17 @@ cudaError_t launch_shared(const StepVariant& var, const DevState& S, const Param
   uint32_t grid = num_programs;
   const uint32_t cap = (uint32_t)num_sms() * 64u;
   if (grid > cap) grid = cap;
-  fn<<<grid, 128, smem, stream>>>(S, P, prog, prog_off, pv_off, pv_ids, num_programs);
+  fn<<<grid, 128, smem, stream>>>(S, P, prog, prog_off, pv_off, pv_ids, num_programs, epoch ? epoch : 128u);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_materialize(const DevState& S, const uint64_t* prog, const uint64_t* prog_off,
+                               const uint32_t* prog_of_vm, uint32_t num_vms, uint64_t wmask, cudaStream_t stream) {
+  if (!num_vms) return cudaSuccess;
+  uint32_t blocks = (num_vms + 7u) / 8u;
+  const uint32_t cap = (uint32_t)num_sms() * 16u;
+  if (blocks > cap) blocks = cap;
+  k_materialize<<<blocks, 256, 0, stream>>>(S, prog, prog_off, prog_of_vm, num_vms, wmask);
   return cudaGetLastError();
 }
 

@@ -65,7 +65,7 @@ _lib = None
 EXPORTS = ["rasp_batch_bytes", "rasp_batch_create", "rasp_load_programs", "rasp_load_inputs",
            "rasp_reset", "rasp_run", "rasp_sync", "rasp_read_state", "rasp_load_state",
            "rasp_read_stats", "rasp_describe", "rasp_autotune", "rasp_halting_histogram",
-           "rasp_top_halting", "rasp_batch_destroy", "rasp_last_error", "rasp_version"]
+           "rasp_top_halting", "rasp_plan_bucket", "rasp_batch_destroy", "rasp_last_error", "rasp_version"]
 
 
 def lib():
@@ -91,11 +91,12 @@ def lib():
         L.rasp_autotune.argtypes = [P, U64, U32]
         L.rasp_halting_histogram.argtypes = [P, P, U32, P, P]
         L.rasp_top_halting.argtypes = [P, U32, P, P, P]
+        L.rasp_plan_bucket.argtypes = [P, U32, U32, U32, U32, U32]
         L.rasp_batch_destroy.argtypes = [P]
         L.rasp_batch_destroy.restype = None
         L.rasp_last_error.restype = ctypes.c_char_p
         L.rasp_version.restype = ctypes.c_char_p
-        for name in EXPORTS[:14]:
+        for name in EXPORTS[:15]:
             getattr(L, name).restype = I
         _lib = L
     return _lib
@@ -179,6 +180,10 @@ def rasp_describe(h) -> dict:
 
 def rasp_autotune(h, max_steps: int = U64_MAX, reps: int = 2):
     _check(lib().rasp_autotune(h, int(max_steps) & U64_MAX, reps))
+
+
+def rasp_plan_bucket(h, bucket: int, sched: int, epoch: int = 0, warps_per_cta: int = 0, ctas_per_sm: int = 0):
+    _check(lib().rasp_plan_bucket(h, bucket, sched, epoch, warps_per_cta, ctas_per_sm))
 
 
 def rasp_halting_histogram(h, edges, counts, other=None):
@@ -312,6 +317,11 @@ class Batch:
         other = np.zeros(4, np.uint64)
         rasp_halting_histogram(self.h, e, counts, other)
         return counts, other
+
+    def plan_bucket(self, bucket: int, sched: int, epoch: int = 0, warps_per_cta: int = 0, ctas_per_sm: int = 0):
+        """Pin the schedule of memory-size bucket ``bucket`` (its "index" in
+        ``describe()["buckets"]``)."""
+        rasp_plan_bucket(self.h, bucket, sched, epoch, warps_per_cta, ctas_per_sm)
 
     def autotune(self, max_steps: int = U64_MAX, reps: int = 2) -> dict:
         """Time the candidate schedules on this batch (state unchanged) and

@@ -106,3 +106,87 @@ def test_shared_full_size_sampled(rasp):
     sel = {k: got[k][ids] for k in ("i", "a", "steps", "status", "uhead", "ylen", "y")}
     sel["mem"] = np.concatenate(mems)
     assert_same_state(sel, st, wl.ell, wl.s, what="shared full-size sample")
+
+
+STEP_BLOCK, COLLECT_STATS = 0x20000, 0x1000
+
+
+@pytest.mark.parametrize("extra", [0, STEP_BLOCK, COLLECT_STATS], ids=["epoch-loop", "per-step", "counters"])
+def test_shared_forms_every_vm(rasp, extra):
+    """The three shared-program kernels (the epoch loop, and the one-step
+    form with and without counters) against the oracle, on templates and on
+    self-modifying code that writes into the shared program words."""
+    for wl in (W.shared_programs(num_programs=256, vms_per_program=32, seed=12), self_modifying_shared(P=150, R=24)):
+        st, _ = oracle_state(wl, threads=THREADS)
+        got, _ = run(rasp, wl, SHARED | extra)
+        assert_same_state(got, st, wl.ell, wl.s, what="shared %s flags %#x" % (wl.name, extra))
+
+
+def test_shared_checked_semantics(rasp):
+    """CHECKED semantics on the shared-program schedule (one-step form)."""
+    wl = self_modifying_shared(P=120, R=16, seed=13)
+    st, _ = oracle_state(wl, checked=True, threads=THREADS)
+    with rasp.Batch(wl.mem_words, wl.ell, wl.s, semantics=rasp.CHECKED, flags=SHARED) as b:
+        b.load_workload(wl)
+        b.run()
+        got = b.read_state()
+    assert_same_state(got, st, wl.ell, wl.s, what="shared CHECKED")
+
+
+def test_shared_lazy_pack_read_back_midway(rasp):
+    """c_0 of the shared-program schedule writes only data words; reading M
+    back fills in the program words first. Reading midway, running on,
+    resetting and running again all match the oracle."""
+    wl = self_modifying_shared(P=120, R=16, seed=11)
+    part, _ = oracle_state(wl, budget=30, threads=THREADS)
+    st, _ = oracle_state(wl, threads=THREADS)
+    with rasp.Batch(wl.mem_words, wl.ell, wl.s, flags=SHARED) as b:
+        b.load_workload(wl)
+        b.run(30)
+        assert_same_state(b.read_state(), part, wl.ell, wl.s, what="lazy pack, read at 30 steps")
+        b.run()
+        assert_same_state(b.read_state(), st, wl.ell, wl.s, what="lazy pack, run on after the read")
+        b.reset()
+        b.run(30)
+        assert_same_state(b.read_state(mem=False), part, wl.ell, wl.s, what="lazy pack again, no M read")
+        b.run()
+        assert_same_state(b.read_state(), st, wl.ell, wl.s, what="lazy pack again, run to the end")
+
+
+def test_shared_lazy_pack_checkpoint_restore(rasp):
+    """A checkpoint taken on one lazily packed batch, restored into another
+    lazily packed batch midway through its own run, then run on."""
+    wl = self_modifying_shared(P=100, R=12, seed=14)
+    st, _ = oracle_state(wl, threads=THREADS)
+    with rasp.Batch(wl.mem_words, wl.ell, wl.s, flags=SHARED) as b1, \
+            rasp.Batch(wl.mem_words, wl.ell, wl.s, flags=SHARED) as b2:
+        b1.load_workload(wl)
+        b1.run(25)
+        ck = b1.read_state()
+        b2.load_workload(wl)
+        b2.run(7)
+        half = wl.num_vms // 2
+        b2.load_state({k: v[:half] for k, v in ck.items() if k != "mem"} |
+                      {"mem": ck["mem"][:int(wl.mem_words[:half].astype(np.uint64).sum())]})
+        b2.run()
+        got = b2.read_state()
+    assert_same_state(got, st, wl.ell, wl.s, what="restored halves then run on")
+
+
+def test_shared_lazy_pack_through_autotune(rasp):
+    """Autotuning a lazily packed batch: its non-shared trials fill in the
+    program words, the state is put back as it was (lazy), and the batch
+    then runs to the oracle's result on whichever schedule was chosen."""
+    wl = self_modifying_shared(P=100, R=20, seed=15)
+    st, _ = oracle_state(wl, threads=THREADS)
+    with rasp.Batch(wl.mem_words, wl.ell, wl.s, flags=SHARED) as b:
+        b.load_workload(wl)
+        b.run(20)
+        before = b.read_state(mem=False)
+        rep = b.autotune(reps=1)
+        after = b.read_state(mem=False)
+        for k in before:
+            assert np.array_equal(before[k], after[k]), k
+        b.run()
+        got = b.read_state()
+    assert_same_state(got, st, wl.ell, wl.s, what="lazy pack through autotune (%s)" % rep["chosen"])

@@ -125,6 +125,53 @@ def test_autotune_leaves_state_and_keeps_parity(rasp, uneven64k):
         assert rep["chosen"] in [t["schedule"] for t in rep["trials"]]
         best = min(rep["trials"], key=lambda t: t["ms"])
         assert rep["chosen"] == best["schedule"]
+        # the per-bucket pass: one entry per non-empty bucket, each choice one
+        # of its trials or the global choice; pinned buckets show in the plan
+        plan = b.describe()
+        assert len(rep["buckets"]) == len(plan["buckets"]) > 1
+        for entry in rep["buckets"]:
+            names = [t["schedule"] for t in entry["trials"]]
+            assert entry["chosen"] in names + [rep["chosen"]]
+            assert rep["chosen"] not in names
+        pinned = sum(e["chosen"] != rep["chosen"] for e in rep["buckets"])
+        assert sum(k["pinned"] for k in plan["buckets"]) == pinned
+        assert rep["per_bucket_ms"] <= best["ms"]
         b.run()
         got = b.read_state()
     assert_same_state(got, st, wl.ell, wl.s, what="after autotune (%s)" % rep["chosen"])
+
+
+PLAIN, PERSIST, PERSIST_GL, AUTO = 0x10, 0x20, 0x30, 0x00
+
+
+@pytest.mark.parametrize("flags", [0x00, 0x4000], ids=["eager", "cuda-graph"])
+def test_pinned_bucket_schedules_every_vm(rasp, uneven64k, flags):
+    """Every memory-size bucket on a schedule of its own (plain, SMEM-staged,
+    HBM-slab with 3 or 5 resident CTAs per SM and 2-warp CTAs, batch-wide):
+    separate launches per bucket, every VM equal to the oracle's, with
+    budget rounds, resumed runs and graph replay."""
+    wl, st = uneven64k
+    choices = [(PLAIN, 0, 0, 0), (PERSIST, 32, 1, 0), (PERSIST_GL, 128, 4, 3), (PERSIST_GL, 64, 2, 5), (AUTO, 0, 0, 0)]
+    part, _ = oracle_state(wl, budget=3000, threads=THREADS)
+    with rasp.Batch(wl.mem_words, wl.ell, wl.s, flags=flags | rasp.BUDGET_ROUNDS) as b:
+        b.load_workload(wl)
+        buckets = b.describe()["buckets"]
+        assert len(buckets) > 3
+        for j, k in enumerate(buckets):
+            b.plan_bucket(k["index"], *choices[j % len(choices)])
+        plan = b.describe()
+        assert [k["pinned"] for k in plan["buckets"]] == [choices[j % len(choices)][0] != AUTO
+                                                         for j in range(len(buckets))]
+        assert len(plan["launches"]) > 3
+        b.run(3000)
+        assert_same_state(b.read_state(), part, wl.ell, wl.s, what="pinned buckets, budget 3000")
+        b.run()
+        assert_same_state(b.read_state(), st, wl.ell, wl.s, what="pinned buckets, resumed")
+        b.reset()
+        b.run(3000)
+        b.run()
+        assert_same_state(b.read_state(), st, wl.ell, wl.s, what="pinned buckets, after reset")
+        with pytest.raises(rasp.RaspError):
+            b.plan_bucket(99, PLAIN)
+        with pytest.raises(rasp.RaspError):
+            b.plan_bucket(0, 0x40)

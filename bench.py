@@ -131,9 +131,10 @@ def make_workload(name: str, rank: int, vms: int = 1 << 20, out_arity: int = 0):
         return wl, ("%s uneven programs (length log-U[8,512], n log-U[16,4096], cap log-U[64,65536], "
                     "15%% built never to halt, ~33%% time out), l=16, s=8" % format(wl.num_vms, ","))
     if name == "shared":
-        wl = W.shared_programs()
-        return wl, ("16,384 programs (48 instr, loop templates) x 256 tapes of 8 ints U[-50,50] = 4,194,304 VMs, "
-                    "n = 96 program + 128 data words, cap 2048")
+        progs = 16384 if vms == 1 << 20 else max(1, vms // 256)    # --vms scales the number of programs
+        wl = W.shared_programs(num_programs=progs)
+        return wl, ("%s programs (48 instr, loop templates) x 256 tapes of 8 ints U[-50,50] = %s VMs, "
+                    "n = 96 program + 128 data words, cap 2048" % (format(progs, ","), format(wl.num_vms, ",")))
     if name == "halting":
         from paper_2604_12902_gb300 import sampler as S
         first, count = shard_range(rank, vms)
@@ -190,7 +191,16 @@ def algorithmic_bytes(stats, fetch_from_smem: bool = False) -> float:
     return float(b)
 
 
-KERNEL_OF = {"persist_gl": "k_persist_gl", "plain": "k_plain", "persist_smem": "k_persist", "shared": "k_shared"}
+KERNEL_OF = {"persist_gl": "k_persist_gl", "plain": "k_plain", "persist_smem": "k_persist", "shared": "k_shared_loop"}
+SCHED_NAME = {0x10: "plain", 0x20: "persist_smem", 0x30: "persist_gl", 0x40: "shared"}
+
+
+def run_kernel_name(chosen: str, flags: int) -> str:
+    """The run kernel a schedule name (autotuner report) or flag set selects."""
+    kernel = KERNEL_OF.get(chosen.split()[0], chosen)
+    if kernel == "k_shared_loop" and flags & 0x20000:     # RASP_STEP_BLOCK: the one-step form
+        kernel = "k_shared"
+    return kernel
 
 
 def time_config(R, torch, wl, desc, flags, steps, warmup, flush_l2=False):
@@ -208,8 +218,8 @@ def time_config(R, torch, wl, desc, flags, steps, warmup, flush_l2=False):
             bs.run()
             stats = bs.stats()
         chosen = tuned["chosen"] if tuned else "flags %#x" % flags
-        kernel = KERNEL_OF.get(chosen.split()[0], chosen)
-        alg = algorithmic_bytes(stats, fetch_from_smem=kernel == "k_shared")
+        kernel = run_kernel_name(chosen if tuned else SCHED_NAME.get(flags & 0xF0, "persist_gl"), flags)
+        alg = algorithmic_bytes(stats, fetch_from_smem=kernel.startswith("k_shared"))
         for _ in range(warmup):
             b.reset()
             b.run()
@@ -244,16 +254,17 @@ def time_config(R, torch, wl, desc, flags, steps, warmup, flush_l2=False):
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
                          "traffic": None, "kernel": kernel, "peak_kind": peak_kind,
                          "bytes_per_step": alg / max(stats["vm_steps"], 1),
-                         "fetch_from_smem_excluded": kernel == "k_shared",
+                         "fetch_from_smem_excluded": kernel.startswith("k_shared"),
                          "kernel_ms": run_avg, "pack_ms": float(np.mean(pack_ms))},
             "outcomes": outcomes(st)}
 
 
-def other_configs(R, torch, steps, warmup):
+def other_configs(R, torch, steps, warmup, serving=True):
     """The benchmark's other single-GPU configurations, each timed like the
     headline after it: 1,024 random programs (config 1), the uneven batch of
-    4,194,304 programs in its CUDA-graph form (config 3) and the
-    shared-program rollout of 16,384 programs x 256 tapes (config 4)."""
+    4,194,304 programs in its CUDA-graph form (config 3), the shared-program
+    rollout of 16,384 programs x 256 tapes (config 4), and serving at 200
+    requests/s for 60 s (config 5: p50/p99 latency and VM-steps/s)."""
     out = {}
     for name in ("random", "shared", "uneven"):
         t0 = time.perf_counter()
@@ -268,6 +279,18 @@ def other_configs(R, torch, steps, warmup):
         out[{"random": "config1_random", "uneven": "config3_uneven", "shared": "config4_shared"}[name]] = rec
         del wl
         torch.cuda.empty_cache()
+    if not serving:
+        return out
+    # config 5: serving at 200 requests/s for 60 s (request generation untimed)
+    m = serving_measure(torch, 200.0, 60.0)
+    o = m["out"]
+    out["config5_serving"] = {"workload": m["desc"], "lambda": 200.0, "duration_s": 60.0,
+                              "requests_done": o["requests"], "p50_ms": o["p50_ms"], "p99_ms": o["p99_ms"],
+                              "value": o["vm_steps_per_s"], "unit": UNIT, "vm_steps": o["vm_steps"],
+                              "wall_s": o["wall_s"], "offered_vms_per_s": m["offered"],
+                              "mean_vms_per_request": o["mean_vms"], "pool": m["pool"], "clocks": m["clocks"],
+                              "generation_s": m["gen_s"]}
+    torch.cuda.empty_cache()
     return out
 
 
@@ -320,15 +343,15 @@ def run_reference(args, ws, rank):
     print(json.dumps(line), flush=True)
 
 
-def run_serving(args, ws, rank):
+def serving_measure(torch, lam, duration, n_requests=64, arena_gb=192.0, lam_sweep=(), sweep_duration=10.0):
     """Config 5: open-loop Poisson arrivals of rollout requests (each 1k-100k
     programs drawn like the uneven batch) into one device arena; requests are
-    admitted as memory frees up and run concurrently (continuous batching)."""
-    import torch
+    admitted as memory frees up and run concurrently (continuous batching).
+    Returns the run's figures, those of any further arrival rates, the
+    clocks sampled during the main run and the pool's counters."""
     from paper_2604_12902_gb300 import serving as SV, workloads as W
-    torch.cuda.set_device(0)
     rng = np.random.default_rng(11)
-    u = rng.integers(0, 1 << 32, size=args.requests, dtype=np.uint64).astype(np.uint32)
+    u = rng.integers(0, 1 << 32, size=n_requests, dtype=np.uint64).astype(np.uint32)
     sizes = W.log_uniform_int(u, 1000, 100000)
     t0 = time.perf_counter()
     reqs = [W.uneven_programs(num_vms=int(n), seed=5, first_vm=k * 100_000, workers=os.cpu_count() or 1)
@@ -338,35 +361,46 @@ def run_serving(args, ws, rank):
         for f in ("programs", "prog_off", "tapes", "tape_off", "caps", "mem_words"):
             setattr(wl, f, _pinned_copy(torch, getattr(wl, f)))
     free, _ = torch.cuda.mem_get_info()
-    arena = int(min(args.arena_gb * 2 ** 30, free * 0.8))
+    arena = int(min(arena_gb * 2 ** 30, free * 0.8))
     sweep = []
     with SV.Pool(arena, reqs[0].ell, reqs[0].s) as pool:
         SV.poisson_run(pool, reqs[:4], lam=50.0, duration=0.2, seed=0)      # warm-up (untimed)
         clk = ClockSampler(torch.cuda.current_device())
         clk.start()
-        out = SV.poisson_run(pool, reqs, lam=args.lam, duration=args.duration, seed=1)
+        out = SV.poisson_run(pool, reqs, lam=lam, duration=duration, seed=1)
         clocks = clk.stop()
         pool_counters = pool.stats()
         # higher arrival rates on the same requests: where does latency grow?
-        for lam in [float(x) for x in args.lam_sweep.split(",") if x]:
-            o = SV.poisson_run(pool, reqs, lam=lam, duration=args.sweep_duration, seed=2, max_waiting=32)
-            sweep.append({"lambda": lam, "p50_ms": o["p50_ms"], "p99_ms": o["p99_ms"],
+        for lam2 in lam_sweep:
+            o = SV.poisson_run(pool, reqs, lam=lam2, duration=sweep_duration, seed=2, max_waiting=32)
+            sweep.append({"lambda": lam2, "p50_ms": o["p50_ms"], "p99_ms": o["p99_ms"],
                           "vm_steps_per_s": o["vm_steps_per_s"], "requests_done": o["requests"],
-                          "rejected": o["rejected"],
-                          "wall_s": o["wall_s"], "offered_vms_per_s": lam * float(np.mean([r.num_vms for r in reqs]))})
-    offered = args.lam * float(np.mean([r.num_vms for r in reqs]))
+                          "rejected": o["rejected"], "wall_s": o["wall_s"],
+                          "offered_vms_per_s": lam2 * float(np.mean([r.num_vms for r in reqs]))})
+    offered = lam * float(np.mean([r.num_vms for r in reqs]))
+    desc = ("serving: Poisson arrivals (lambda %.0f/s) for %.0f s of rollout requests, each log-U[1e3,1e5] "
+            "programs drawn as the uneven batch, inputs in pinned host memory; %d distinct requests cycled; "
+            "arena %.1f GiB" % (lam, duration, len(reqs), arena / 2 ** 30))
+    return {"out": out, "sweep": sweep, "clocks": clocks, "pool": pool_counters, "gen_s": gen_s,
+            "offered": offered, "desc": desc}
+
+
+def run_serving(args, ws, rank):
+    import torch
+    torch.cuda.set_device(0)
+    m = serving_measure(torch, args.lam, args.duration, args.requests, args.arena_gb,
+                        [float(x) for x in args.lam_sweep.split(",") if x], args.sweep_duration)
+    out = m["out"]
     line = {"metric": METRIC, "value": out["vm_steps_per_s"], "unit": UNIT, "n_gpus": 1, "steps": out["requests"],
             "warmup": 1, "ms_per_step": out["wall_s"] * 1e3 / max(out["requests"], 1), "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "int64", "data": "synthetic",
-            "config": {"workload": "serving: Poisson arrivals (lambda %.0f/s) for %.0f s of rollout requests, "
-                                   "each log-U[1e3,1e5] programs drawn as the uneven batch, inputs in pinned host "
-                                   "memory; %d distinct requests cycled; arena %.1f GiB" % (args.lam, args.duration, len(reqs), arena / 2 ** 30)},
+            "config": {"workload": m["desc"]},
             "serving": {"requests_done": out["requests"], "p50_ms": out["p50_ms"], "p99_ms": out["p99_ms"],
                         "wall_s": out["wall_s"], "vm_steps": out["vm_steps"], "mean_vms_per_request": out["mean_vms"],
-                        "offered_vms_per_s": offered, "request_gen_s": gen_s, "lambda_sweep": sweep,
-                        "sweep_duration_s": args.sweep_duration, "pool": pool_counters,
+                        "offered_vms_per_s": m["offered"], "request_gen_s": m["gen_s"], "lambda_sweep": m["sweep"],
+                        "sweep_duration_s": args.sweep_duration, "pool": m["pool"],
                         "design": "one persistent serving kernel over a device ring shared by all admitted requests"},
-            "clocks": clocks}
+            "clocks": m["clocks"]}
     print(json.dumps(line), flush=True)
 
 
@@ -421,6 +455,8 @@ def main():
     ap.add_argument("--sweep-duration", type=float, default=10.0, help="serving: seconds of arrivals per swept rate")
     ap.add_argument("--rounds", type=int, default=4, help="search: rounds")
     ap.add_argument("--tau-max", type=int, default=10 ** 5, help="search: step cap")
+    ap.add_argument("--no-serving", action="store_true",
+                    help="leave config 5 (60 s of serving) out of the other configurations")
     ap.add_argument("--no-other", action="store_true",
                     help="skip the other configurations (random, uneven, shared) after the headline")
     ap.add_argument("--out-arity", type=int, default=0,
@@ -465,7 +501,9 @@ def main():
         bs.run()
         stats = bs.stats()
     total_steps = stats["vm_steps"]
-    alg_bytes = algorithmic_bytes(stats)
+    kernel = run_kernel_name(tuned["chosen"] if tuned else SCHED_NAME.get(args.flags & 0xF0, "persist_gl"), args.flags)
+    # the shared-program kernel reads instruction pairs from shared memory
+    alg_bytes = algorithmic_bytes(stats, fetch_from_smem=kernel.startswith("k_shared"))
 
     # halting workload: the tau_h histogram is computed on the device in every step
     hist_edges = np.concatenate([np.arange(0, 101), [10 ** 6, 1 << 62]]).astype(np.uint64)
@@ -519,13 +557,19 @@ def main():
     hbm, peak_kind = peaks()
     run_avg = float(np.mean(run_ms))
     achieved = alg_bytes / (run_avg * 1e-3) / 1e9
-    # the summary was taken on the default shape (HBM-slab persistent, epoch 128, 4 warps)
+    # the summary was taken on the default launch shape (HBM-slab persistent,
+    # 4 warps x 7 CTAs per SM, epoch 128); a tuned shape that differs only in
+    # its epoch runs the same kernel at the same occupancy
+    chosen = tuned.get("chosen", "") if tuned else "persist_gl e128 w4"
     same_shape = args.workload == "templates" and args.flags == 0 and not args.epoch and \
-        (tuned is None or tuned.get("chosen") == "persist_gl e128 w4")
+        chosen.startswith("persist_gl e") and chosen.endswith(" w4")
     traffic = profiled_traffic(total_steps) if same_shape else None
     roofline = {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
                 "frac": achieved / hbm, "traffic": traffic,
-                "kernel": "k_persist_gl", "peak_kind": peak_kind,
+                "traffic_source": "profiles/traffic.json (ncu, 262,144-VM case, epoch 128, scaled by VM-steps)"
+                if traffic is not None else None,
+                "kernel": kernel, "peak_kind": peak_kind,
+                "fetch_from_smem_excluded": kernel.startswith("k_shared"),
                 "bytes_per_step": alg_bytes / max(total_steps, 1),
                 "kernel_ms": run_avg, "pack_ms": float(np.mean(pack_ms))}
 
@@ -624,7 +668,7 @@ def main():
     others = None
     if rank == 0 and ws == 1 and args.workload == "templates" and args.vms == 1 << 20 and args.flags == 0 \
             and not args.no_other:
-        others = other_configs(R, torch, args.steps, args.warmup)
+        others = other_configs(R, torch, args.steps, args.warmup, serving=not args.no_serving)
 
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,

@@ -378,3 +378,27 @@ def test_argument_errors(rasp):
         b.run()
         with pytest.raises(R.RaspError):
             b.read_state(first=5, count=10)
+
+
+def test_self_modifying_programs_across_kernel_switches(rasp):
+    """Self-modifying programs switched between the HBM-slab epoch loop and
+    the plain kernel midway (per-bucket plans pinned between runs), in both
+    orders, then reset and run again: every VM equal to the oracle's."""
+    R = rasp
+    wl = W.random_programs(num_vms=2048, seed=21)
+    st, _ = oracle_state(wl)
+    cuts = (40, 90, 160)
+    parts = [oracle_state(wl, budget=c)[0] for c in cuts]
+    for order in ((0x30, 0x10, 0x30, 0x10), (0x10, 0x30, 0x10, 0x30)):
+        with R.Batch(wl.mem_words, wl.ell, wl.s) as b:
+            b.load_workload(wl)
+            for rep in range(2):
+                for j, (c, part) in enumerate(zip(cuts, parts)):
+                    b.plan_bucket(b.describe()["buckets"][0]["index"], order[j])
+                    b.run(c)
+                    if j == 1:
+                        assert_same_state(b.read_state(), part, wl.ell, wl.s, what="order %s, %d steps" % (order, c))
+                b.plan_bucket(b.describe()["buckets"][0]["index"], order[3])
+                b.run()
+                assert_same_state(b.read_state(), st, wl.ell, wl.s, what="order %s, to the end" % (order,))
+                b.reset()

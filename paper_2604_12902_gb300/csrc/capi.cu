@@ -129,6 +129,7 @@ struct rasp_batch {
   uint32_t max_plen = 0;
   bool dirty_valid = false;    // codedirty is up to date (only the shared kernel tracks it)
   bool code_lazy = false;      // slabs of VMs with codedirty = 0 lack their program words (lazy pack)
+  bool narrow = false;         // M in 4-byte words (w <= 32)
   bool ids_uploaded = false;   // d_ids holds h_ids
   bool ids_base = true;        // h_ids is h_ids_base (bucket order, no cap-class sort)
   uint64_t max_cap = ~0ull;    // largest step cap of the batch (no VM runs further)
@@ -173,7 +174,15 @@ int validate_config(const rasp_config* cfg, uint64_t num_vms, const uint32_t* me
 // Blocks of the first top-k pass (each takes at least 1024 fresh candidates per tile).
 uint64_t topk_blocks(uint64_t V) { return std::min<uint64_t>(kMaxTopBlocks, (V + 1023) / 1024); }
 
-Layout make_layout(uint64_t V, uint64_t mem_words, uint32_t ellp, uint32_t sp) {
+// M in 4-byte words: w <= 32 on the schedules that read M through a narrow
+// view (plain and HBM-slab persistent; the shared-program and SMEM-staged
+// kernels keep 8-byte words, and so do the serving pool's batches).
+bool narrow_layout(const rasp_config* cfg, bool plan) {
+  const uint32_t sched = cfg->flags & RASP_SCHED_MASK;
+  return plan && cfg->word_bits <= 32 && sched != RASP_SCHED_SHARED && sched != RASP_SCHED_PERSIST;
+}
+
+Layout make_layout(uint64_t V, uint64_t mem_words, uint32_t ellp, uint32_t sp, uint32_t word_bytes) {
   Layout L{};
   size_t o = 0;
   auto take = [&](size_t bytes) {
@@ -190,7 +199,7 @@ Layout make_layout(uint64_t V, uint64_t mem_words, uint32_t ellp, uint32_t sp) {
   L.off_ylen = take(4 * V);
   L.off_n = take(4 * V);
   L.off_memoff = take(8 * V);
-  L.off_mem = take(8 * mem_words);
+  L.off_mem = take((uint64_t)word_bytes * mem_words);
   L.off_prog = take(8 * mem_words);           // programs never exceed the M arena
   L.off_progoff = take(8 * (V + 1));
   L.off_progvm = take(4 * V);
@@ -222,6 +231,7 @@ StepVariant variant_of(const rasp_batch* b) {
   v.vote = (b->cfg.flags & RASP_DISPATCH_VOTE) != 0;
   v.classic = (b->cfg.flags & RASP_ISA_CLASSIC) != 0;
   v.block = (b->cfg.flags & RASP_STEP_BLOCK) != 0;
+  v.narrow = b->narrow;
   return v;
 }
 
@@ -251,7 +261,7 @@ void plan_buckets(rasp_batch* b) {
     // default before autotuning: persistent workers over HBM-resident slabs
     // (measured fastest on the 256-word template workload)
     if (sched == RASP_SCHED_AUTO) sched = RASP_SCHED_PERSIST_GL;
-    if (sched == RASP_SCHED_PERSIST && staged_bytes > 220u * 1024u) sched = RASP_SCHED_PERSIST_GL;
+    if (sched == RASP_SCHED_PERSIST && (staged_bytes > 220u * 1024u || b->narrow)) sched = RASP_SCHED_PERSIST_GL;
     k.sched = sched;
     PersistShape& sh = k.shape;
     sh = PersistShape{};
@@ -409,7 +419,8 @@ int rasp_batch_bytes(const rasp_config* cfg, uint64_t num_vms, const uint32_t* m
   if (!out_bytes) return fail(RASP_EINVAL, "out_bytes is NULL");
   uint64_t mw = 0;
   for (uint64_t v = 0; v < num_vms; ++v) mw += even(mem_words[v]);
-  *out_bytes = make_layout(num_vms, mw, even(cfg->in_cap), even(cfg->out_cap)).total + ALIGN;
+  *out_bytes = make_layout(num_vms, mw, even(cfg->in_cap), even(cfg->out_cap), narrow_layout(cfg, true) ? 4u : 8u).total +
+               ALIGN;
   return RASP_OK;
 }
 
@@ -446,7 +457,8 @@ int rasp::create_batch(const rasp_config* cfg, uint64_t num_vms, const uint32_t*
     off += even(mem_words[v]);
   }
   b->mem_words = off;
-  b->L = make_layout(num_vms, off, b->ellp, b->sp);
+  b->narrow = narrow_layout(cfg, plan);
+  b->L = make_layout(num_vms, off, b->ellp, b->sp, b->narrow ? 4u : 8u);
   if (cfg->arena) {
     const uintptr_t p = (uintptr_t)cfg->arena;
     const uintptr_t aligned = (p + ALIGN - 1) & ~(uintptr_t)(ALIGN - 1);
@@ -486,6 +498,7 @@ int rasp::create_batch(const rasp_config* cfg, uint64_t num_vms, const uint32_t*
   S.n = (const uint32_t*)(B + L.off_n);
   S.mem_off = (const uint64_t*)(B + L.off_memoff);
   S.mem = (uint64_t*)(B + L.off_mem);
+  S.mem32 = b->narrow ? (uint32_t*)(B + L.off_mem) : nullptr;
   S.tape = (const uint64_t*)(B + L.off_tape);
   S.y = (uint64_t*)(B + L.off_y);
   b->d_prog = (uint64_t*)(B + L.off_prog);
@@ -874,6 +887,7 @@ int rasp_read_state(rasp_batch* b, uint64_t first, uint64_t count, rasp_state_vi
   if (out->uhead) CK(cudaMemcpyAsync(out->uhead, S.uhead + first, 4 * count, cudaMemcpyDeviceToHost, st));
   if (out->ylen) CK(cudaMemcpyAsync(out->ylen, S.ylen + first, 4 * count, cudaMemcpyDeviceToHost, st));
   std::vector<uint64_t> ybuf, mbuf;
+  std::vector<uint32_t> m32;
   if (out->y && b->s) {
     if (b->sp == b->s) {
       CK(cudaMemcpyAsync(out->y, S.y + first * b->sp, 8 * count * b->sp, cudaMemcpyDeviceToHost, st));
@@ -890,7 +904,10 @@ int rasp_read_state(rasp_batch* b, uint64_t first, uint64_t count, rasp_state_vi
                                            (unsigned long long)out->mem_words, (unsigned long long)need);
     const uint64_t lo = b->h_memoff[first];
     const uint64_t hi = b->h_memoff[first + count - 1] + even(b->h_n[first + count - 1]);
-    if (need == hi - lo) {
+    if (b->narrow) {                         // 4-byte words, widened below
+      m32.resize(hi - lo);
+      CK(cudaMemcpyAsync(m32.data(), S.mem32 + lo, 4 * (hi - lo), cudaMemcpyDeviceToHost, st));
+    } else if (need == hi - lo) {
       CK(cudaMemcpyAsync(out->mem, S.mem + lo, 8 * need, cudaMemcpyDeviceToHost, st));
     } else {
       mbuf.resize(hi - lo);
@@ -906,6 +923,15 @@ int rasp_read_state(rasp_batch* b, uint64_t first, uint64_t count, rasp_state_vi
     uint64_t o = 0;
     for (uint64_t v = first; v < first + count; ++v) {
       memcpy(out->mem + o, mbuf.data() + (b->h_memoff[v] - lo), 8ull * b->h_n[v]);
+      o += b->h_n[v];
+    }
+  }
+  if (!m32.empty()) {
+    const uint64_t lo = b->h_memoff[first];
+    uint64_t o = 0;
+    for (uint64_t v = first; v < first + count; ++v) {
+      const uint32_t* src = m32.data() + (b->h_memoff[v] - lo);
+      for (uint32_t k = 0; k < b->h_n[v]; ++k) out->mem[o + k] = (int64_t)src[k];
       o += b->h_n[v];
     }
   }
@@ -942,16 +968,23 @@ int rasp_load_state(rasp_batch* b, uint64_t first, uint64_t count, const rasp_st
       for (uint32_t k = 0; k < b->s; ++k) ybuf[v * b->sp + k] = (uint64_t)in->y[v * b->s + k] & b->wmask;
     CK(cudaMemcpyAsync(S.y + first * b->sp, ybuf.data(), 8 * ybuf.size(), cudaMemcpyHostToDevice, st));
   }
+  std::vector<uint32_t> m32;
   if (in->mem) {
     const uint64_t lo = b->h_memoff[first];
     const uint64_t hi = b->h_memoff[first + count - 1] + even(b->h_n[first + count - 1]);
-    mbuf.assign(hi - lo, 0);
+    if (b->narrow) m32.assign(hi - lo, 0);
+    else mbuf.assign(hi - lo, 0);
     uint64_t o = 0;
     for (uint64_t v = first; v < first + count; ++v) {
-      for (uint32_t k = 0; k < b->h_n[v]; ++k) mbuf[b->h_memoff[v] - lo + k] = (uint64_t)in->mem[o + k] & b->wmask;
+      for (uint32_t k = 0; k < b->h_n[v]; ++k) {
+        const uint64_t w = (uint64_t)in->mem[o + k] & b->wmask;
+        if (b->narrow) m32[b->h_memoff[v] - lo + k] = (uint32_t)w;
+        else mbuf[b->h_memoff[v] - lo + k] = w;
+      }
       o += b->h_n[v];
     }
-    CK(cudaMemcpyAsync(S.mem + lo, mbuf.data(), 8 * mbuf.size(), cudaMemcpyHostToDevice, st));
+    if (b->narrow) CK(cudaMemcpyAsync(S.mem32 + lo, m32.data(), 4 * m32.size(), cudaMemcpyHostToDevice, st));
+    else CK(cudaMemcpyAsync(S.mem + lo, mbuf.data(), 8 * mbuf.size(), cudaMemcpyHostToDevice, st));
     CK(cudaMemsetAsync(b->S.codedirty + first, 1, count, st));   // restored M may differ from the program
   }
   CK(cudaStreamSynchronize(st));
@@ -1088,7 +1121,7 @@ int rasp_autotune(rasp_batch* b, uint64_t max_steps, uint32_t reps) {
   // the shared-program schedule is a candidate only when programs are shared;
   // the classic opcode set runs on the HBM-slab persistent and plain schedules only
   const bool classic = (b->cfg.flags & RASP_ISA_CLASSIC) != 0;
-  const int ncand = classic ? 7 : (int)(sizeof(cands) / sizeof(cands[0])) - (b->shared_programs ? 0 : 1);
+  const int ncand = classic ? 7 : (int)(sizeof(cands) / sizeof(cands[0])) - (b->shared_programs && !b->narrow ? 0 : 1);
   const rasp_config saved = b->cfg;
   b->over.clear();                         // the global pass tunes the batch-wide settings
   cudaEvent_t e0, e1;
@@ -1263,7 +1296,9 @@ int rasp_describe(const rasp_batch* b, char* buf, uint64_t size) {
     s += tmp;
     first = false;
   }
-  s += "], \"cuda_graph\": ";
+  s += "], \"word_bytes\": ";
+  s += b->narrow ? "4" : "8";
+  s += ", \"cuda_graph\": ";
   s += b->cap_stream ? "true" : "false";
   s += ", \"autotune\": ";
   s += b->tuned.empty() ? "null" : b->tuned;

@@ -36,7 +36,8 @@ struct DevState {
   uint32_t* ylen;             // y_0
   const uint32_t* n;          // memory words
   const uint64_t* mem_off;    // word offset of the VM's M slab (even)
-  uint64_t* mem;              // M slabs
+  uint64_t* mem;              // M slabs (8-byte words)
+  uint32_t* mem32;            // M slabs of a narrow batch (w <= 32: 4-byte words; NULL otherwise)
   const uint64_t* tape;       // u_1..u_l, stride ellp words per VM
   uint64_t* y;                // y_1..y_s, stride sp words per VM
   uint8_t* codedirty;         // 1 if the VM may have written into its program words (NULL: untracked)
@@ -211,6 +212,19 @@ __device__ __forceinline__ void mem_wr(const ShView& V, bool& clean, uint32_t k,
   }
   V.M[k] = v;
 }
+
+// The view of a VM of a narrow batch (w <= 32): M holds 4-byte words, the
+// same values as 8-byte words would (every word is below 2^w). Pairs are
+// 8-byte aligned (k even, slabs start at an even word).
+struct NarrowView {
+  uint32_t* M;
+};
+__device__ __forceinline__ ulonglong2 mem_pair(const NarrowView& V, bool, uint32_t k) {
+  const uint2 p = *reinterpret_cast<const uint2*>(V.M + k);
+  return make_ulonglong2(p.x, p.y);
+}
+__device__ __forceinline__ uint64_t mem_rd(const NarrowView& V, bool, uint32_t k) { return V.M[k]; }
+__device__ __forceinline__ void mem_wr(const NarrowView& V, bool&, uint32_t k, uint64_t v) { V.M[k] = (uint32_t)v; }
 
 // <o, j> = <M[i mod n], M[(i (+) 1) mod n]> when the pair is not one aligned
 // 16-byte word (odd n or odd i mod n, or i = 2^w - 1 where i (+) 1 wraps to 0).
@@ -693,11 +707,117 @@ __device__ __forceinline__ uint32_t fast_loop_ptx_sh(uint64_t* M, const uint64_t
   return rare;
 }
 
+// The epoch loop of a narrow batch (w <= 32, M in 4-byte words): the same
+// steps as fast_loop_ptx with 32-bit words and 32-bit arithmetic (every word
+// and a are below 2^w <= 2^32, so a word's high half is never looked at and
+// the sum and product are taken mod 2^32, then reduced to w bits when
+// w < 32). Tape words and outputs stay 8-byte words whose high halves are
+// zero: RD reads a tape word's low half, PRI writes an output's low half.
+// a, co and cj are 32-bit here; the caller widens them.
+#define RASP_NLOOP_A \
+      "{\n\t" \
+      ".reg .pred px, pq, po, pz, pt, pe, ph, pop, p4, p6, pad, p1, p2, p3, pw, pp, pany;\n\t" \
+      ".reg .b32 m, t0, t1, nip, v, tv, am, jl, ol;\n\t" \
+      ".reg .b64 ado, adn, adt, ady;\n\t" \
+      "setp.ne.u32 ph, %6, 0;\n\t" \
+      "RASP_NLOOP:\n\t" \
+      "mov.b32 ol, %1;\n\t" \
+      "mov.b32 jl, %2;\n\t" \
+      "setp.eq.or.u32 px, %7, 0, !ph;\n\t" \
+      "add.u32 t0, ol, -1;\n\t" \
+      "setp.ge.or.u32 px, t0, 7, px;\n\t" \
+      "shl.b32 m, 1, ol;\n\t"
+#define RASP_NLOOP_PZ_WORD "setp.ne.u32 pz, %0, 0;\n\t"
+#define RASP_NLOOP_PZ_CLASSIC "add.u32 am, %0, -1;\n\tsetp.lt.u32 pz, am, %17;\n\t"
+#define RASP_NLOOP_B \
+      "setp.eq.and.u32 pt, ol, 5, pz;\n\t" \
+      "setp.ge.u32 po, jl, %12;\n\t" \
+      "and.b32 t0, m, 0xDC;\n\t" \
+      "setp.ne.or.u32 pad, t0, 0, pt;\n\t" \
+      "and.pred pq, po, pad;\n\t" \
+      "or.pred px, px, pq;\n\t" \
+      "setp.eq.u32 p6, ol, 6;\n\t" \
+      "setp.ge.and.u32 pq, %4, %14, p6;\n\t" \
+      "or.pred px, px, pq;\n\t" \
+      "setp.eq.and.u32 pq, jl, %3, pt;\n\t" \
+      "or.pred px, px, pq;\n\t" \
+      "vote.sync.any.pred pany, px, %16;\n\t" \
+      "@pany bra.uni RASP_NDONE;\n\t" \
+      "add.u32 nip, %3, 2;\n\t" \
+      "selp.b32 %3, jl, nip, pt;\n\t" \
+      "shf.l.wrap.b32 t1, %3, %3, 31;\n\t" \
+      "setp.lt.u32 pe, t1, %13;\n\t" \
+      "mad.wide.u32 adn, %3, 4, %9;\n\t" \
+      "mad.wide.u32 ado, jl, 4, %9;\n\t" \
+      "xor.b32 t1, jl, %3;\n\t" \
+      "setp.eq.u32 p1, ol, 1;\n\t" \
+      "@p1 mov.b32 %0, jl;\n\t" \
+      "@pe ld.global.v2.u32 {%1, %2}, [adn];\n\t" \
+      "and.b32 t0, m, 0x8C;\n\t" \
+      "setp.ne.u32 pop, t0, 0;\n\t" \
+      "@pop ld.global.u32 v, [ado];\n\t" \
+      "mad.wide.u32 adt, %4, 8, %10;\n\t" \
+      "@p6 ld.global.u32 tv, [adt];\n\t" \
+      "setp.eq.u32 p4, ol, 4;\n\t" \
+      "@p4 st.global.u32 [ado], %0;\n\t" \
+      "@p6 st.global.u32 [ado], tv;\n\t" \
+      "or.pred pw, p4, p6;\n\t" \
+      "setp.eq.u32 p2, ol, 2;\n\t" \
+      "setp.eq.u32 p3, ol, 3;\n\t" \
+      "@p2 add.u32 %0, %0, v;\n\t"
+#define RASP_NLOOP_PD_WORD "@p3 mul.lo.u32 %0, %0, v;\n\t"
+#define RASP_NLOOP_PD_CLASSIC "@p3 sub.u32 %0, %0, v;\n\t"
+#define RASP_NLOOP_D \
+      "setp.lt.u32 pp, %5, %15;\n\t" \
+      "setp.eq.and.u32 pp, ol, 7, pp;\n\t" \
+      "mad.wide.u32 ady, %5, 8, %11;\n\t" \
+      "@pp st.global.u32 [ady], v;\n\t" \
+      "@pp add.u32 %5, %5, 1;\n\t" \
+      "@p6 add.u32 %4, %4, 1;\n\t" \
+      "setp.ge.or.u32 pq, t1, 2, !pw;\n\t" \
+      "and.pred ph, pe, pq;\n\t" \
+      "add.u32 %7, %7, -1;\n\t" \
+      "bra.uni RASP_NLOOP;\n\t" \
+      "RASP_NDONE:\n\t" \
+      "setp.ne.and.u32 px, %7, 0, px;\n\t" \
+      "selp.u32 %8, 1, 0, px;\n\t" \
+      "selp.u32 %6, 1, 0, ph;\n\t" \
+      "}"
+#define RASP_NLOOP_OPERANDS                                                                                \
+  : "+r"(a), "+r"(co), "+r"(cj), "+r"(ip), "+r"(u0), "+r"(y0), "+r"(have), "+r"(kk), "=r"(rare)             \
+  : "l"(M), "l"(T), "l"(Y), "r"(n), "r"(ilim >> 1), "r"(ell), "r"(s), "r"(mask), "r"(wmask >> 1),           \
+    "r"(wmask)                                                                                               \
+  : "memory"
+
+// MASK: w < 32 (the new accumulator is reduced to w bits, %18 = 2^w - 1).
+template <bool MASK, bool CLASSIC>
+__device__ __forceinline__ uint32_t fast_loop_ptx_narrow(uint32_t* M, const uint64_t* T, uint64_t* Y, uint32_t n,
+                                                         uint32_t ell, uint32_t s, uint32_t ilim, uint32_t wmask,
+                                                         uint32_t mask, uint32_t& a, uint32_t& co, uint32_t& cj,
+                                                         uint32_t& ip, uint32_t& u0, uint32_t& y0, uint32_t& have,
+                                                         uint32_t& kk) {
+  uint32_t rare;
+  if constexpr (MASK && CLASSIC) {
+    asm volatile(RASP_NLOOP_A RASP_NLOOP_PZ_CLASSIC RASP_NLOOP_B RASP_NLOOP_PD_CLASSIC
+                 "and.b32 %0, %0, %18;\n\t" RASP_NLOOP_D RASP_NLOOP_OPERANDS);
+  } else if constexpr (MASK) {
+    asm volatile(RASP_NLOOP_A RASP_NLOOP_PZ_WORD RASP_NLOOP_B RASP_NLOOP_PD_WORD
+                 "and.b32 %0, %0, %18;\n\t" RASP_NLOOP_D RASP_NLOOP_OPERANDS);
+  } else if constexpr (CLASSIC) {
+    asm volatile(RASP_NLOOP_A RASP_NLOOP_PZ_CLASSIC RASP_NLOOP_B RASP_NLOOP_PD_CLASSIC RASP_NLOOP_D
+                 RASP_NLOOP_OPERANDS);
+  } else {
+    asm volatile(RASP_NLOOP_A RASP_NLOOP_PZ_WORD RASP_NLOOP_B RASP_NLOOP_PD_WORD RASP_NLOOP_D
+                 RASP_NLOOP_OPERANDS);
+  }
+  return rare;
+}
+
 template <bool MASKED, bool CHECKED, bool HIST, bool PIPE, bool CLASSIC = false, class Mem>
 __device__ __forceinline__ uint32_t one_step(Mem M, const uint64_t* __restrict__ T, uint64_t* __restrict__ Y,
                                              const Params& P, Regs& r, Hist& h) {
   const uint32_t ip = r.ip, n = r.n;
-  if constexpr (PIPE && !CHECKED && !HIST && !std::is_same<Mem, ShView>::value) {
+  if constexpr (PIPE && !CHECKED && !HIST && std::is_pointer<Mem>::value) {
     if (r.have) {
       uint64_t co = r.cur.x, cj = r.cur.y;
       uint32_t hv = 1;

@@ -20,6 +20,7 @@ struct StepVariant {
   bool classic;  // classic opcode set (Sec. 1.1: SUB, BPA); plain and HBM-slab persistent, select only
   bool block;    // HBM-slab persistent: one predicated block per step instead of the epoch loop;
                  // shared-program schedule: one step at a time per lane instead of the epoch loop
+  bool narrow;   // M in 4-byte words (w <= 32): plain and HBM-slab persistent schedules
 };
 
 // Persistent-kernel launch shape for one bucket of VMs.

@@ -44,9 +44,25 @@ __global__ void __launch_bounds__(256) k_pack(DevState S, const uint64_t* __rest
     const uint64_t po = prog_off[p];
     const uint64_t plen = prog_off[p + 1] - po;
     const uint64_t* src = prog + po;                   // po is even: 16-byte aligned
-    uint64_t* dst = S.mem + S.mem_off[v];
     const uint32_t npad = (S.n[v] + 1u) & ~1u;
-    for (uint32_t k = (lazy ? (uint32_t)plen : 0u) + 2u * lane; k < npad; k += 64u) {
+    if (S.mem32) {
+      // narrow batch (w <= 32): 4-byte words, two per 8-byte store
+      uint32_t* dst = S.mem32 + S.mem_off[v];
+      for (uint32_t k = 2u * lane; k < npad; k += 64u) {
+        uint2 w;
+        if (k + 1u < plen) {
+          const ulonglong2 q = *reinterpret_cast<const ulonglong2*>(src + k);
+          w.x = (uint32_t)(q.x & wmask);
+          w.y = (uint32_t)(q.y & wmask);
+        } else {
+          w.x = (k < plen) ? (uint32_t)(src[k] & wmask) : 0u;
+          w.y = 0u;
+        }
+        *reinterpret_cast<uint2*>(dst + k) = w;
+      }
+    }
+    uint64_t* dst = S.mem + S.mem_off[v];
+    for (uint32_t k = (lazy ? (uint32_t)plen : 0u) + 2u * lane; !S.mem32 && k < npad; k += 64u) {
       ulonglong2 w;
       if (k + 1u < plen) {
         w = *reinterpret_cast<const ulonglong2*>(src + k);
@@ -77,10 +93,9 @@ __global__ void __launch_bounds__(256) k_pack(DevState S, const uint64_t* __rest
 // take part. Lanes are grouped by opcode with __match_any_sync and each group
 // runs the handler of its case of the Sec. 2.1 equation. Returns CONT or a
 // final status like one_step.
-template <bool MASKED, bool CHECKED, bool HIST>
-__device__ __forceinline__ uint32_t vote_step(uint64_t* __restrict__ M, const uint64_t* __restrict__ T,
-                                              uint64_t* __restrict__ Y, const Params& P, Regs& r, Hist& h,
-                                              bool active) {
+template <bool MASKED, bool CHECKED, bool HIST, class Mem>
+__device__ __forceinline__ uint32_t vote_step(Mem M, const uint64_t* __restrict__ T, uint64_t* __restrict__ Y,
+                                              const Params& P, Regs& r, Hist& h, bool active) {
   Decoded d;
   d.j = 0;
   d.op = 0;
@@ -105,30 +120,30 @@ __device__ __forceinline__ uint32_t vote_step(uint64_t* __restrict__ M, const ui
           r.a = d.j & wm;
           break;
         case 2u: {     // ADD
-          const uint64_t v = M[d.jm];
+          const uint64_t v = mem_rd(M, r.clean, d.jm);
           const uint64_t s = a + v;
           if (CHECKED && (int64_t)((a ^ s) & (v ^ s)) < 0) result = ST_FAULT_OVERFLOW;
           else r.a = s & wm;
           break;
         }
         case 3u: {     // MUL
-          const uint64_t v = M[d.jm];
+          const uint64_t v = mem_rd(M, r.clean, d.jm);
           const uint64_t p = a * v;
           if (CHECKED && __mul64hi((long long)a, (long long)v) != ((int64_t)p >> 63)) result = ST_FAULT_OVERFLOW;
           else r.a = p & wm;
           break;
         }
         case 4u:       // STO
-          M[d.jm] = a;
+          mem_wr(M, r.clean, d.jm, a);
           break;
         case 5u:       // BNZ: the jump itself is taken in advance()
           break;
         case 6u:       // RD
-          M[d.jm] = T[r.u0];
+          mem_wr(M, r.clean, d.jm, T[r.u0]);
           r.u0 += 1u;
           break;
         default: {     // PRI
-          const uint64_t v = M[d.jm];
+          const uint64_t v = mem_rd(M, r.clean, d.jm);
           if (r.y0 < P.s) {
             Y[r.y0] = v;
             r.y0 += 1u;
@@ -149,7 +164,12 @@ __device__ __forceinline__ uint32_t vote_step(uint64_t* __restrict__ M, const ui
 }
 
 // ------------------------------------------------------------------ plain
-template <bool MASKED, bool CHECKED, bool HIST, bool VOTE, bool CLASSIC = false>
+// The memory view of VM v at word offset moff: its slab of 8-byte words, or
+// of 4-byte words in a narrow batch.
+__device__ __forceinline__ void attach_mem(uint64_t*& M, const DevState& S, uint64_t moff) { M = S.mem + moff; }
+__device__ __forceinline__ void attach_mem(NarrowView& M, const DevState& S, uint64_t moff) { M.M = S.mem32 + moff; }
+
+template <bool MASKED, bool CHECKED, bool HIST, bool VOTE, bool CLASSIC = false, bool NARROW = false>
 __global__ void __launch_bounds__(256) k_plain(DevState S, Params P, const uint32_t* __restrict__ ids,
                                                uint32_t count) {
   const uint32_t t = blockIdx.x * blockDim.x + threadIdx.x;
@@ -158,7 +178,7 @@ __global__ void __launch_bounds__(256) k_plain(DevState S, Params P, const uint3
   bool active = false;
   uint32_t v = 0;
   Regs r{};
-  uint64_t* M = nullptr;
+  std::conditional_t<NARROW, NarrowView, uint64_t*> M{};
   const uint64_t* T = nullptr;
   uint64_t* Y = nullptr;
   if (t < count) {
@@ -166,7 +186,7 @@ __global__ void __launch_bounds__(256) k_plain(DevState S, Params P, const uint3
     if (S.status[v] == ST_RUNNING) {
       load_regs(S, P, v, r);
       arm_regs(P, r);
-      M = S.mem + S.mem_off[v];
+      attach_mem(M, S, S.mem_off[v]);
       T = S.tape + (uint64_t)v * P.ellp;
       Y = S.y + (uint64_t)v * P.sp;
       active = true;
@@ -193,8 +213,8 @@ __global__ void __launch_bounds__(256) k_plain(DevState S, Params P, const uint3
 }
 
 // Run `epoch` steps of every active lane (warp-uniform loop).
-template <bool MASKED, bool CHECKED, bool HIST, bool VOTE, bool PIPE, bool CLASSIC = false>
-__device__ __forceinline__ void run_epoch(uint64_t* M, const uint64_t* T, uint64_t* Y, const Params& P, Regs& r,
+template <bool MASKED, bool CHECKED, bool HIST, bool VOTE, bool PIPE, bool CLASSIC = false, class Mem>
+__device__ __forceinline__ void run_epoch(Mem M, const uint64_t* T, uint64_t* Y, const Params& P, Regs& r,
                                           Hist& h, bool& active, uint32_t& final_st, uint32_t epoch) {
   if (VOTE) {
     for (uint32_t t = 0; t < epoch; ++t) {
@@ -249,6 +269,19 @@ __device__ __forceinline__ void run_epoch_loop(Mem M, const uint64_t* T, uint64_
           rare = fast_loop_ptx_sh<MASKED>(M.M, cl ? M.Pg : M.M, cl ? M.plen : 0u, T, Y, r.n, P.ell, P.s,
                                           cl ? min(M.plen, r.ilim) : r.ilim, P.wmask, mask, r.a, co, cj, r.ip,
                                           r.u0, r.y0, hv, kk);
+        } else if constexpr (std::is_same<Mem, NarrowView>::value) {
+          // 4-byte words: the loop runs on 32-bit values (w <= 32)
+          uint32_t a32 = (uint32_t)r.a, co32 = (uint32_t)co, cj32 = (uint32_t)cj;
+          const uint32_t wm32 = (uint32_t)P.wmask;
+          if (wm32 == 0xFFFFFFFFu)
+            rare = fast_loop_ptx_narrow<false, CLASSIC>(M.M, T, Y, r.n, P.ell, P.s, r.ilim, wm32, mask, a32, co32,
+                                                        cj32, r.ip, r.u0, r.y0, hv, kk);
+          else
+            rare = fast_loop_ptx_narrow<true, CLASSIC>(M.M, T, Y, r.n, P.ell, P.s, r.ilim, wm32, mask, a32, co32,
+                                                       cj32, r.ip, r.u0, r.y0, hv, kk);
+          r.a = a32;
+          co = co32;
+          cj = cj32;
         } else {
           rare = fast_loop_ptx<MASKED, CLASSIC>(M, T, Y, r.n, P.ell, P.s, r.ilim, P.wmask, mask, r.a, co, cj, r.ip,
                                                 r.u0, r.y0, hv, kk);
@@ -405,7 +438,8 @@ __global__ void __launch_bounds__(256) k_persist(DevState S, Params P, Queue Q, 
 // end no VM waits in a busy lane's prefetch slot while other lanes idle.
 enum : uint32_t { PF_EMPTY = 0, PF_ID = 1, PF_REGS = 2, PF_NONE = 3 };   // PF_REGS: entries warmed in L2
 
-template <bool MASKED, bool CHECKED, bool HIST, bool VOTE, bool CLASSIC = false, bool LOOP = false>
+template <bool MASKED, bool CHECKED, bool HIST, bool VOTE, bool CLASSIC = false, bool LOOP = false,
+          bool NARROW = false>
 __global__ void __launch_bounds__(128, 7) k_persist_gl(DevState S, Params P, Queue Q, uint32_t epoch,
                                                        uint32_t idle_exit) {
   static_assert(!LOOP || (!CHECKED && !HIST && !VOTE), "the epoch loop serves WRAP select steps without counters");
@@ -441,7 +475,8 @@ __global__ void __launch_bounds__(128, 7) k_persist_gl(DevState S, Params P, Que
   int32_t vm = -1;
   bool active = false;
   uint32_t final_st = ST_RUNNING;
-  uint64_t* M = S.mem;
+  std::conditional_t<NARROW, NarrowView, uint64_t*> M{};
+  attach_mem(M, S, 0ull);
   const uint64_t* T = S.tape;
   uint64_t* Y = S.y;
   // prefetched VM
@@ -460,7 +495,7 @@ __global__ void __launch_bounds__(128, 7) k_persist_gl(DevState S, Params P, Que
         const uint64_t moff = S.mem_off[pf_vm];
         arm_regs(P, r);
         vm = (int32_t)pf_vm;
-        M = S.mem + moff;
+        attach_mem(M, S, moff);
         T = S.tape + (uint64_t)pf_vm * P.ellp;
         Y = S.y + (uint64_t)pf_vm * P.sp;
         if (!VOTE) prime(M, r);
@@ -540,7 +575,7 @@ __global__ void __launch_bounds__(128, 7) k_persist_gl(DevState S, Params P, Que
         const uint64_t moff = S.mem_off[pf_vm];
         arm_regs(P, r);
         vm = (int32_t)pf_vm;
-        M = S.mem + moff;
+        attach_mem(M, S, moff);
         T = S.tape + (uint64_t)pf_vm * P.ellp;
         Y = S.y + (uint64_t)pf_vm * P.sp;
         if (!VOTE) prime(M, r);
@@ -1079,6 +1114,7 @@ PlainFn plain_fn(bool vote) {
 // The classic opcode set (Sec. 1.1) is built for the select dispatch only.
 template <bool CL>
 PlainFn plain_select(const StepVariant& v) {
+  if (v.narrow) return v.hist ? k_plain<true, false, true, false, CL, true> : k_plain<true, false, false, false, CL, true>;
   if (v.checked) return v.hist ? k_plain<false, true, true, false, CL> : k_plain<false, true, false, false, CL>;
   if (v.masked) return v.hist ? k_plain<true, false, true, false, CL> : k_plain<true, false, false, false, CL>;
   return v.hist ? k_plain<false, false, true, false, CL> : k_plain<false, false, false, false, CL>;
@@ -1086,6 +1122,11 @@ PlainFn plain_select(const StepVariant& v) {
 
 template <bool CL>
 GlobalFn global_select(const StepVariant& v) {
+  if (v.narrow) {
+    if (v.hist) return k_persist_gl<true, false, true, false, CL, false, true>;
+    if (v.block) return k_persist_gl<true, false, false, false, CL, false, true>;
+    return k_persist_gl<true, false, false, false, CL, true, true>;
+  }
   if (v.checked)
     return v.hist ? k_persist_gl<false, true, true, false, CL> : k_persist_gl<false, true, false, false, CL>;
   if (v.masked)
@@ -1097,6 +1138,8 @@ GlobalFn global_select(const StepVariant& v) {
 
 PlainFn pick_plain(const StepVariant& v) {
   if (v.classic) return plain_select<true>(v);
+  if (v.narrow && v.vote) return v.hist ? k_plain<true, false, true, true, false, true> : k_plain<true, false, false, true, false, true>;
+  if (v.narrow) return plain_select<false>(v);
   if (v.checked) return v.hist ? plain_fn<false, true, true>(v.vote) : plain_fn<false, true, false>(v.vote);
   if (v.masked) return v.hist ? plain_fn<true, false, true>(v.vote) : plain_fn<true, false, false>(v.vote);
   return v.hist ? plain_fn<false, false, true>(v.vote) : plain_fn<false, false, false>(v.vote);
@@ -1120,6 +1163,8 @@ GlobalFn global_fn(bool vote) {
 
 GlobalFn pick_global(const StepVariant& v) {
   if (v.classic) return global_select<true>(v);
+  if (v.narrow && v.vote)
+    return v.hist ? k_persist_gl<true, false, true, true, false, false, true> : k_persist_gl<true, false, false, true, false, false, true>;
   if (!v.vote) return global_select<false>(v);
   if (v.checked) return v.hist ? global_fn<false, true, true>(v.vote) : global_fn<false, true, false>(v.vote);
   if (v.masked) return v.hist ? global_fn<true, false, true>(v.vote) : global_fn<true, false, false>(v.vote);

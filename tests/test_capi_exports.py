@@ -39,3 +39,17 @@ def test_batch_bytes_validates_without_gpu():
         assert e.code == rasp.RASP_EINVAL
     assert "version" not in rasp.rasp_last_error()
     assert rasp.rasp_version().startswith("rasp_gb300")
+
+
+def test_narrow_batches_take_half_the_memory_words():
+    """w <= 32 holds M in 4-byte words (plain and HBM-slab schedules); the
+    shared-program and SMEM-staged schedules keep 8-byte words."""
+    from paper_2604_12902_gb300 import rasp
+    import numpy as np
+    n = np.full(4096, 256, np.uint32)
+    size = lambda w, flags: rasp.rasp_batch_bytes(rasp.rasp_config(w, 0, 4, 8, flags, 0, 0, 0, 0, 0, None, None, 0), n)
+    m_words = 4096 * 256
+    assert size(64, 0) - size(32, 0) >= 4 * m_words - 4096
+    assert size(32, 0x10) == size(32, 0)
+    assert size(32, 0x40) == size(64, 0x40) == size(64, 0)
+    assert size(32, 0x20) == size(64, 0)

@@ -402,3 +402,31 @@ def test_self_modifying_programs_across_kernel_switches(rasp):
                 b.run()
                 assert_same_state(b.read_state(), st, wl.ell, wl.s, what="order %s, to the end" % (order,))
                 b.reset()
+
+
+@pytest.mark.parametrize("w", [32, 20, 5])
+def test_narrow_words_checkpoint_and_schedules(rasp, w):
+    """w <= 32: M is held in 4-byte words on the plain and HBM-slab
+    schedules (8-byte words on the shared-program and SMEM-staged ones).
+    Self-modifying programs on every schedule, a checkpoint read midway
+    (M widened to int64), restored into a fresh batch and run on: every VM
+    equal to the oracle's."""
+    R = rasp
+    wl = W.random_programs(num_vms=1500, seed=23)
+    wl.w = w
+    st, _ = oracle_state(wl)
+    part, _ = oracle_state(wl, budget=50)
+    for flags, bytes_ in ((0x00, 4), (0x10, 4), (0x30, 4), (0x20, 8), (0x30 | 0x100, 4), (0x30 | 0x20000, 4)):
+        with R.Batch(wl.mem_words, wl.ell, wl.s, word_bits=w, flags=flags) as b:
+            assert b.describe()["word_bytes"] == bytes_
+            b.load_workload(wl)
+            b.run(50)
+            ck = b.read_state()
+            assert_same_state(ck, part, wl.ell, wl.s, what="w %d flags %#x at 50 steps" % (w, flags))
+            b.run()
+            assert_same_state(b.read_state(), st, wl.ell, wl.s, what="w %d flags %#x" % (w, flags))
+        with R.Batch(wl.mem_words, wl.ell, wl.s, word_bits=w, flags=flags) as b2:
+            b2.load_workload(wl)
+            b2.load_state(ck)
+            b2.run()
+            assert_same_state(b2.read_state(), st, wl.ell, wl.s, what="w %d flags %#x restored" % (w, flags))

@@ -179,16 +179,18 @@ def outcomes(stats) -> dict:
     return out
 
 
-def algorithmic_bytes(stats, fetch_from_smem: bool = False) -> float:
+def algorithmic_bytes(stats, fetch_from_smem: bool = False, word_bytes: int = 8) -> float:
     """Opcode-weighted bytes of VM state touched by the executed steps; with
     fetch_from_smem the 16-byte instruction fetch is left out (the
-    shared-program kernel reads the program words from shared memory)."""
+    shared-program kernel reads the program words from shared memory). The
+    table is in 8-byte words; a batch held in 4-byte words (w <= 32) touches
+    half as many bytes per access."""
     ops = stats["op_steps"]
     b = sum(BYTES_PER_OP[k] * ops[k] for k in range(1, 8))
     b -= (BYTES_PER_OP[7] - PRI_FULL_BYTES) * stats["pri_full"]
     if fetch_from_smem:
         b -= 16 * sum(ops[k] for k in range(1, 8))
-    return float(b)
+    return float(b) * word_bytes / 8.0
 
 
 KERNEL_OF = {"persist_gl": "k_persist_gl", "plain": "k_plain", "persist_smem": "k_persist", "shared": "k_shared_loop"}
@@ -219,7 +221,8 @@ def time_config(R, torch, wl, desc, flags, steps, warmup, flush_l2=False):
             stats = bs.stats()
         chosen = tuned["chosen"] if tuned else "flags %#x" % flags
         kernel = run_kernel_name(chosen if tuned else SCHED_NAME.get(flags & 0xF0, "persist_gl"), flags)
-        alg = algorithmic_bytes(stats, fetch_from_smem=kernel.startswith("k_shared"))
+        word_bytes = b.describe().get("word_bytes", 8)
+        alg = algorithmic_bytes(stats, fetch_from_smem=kernel.startswith("k_shared"), word_bytes=word_bytes)
         for _ in range(warmup):
             b.reset()
             b.run()
@@ -254,7 +257,7 @@ def time_config(R, torch, wl, desc, flags, steps, warmup, flush_l2=False):
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
                          "traffic": None, "kernel": kernel, "peak_kind": peak_kind,
                          "bytes_per_step": alg / max(stats["vm_steps"], 1),
-                         "fetch_from_smem_excluded": kernel.startswith("k_shared"),
+                         "fetch_from_smem_excluded": kernel.startswith("k_shared"), "word_bytes": word_bytes,
                          "kernel_ms": run_avg, "pack_ms": float(np.mean(pack_ms))},
             "outcomes": outcomes(st)}
 
@@ -263,20 +266,24 @@ def other_configs(R, torch, steps, warmup, serving=True):
     """The benchmark's other single-GPU configurations, each timed like the
     headline after it: 1,024 random programs (config 1), the uneven batch of
     4,194,304 programs in its CUDA-graph form (config 3), the shared-program
-    rollout of 16,384 programs x 256 tapes (config 4), and serving at 200
+    rollout of 16,384 programs x 256 tapes (config 4), the halting workload of
+    Sec. 3 (2^20 sampled programs, w = 32, tau_max = 10^6), and serving at 200
     requests/s for 60 s (config 5: p50/p99 latency and VM-steps/s)."""
     out = {}
-    for name in ("random", "shared", "uneven"):
+    for name in ("random", "shared", "uneven", "halting"):
         t0 = time.perf_counter()
         wl, desc = make_workload(name, 0)
         gen_s = time.perf_counter() - t0
-        flags = R.CUDA_GRAPH if name == "uneven" else 0
+        # the halting workload (Sec. 3, w = 32) runs on the HBM-slab schedule
+        # without autotuning (one plain-form trial alone takes 2.8 s)
+        flags = R.CUDA_GRAPH if name == "uneven" else (R.SCHED_PERSIST_GL if name == "halting" else 0)
         clk = ClockSampler(torch.cuda.current_device())
         clk.start()
         rec = time_config(R, torch, wl, desc, flags, steps, warmup, flush_l2=name == "random")
         rec["clocks"] = clk.stop()
         rec["generation_s"] = gen_s
-        out[{"random": "config1_random", "uneven": "config3_uneven", "shared": "config4_shared"}[name]] = rec
+        out[{"random": "config1_random", "uneven": "config3_uneven", "shared": "config4_shared",
+             "halting": "next2_halting"}[name]] = rec
         del wl
         torch.cuda.empty_cache()
     if not serving:
@@ -503,7 +510,8 @@ def main():
     total_steps = stats["vm_steps"]
     kernel = run_kernel_name(tuned["chosen"] if tuned else SCHED_NAME.get(args.flags & 0xF0, "persist_gl"), args.flags)
     # the shared-program kernel reads instruction pairs from shared memory
-    alg_bytes = algorithmic_bytes(stats, fetch_from_smem=kernel.startswith("k_shared"))
+    word_bytes = b.describe().get("word_bytes", 8)
+    alg_bytes = algorithmic_bytes(stats, fetch_from_smem=kernel.startswith("k_shared"), word_bytes=word_bytes)
 
     # halting workload: the tau_h histogram is computed on the device in every step
     hist_edges = np.concatenate([np.arange(0, 101), [10 ** 6, 1 << 62]]).astype(np.uint64)
@@ -569,7 +577,7 @@ def main():
                 "traffic_source": "profiles/traffic.json (ncu, 262,144-VM case, epoch 128, scaled by VM-steps)"
                 if traffic is not None else None,
                 "kernel": kernel, "peak_kind": peak_kind,
-                "fetch_from_smem_excluded": kernel.startswith("k_shared"),
+                "fetch_from_smem_excluded": kernel.startswith("k_shared"), "word_bytes": word_bytes,
                 "bytes_per_step": alg_bytes / max(total_steps, 1),
                 "kernel_ms": run_avg, "pack_ms": float(np.mean(pack_ms))}
 

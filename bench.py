@@ -448,6 +448,7 @@ def main():
     ap.add_argument("--isa", default="word", choices=["word", "classic"],
                     help="opcode set: the word machine (Sec. 2.1) or the classic one (Sec. 1.1: SUB, BPA)")
     ap.add_argument("--epoch", type=int, default=0)
+    ap.add_argument("--ctas-per-sm", type=int, default=0, help="resident CTAs per SM of the persistent kernels (0: as many as fit)")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU-oracle baseline")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-plain", action="store_true")
@@ -496,10 +497,11 @@ def main():
 
     wl, desc = make_workload(args.workload, rank, args.vms, args.out_arity)
     stream = torch.cuda.current_stream()
-    b = R.Batch(wl.mem_words, wl.ell, wl.s, word_bits=wl.w, flags=args.flags, epoch=args.epoch)
+    b = R.Batch(wl.mem_words, wl.ell, wl.s, word_bits=wl.w, flags=args.flags, epoch=args.epoch,
+                ctas_per_sm=args.ctas_per_sm)
     b.load_workload(wl)
     tuned = None
-    if (args.flags & R.SCHED_PERSIST_GL) == 0 and not args.epoch and not args.no_tune:
+    if (args.flags & R.SCHED_PERSIST_GL) == 0 and not args.epoch and not args.ctas_per_sm and not args.no_tune:
         tuned = b.autotune(reps=2)      # untimed: measured schedule choice, state unchanged
 
     # opcode mix (and total steps) from an untimed counting run

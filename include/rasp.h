@@ -192,6 +192,17 @@ int rasp_load_programs(rasp_batch* b, const int64_t* words,
                        const uint64_t* offsets, uint64_t num_programs,
                        const uint32_t* prog_of_vm);
 
+/* As rasp_load_programs, for programs whose words all lie in
+ * [-2^31, 2^31): the words are given as int32 and stand for the same int64
+ * values (sign extension), so half as many bytes cross to the device. They
+ * are copied into the batch's machine memory (which c_0 overwrites) and
+ * widened there on the device once the checks have passed. Same arguments,
+ * errors and c_0 as rasp_load_programs; after a failed check the batch holds
+ * no programs and its machine memory is undefined until loaded again. */
+int rasp_load_programs_i32(rasp_batch* b, const int32_t* words,
+                           const uint64_t* offsets, uint64_t num_programs,
+                           const uint32_t* prog_of_vm);
+
 /* Load input tapes x (u = [0, x, 0^(l-|x|)], Sec. 2.1) and per-VM step
  * caps. tape/offsets[num_vms+1] as for programs; caps NULL = no cap
  * (UINT64_MAX). Resets u_0 = 0. EINVAL: |x| > l, offsets not increasing;

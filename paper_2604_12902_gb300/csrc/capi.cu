@@ -130,6 +130,7 @@ struct rasp_batch {
   bool dirty_valid = false;    // codedirty is up to date (only the shared kernel tracks it)
   bool code_lazy = false;      // slabs of VMs with codedirty = 0 lack their program words (lazy pack)
   bool narrow = false;         // M in 4-byte words (w <= 32)
+  bool uhead_pending = false;  // u_0 = 0 owed since rasp_load_inputs (done by the pack or before the next use)
   bool ids_uploaded = false;   // d_ids holds h_ids
   bool ids_base = true;        // h_ids is h_ids_base (bucket order, no cap-class sort)
   uint64_t max_cap = ~0ull;    // largest step cap of the batch (no VM runs further)
@@ -376,6 +377,15 @@ cudaError_t materialize(rasp_batch* b, cudaStream_t st) {
                             b->wmask, st);
 }
 
+// rasp_load_inputs resets u_0 without queuing a kernel (so that the next
+// load's wait for its host copies cannot stall behind kernels of other
+// batches): the pack does it, or this before u_0 is next read.
+cudaError_t apply_uhead_reset(rasp_batch* b, cudaStream_t st) {
+  if (!b->uhead_pending) return cudaSuccess;
+  b->uhead_pending = false;
+  return fill_bytes(b->S.uhead, 0, 4ull * b->V, st);
+}
+
 int replan(rasp_batch* b);
 
 int check_device_error(rasp_batch* b) {
@@ -584,6 +594,21 @@ extern "C" {
 
 int rasp_load_programs(rasp_batch* b, const int64_t* words, const uint64_t* offsets, uint64_t num_programs,
                        const uint32_t* prog_of_vm) {
+  return rasp::load_programs(b, words, 8, offsets, num_programs, prog_of_vm);
+}
+
+int rasp_load_programs_i32(rasp_batch* b, const int32_t* words, const uint64_t* offsets, uint64_t num_programs,
+                           const uint32_t* prog_of_vm) {
+  return rasp::load_programs(b, words, 4, offsets, num_programs, prog_of_vm);
+}
+
+}  // extern "C"
+
+// Programs given as 8-byte words are copied into the program area; 4-byte
+// words are copied into the M arena (which the pack overwrites anyway) and
+// widened on the device, with sign extension, once the checks have passed.
+int rasp::load_programs(rasp_batch* b, const void* words, int word_size, const uint64_t* offsets,
+                        uint64_t num_programs, const uint32_t* prog_of_vm) {
   if (!b) return fail(RASP_EINVAL, "batch is NULL");
   if (!offsets || num_programs == 0) return fail(RASP_EINVAL, "offsets NULL or no programs");
   if (!prog_of_vm && num_programs != b->V)
@@ -600,7 +625,10 @@ int rasp_load_programs(rasp_batch* b, const int64_t* words, const uint64_t* offs
   // whatever the offsets say). A failed check discards the programs: the
   // copy has already replaced the earlier ones.
   cudaStream_t st = b->stream;
-  if (total) CK(cudaMemcpyAsync(b->d_prog, words, 8 * total, cudaMemcpyHostToDevice, st));
+  int32_t* staged = reinterpret_cast<int32_t*>(b->S.mem);   // 4-byte words: M arena (>= 4 * total bytes)
+  if (total)
+    CK(cudaMemcpyAsync(word_size == 8 ? (void*)b->d_prog : (void*)staged, words, (size_t)word_size * total,
+                       cudaMemcpyHostToDevice, st));
   CK(cudaMemcpyAsync(b->d_progoff, offsets, 8 * (num_programs + 1), cudaMemcpyHostToDevice, st));
   if (prog_of_vm) CK(cudaMemcpyAsync(b->d_progvm, prog_of_vm, 4ull * b->V, cudaMemcpyHostToDevice, st));
   b->programs_loaded = false;
@@ -650,15 +678,21 @@ int rasp_load_programs(rasp_batch* b, const int64_t* words, const uint64_t* offs
     CK(cudaStreamSynchronize(st));
   }
   CK(cudaStreamSynchronize(st));   // the caller's buffers are read before the call returns
+  // widening, like the pack, is left queued on the stream: it may have to
+  // wait for SMs that another batch's run holds, and the host need not
+  if (word_size == 4 && total) CK(launch_widen(staged, b->d_prog, total, st));
   CK(fill_bytes(b->d_hist, 0, 8 * 10, st));
   b->code_lazy = pack_lazy(b);
   CK(launch_pack(b->S, b->d_prog, b->d_progoff, b->shared_programs ? b->d_progvm : nullptr, b->V, b->wmask, b->sp,
                  b->code_lazy, st));
+  b->uhead_pending = false;        // the pack resets u_0
   b->programs_loaded = true;
   b->dirty_valid = true;
   g_err.clear();
   return RASP_OK;
 }
+
+extern "C" {
 
 int rasp_load_inputs(rasp_batch* b, const int64_t* tape, const uint64_t* offsets, const uint64_t* caps) {
   if (!b) return fail(RASP_EINVAL, "batch is NULL");
@@ -715,7 +749,7 @@ int rasp_load_inputs(rasp_batch* b, const int64_t* tape, const uint64_t* offsets
     const int rc = order_ids(b);
     if (rc) return rc;
   }
-  CK(fill_bytes(b->S.uhead, 0, 4ull * b->V, st));
+  b->uhead_pending = true;         // u_0 = 0: by the next pack, or before u_0 is next read
   b->inputs_loaded = true;
   g_err.clear();
   return RASP_OK;
@@ -728,6 +762,7 @@ int rasp_reset(rasp_batch* b) {
   b->code_lazy = pack_lazy(b);
   CK(launch_pack(b->S, b->d_prog, b->d_progoff, b->shared_programs ? b->d_progvm : nullptr, b->V, b->wmask, b->sp,
                  b->code_lazy, b->stream));
+  b->uhead_pending = false;
   b->dirty_valid = true;
   return RASP_OK;
 }
@@ -833,6 +868,7 @@ extern "C" {
 int rasp_run(rasp_batch* b, uint64_t max_steps) {
   if (!b) return fail(RASP_EINVAL, "batch is NULL");
   if (!b->programs_loaded || !b->inputs_loaded) return fail(RASP_ESTATE, "load programs and inputs before rasp_run");
+  CK(apply_uhead_reset(b, b->stream));   // eagerly, outside any captured graph
   if (!b->planned) {
     b->planned = true;
     const int rc = replan(b);
@@ -875,6 +911,7 @@ int rasp_read_state(rasp_batch* b, uint64_t first, uint64_t count, rasp_state_vi
   if (!b || !out) return fail(RASP_EINVAL, "batch or view is NULL");
   if (first > b->V || count > b->V - first) return fail(RASP_EINVAL, "range [%llu, +%llu) outside the batch",
                                                       (unsigned long long)first, (unsigned long long)count);
+  CK(apply_uhead_reset(b, b->stream));
   int rc = check_device_error(b);
   if (rc) return rc;
   if (!count) return RASP_OK;
@@ -955,6 +992,7 @@ int rasp_load_state(rasp_batch* b, uint64_t first, uint64_t count, const rasp_st
   }
   cudaStream_t st = b->stream;
   const DevState& S = b->S;
+  CK(apply_uhead_reset(b, st));
   if (in->i) CK(cudaMemcpyAsync(S.i + first, in->i, 8 * count, cudaMemcpyHostToDevice, st));
   if (in->a) CK(cudaMemcpyAsync(S.a + first, in->a, 8 * count, cudaMemcpyHostToDevice, st));
   if (in->steps) CK(cudaMemcpyAsync(S.steps + first, in->steps, 8 * count, cudaMemcpyHostToDevice, st));
@@ -1081,6 +1119,7 @@ int rasp_autotune(rasp_batch* b, uint64_t max_steps, uint32_t reps) {
   if (!b) return fail(RASP_EINVAL, "batch is NULL");
   if (!b->programs_loaded || !b->inputs_loaded) return fail(RASP_ESTATE, "load programs and inputs before tuning");
   if (reps == 0) reps = 1;
+  CK(apply_uhead_reset(b, b->stream));
   int rc = check_device_error(b);
   if (rc) return rc;
   cudaStream_t st = b->stream;

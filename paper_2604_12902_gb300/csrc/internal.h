@@ -153,6 +153,13 @@ cudaError_t launch_ring_append(uint64_t* ring, uint64_t mask, unsigned long long
                                const uint32_t* ids, uint32_t count, unsigned long long* credits,
                                cudaStream_t stream);
 
+// rasp_load_programs from 8-byte (word_size 8) or 4-byte (word_size 4) words.
+int load_programs(rasp_batch* b, const void* words, int word_size, const uint64_t* offsets, uint64_t num_programs,
+                  const uint32_t* prog_of_vm);
+
+// dst[k] = src[k] sign-extended, k < count (device pointers, 16-byte aligned).
+cudaError_t launch_widen(const int32_t* src, uint64_t* dst, uint64_t count, cudaStream_t stream);
+
 // rasp_batch_create; with plan = false the launch plan is left to the first
 // rasp_run (the serving pool's batches are never run by rasp_run).
 int create_batch(const rasp_config* cfg, uint64_t num_vms, const uint32_t* mem_words, bool plan,

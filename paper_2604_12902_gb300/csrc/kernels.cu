@@ -1177,6 +1177,32 @@ const void* persist_symbol(const StepVariant& v, bool staged) {
 
 }  // namespace
 
+// 4-byte program words widened to 8 bytes with sign extension: four per
+// thread per iteration (one 16-byte load, two 16-byte stores), the tail one
+// by one.
+__global__ void __launch_bounds__(256) k_widen(const int32_t* __restrict__ src, uint64_t* __restrict__ dst,
+                                               uint64_t count) {
+  const uint64_t quads = count / 4u;
+  const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+  for (uint64_t q = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; q < quads; q += stride) {
+    const int4 w = reinterpret_cast<const int4*>(src)[q];
+    reinterpret_cast<longlong2*>(dst)[2 * q] = make_longlong2(w.x, w.y);
+    reinterpret_cast<longlong2*>(dst)[2 * q + 1] = make_longlong2(w.z, w.w);
+  }
+  for (uint64_t k = 4u * quads + blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; k < count; k += stride)
+    dst[k] = (uint64_t)(int64_t)src[k];
+}
+
+cudaError_t launch_widen(const int32_t* src, uint64_t* dst, uint64_t count, cudaStream_t stream) {
+  if (!count) return cudaSuccess;
+  uint64_t blocks = (count / 4u + 255u) / 256u;
+  const uint64_t cap = (uint64_t)num_sms() * 16u;
+  if (blocks > cap) blocks = cap;
+  if (blocks == 0) blocks = 1;
+  k_widen<<<(uint32_t)blocks, 256, 0, stream>>>(src, dst, count);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_pack(const DevState& S, const uint64_t* prog, const uint64_t* prog_off,
                         const uint32_t* prog_of_vm, uint32_t num_vms, uint64_t wmask, uint32_t sp,
                         bool lazy, cudaStream_t stream) {

@@ -65,7 +65,8 @@ _lib = None
 EXPORTS = ["rasp_batch_bytes", "rasp_batch_create", "rasp_load_programs", "rasp_load_inputs",
            "rasp_reset", "rasp_run", "rasp_sync", "rasp_read_state", "rasp_load_state",
            "rasp_read_stats", "rasp_describe", "rasp_autotune", "rasp_halting_histogram",
-           "rasp_top_halting", "rasp_plan_bucket", "rasp_batch_destroy", "rasp_last_error", "rasp_version"]
+           "rasp_top_halting", "rasp_plan_bucket", "rasp_load_programs_i32", "rasp_batch_destroy",
+           "rasp_last_error", "rasp_version"]
 
 
 def lib():
@@ -92,11 +93,12 @@ def lib():
         L.rasp_halting_histogram.argtypes = [P, P, U32, P, P]
         L.rasp_top_halting.argtypes = [P, U32, P, P, P]
         L.rasp_plan_bucket.argtypes = [P, U32, U32, U32, U32, U32]
+        L.rasp_load_programs_i32.argtypes = [P, P, P, U64, P]
         L.rasp_batch_destroy.argtypes = [P]
         L.rasp_batch_destroy.restype = None
         L.rasp_last_error.restype = ctypes.c_char_p
         L.rasp_version.restype = ctypes.c_char_p
-        for name in EXPORTS[:15]:
+        for name in EXPORTS[:16]:
             getattr(L, name).restype = I
         _lib = L
     return _lib
@@ -136,6 +138,14 @@ def rasp_load_programs(h, words, offsets, prog_of_vm=None):
     o = _c(offsets, np.uint64)
     pv = _c(prog_of_vm, np.uint32)
     _check(lib().rasp_load_programs(h, _p(w), _p(o), o.shape[0] - 1, _p(pv)))
+
+
+def rasp_load_programs_i32(h, words, offsets, prog_of_vm=None):
+    """Programs as int32 words (each stands for its sign-extended int64)."""
+    w = _c(words, np.int32) if len(words) else np.zeros(1, np.int32)
+    o = _c(offsets, np.uint64)
+    pv = _c(prog_of_vm, np.uint32)
+    _check(lib().rasp_load_programs_i32(h, _p(w), _p(o), o.shape[0] - 1, _p(pv)))
 
 
 def rasp_load_inputs(h, tape, offsets, caps=None):

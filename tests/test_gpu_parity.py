@@ -430,3 +430,62 @@ def test_narrow_words_checkpoint_and_schedules(rasp, w):
             b2.load_state(ck)
             b2.run()
             assert_same_state(b2.read_state(), st, wl.ell, wl.s, what="w %d flags %#x restored" % (w, flags))
+
+
+def test_programs_loaded_as_int32_words(rasp):
+    """Programs whose words fit in 32 bits, loaded as int32 words and
+    sign-extended on the device, give the same machines as int64 words:
+    templates (negative immediates), self-modifying random programs at
+    w = 64 and w = 32 (4-byte machine words), shared programs; a reset
+    re-packs from the widened programs; a failed load leaves no programs."""
+    R = rasp
+    cases = [(W.template_programs(num_vms=3000, seed=31), 64), (W.random_programs(num_vms=2000, seed=32), 64),
+             (W.random_programs(num_vms=2000, seed=33), 32), (W.shared_programs(num_programs=64, vms_per_program=16), 64)]
+    for wl, w in cases:
+        wl.w = w
+        assert np.all(np.abs(wl.programs) < (1 << 31))
+        st, _ = oracle_state(wl)
+        with R.Batch(wl.mem_words, wl.ell, wl.s, word_bits=w) as b:
+            R.rasp_load_programs_i32(b.h, wl.programs.astype(np.int32), wl.prog_off, wl.prog_of_vm)
+            b.load_inputs(wl.tapes, wl.tape_off, wl.caps)
+            b.run()
+            assert_same_state(b.read_state(), st, wl.ell, wl.s, what="int32 programs, %s w %d" % (wl.name, w))
+            b.reset()
+            b.run()
+            assert_same_state(b.read_state(), st, wl.ell, wl.s, what="int32 programs after reset, %s" % wl.name)
+            bad = wl.prog_off.copy()
+            bad[1] = 3
+            with pytest.raises(R.RaspError):
+                R.rasp_load_programs_i32(b.h, wl.programs.astype(np.int32), bad, wl.prog_of_vm)
+            with pytest.raises(R.RaspError) as e:
+                b.run()
+            assert e.value.code == R.RASP_ESTATE
+
+
+@pytest.mark.parametrize("flags", [0x00, 0x4000], ids=["eager", "cuda-graph"])
+def test_inputs_reloaded_midway_reset_the_read_head(rasp, flags):
+    """rasp_load_inputs resets u_0 = 0 (applied by the next pack, or before
+    u_0 is next read or run): reloading the tapes midway reads back u_0 = 0,
+    and running on equals restoring the midway state with u_0 = 0."""
+    R = rasp
+    wl = W.template_programs(num_vms=2500, seed=41)
+    with R.Batch(wl.mem_words, wl.ell, wl.s, flags=flags) as a, R.Batch(wl.mem_words, wl.ell, wl.s, flags=flags) as b:
+        a.load_workload(wl)
+        b.load_workload(wl)
+        a.run(30)
+        b.run(30)
+        mid = b.read_state()
+        assert mid["uhead"].max() > 0
+        a.load_inputs(wl.tapes, wl.tape_off, wl.caps)
+        after = a.read_state()
+        assert after["uhead"].max() == 0
+        for k in ("i", "a", "steps", "status", "mem"):
+            assert np.array_equal(after[k], mid[k]), k
+        a.load_inputs(wl.tapes, wl.tape_off, wl.caps)       # again, then straight into a run
+        a.run()
+        mid["uhead"][:] = 0
+        b.load_state(mid)
+        b.run()
+        ga, gb = a.read_state(), b.read_state()
+    for k in ga:
+        assert np.array_equal(ga[k], gb[k]), k

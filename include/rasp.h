@@ -99,9 +99,9 @@ enum rasp_semantics {
                                           every step as one predicated block
                                           (the earlier form) instead of the
                                           epoch loop that leaves by warp vote;
-                                          shared-program schedule: one step at
-                                          a time per lane instead of the
-                                          epoch loop                           */
+                                          SMEM-staged and shared-program
+                                          schedules: one step at a time per
+                                          lane instead of the epoch loop      */
 #define RASP_ISA_CLASSIC       0x8000u /* the classic RASP opcode set (Sec. 1.1)
                                           on the same words: opcode 3 is SUB
                                           (a - M_j mod 2^w), opcode 5 is BPA
@@ -271,10 +271,12 @@ int rasp_top_halting(rasp_batch* b, uint32_t k, uint64_t* steps_out, uint32_t* v
 
 /* Measured schedule choice (the autotuner): times candidate schedules
  * (persistent over HBM slabs with several epochs and CTA shapes, plain, and
- * SMEM-staged where it fits) on this batch from its current state with the
+ * SMEM-staged where it fits, as its epoch loop and one step at a time) on
+ * this batch from its current state with the
  * given step budget, `reps` times each, restoring the state after every
  * trial, then adopts the fastest for later rasp_run calls (replacing any
- * schedule flag of the config). The machine state is left unchanged.
+ * schedule flag of the config; the one-step staged form adds
+ * RASP_STEP_BLOCK). The machine state is left unchanged.
  * Allocates a temporary snapshot of the state (ENOMEM if it does not fit).
  * Synchronises the stream. The trial times appear in rasp_describe.
  * With more than one memory-size bucket a second pass follows (coordinate

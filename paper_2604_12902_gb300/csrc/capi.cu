@@ -76,6 +76,7 @@ struct Group {
 struct BucketPlan {
   bool set = false;
   uint32_t sched = 0, epoch = 0, warps = 0, ctas = 0;
+  bool block = false;      // the per-step form instead of the epoch loop
 };
 
 struct Layout {
@@ -269,6 +270,7 @@ void plan_buckets(rasp_batch* b) {
     sh.ncap = k.ncap;
     sh.slot_words = slot;
     sh.epoch = cfg_epoch ? cfg_epoch : 32u;
+    sh.block = own && b->over[bi].block;
     if (sched == RASP_SCHED_PERSIST) {
       sh.staged = true;
       sh.warps = 1;
@@ -347,7 +349,8 @@ void build_groups(rasp_batch* b) {
     if (!k.count) continue;
     const PersistShape& gs = b->groups.empty() ? k.shape : b->groups.back().shape;
     const bool same_shape = gs.warps == k.shape.warps && gs.epoch == k.shape.epoch && gs.grid == k.shape.grid &&
-                            gs.ctas_per_sm == k.shape.ctas_per_sm && gs.idle_exit == k.shape.idle_exit;
+                            gs.ctas_per_sm == k.shape.ctas_per_sm && gs.idle_exit == k.shape.idle_exit &&
+                            gs.block == k.shape.block;
     if (!b->groups.empty() && k.sched == RASP_SCHED_PERSIST_GL && b->groups.back().sched == RASP_SCHED_PERSIST_GL &&
         same_shape && b->groups.back().first + b->groups.back().count == k.first) {
       b->groups.back().count += k.count;
@@ -1149,14 +1152,20 @@ int rasp_autotune(rasp_batch* b, uint64_t max_steps, uint32_t reps) {
   // HBM-slab persistent shapes: epochs, CTA sizes and resident CTAs per SM
   // (fewer resident VMs keep large memories in L1/L2: the uneven batch runs
   // best at 12 warps per SM, the template batch at 28)
-  struct Cand { const char* name; uint32_t sched, epoch, warps, ctas; };
+  // The SMEM-staged schedule in both forms: its epoch loop, and one step at
+  // a time (fastest when a few thousand short runs leave the loop often).
+  struct Cand { const char* name; uint32_t sched, epoch, warps, ctas; bool block; };
   static const Cand cands[] = {
-      {"persist_gl e128 w4", RASP_SCHED_PERSIST_GL, 128, 4, 0}, {"persist_gl e64 w4", RASP_SCHED_PERSIST_GL, 64, 4, 0},
-      {"persist_gl e256 w4", RASP_SCHED_PERSIST_GL, 256, 4, 0}, {"persist_gl e128 w2", RASP_SCHED_PERSIST_GL, 128, 2, 0},
-      {"persist_gl e128 w4 c3", RASP_SCHED_PERSIST_GL, 128, 4, 3},
-      {"persist_gl e128 w4 c5", RASP_SCHED_PERSIST_GL, 128, 4, 5},
-      {"plain", RASP_SCHED_PLAIN, 0, 0, 0},                     {"persist_smem e32 w1", RASP_SCHED_PERSIST, 32, 1, 0},
-      {"shared", RASP_SCHED_SHARED, 0, 0, 0}};
+      {"persist_gl e128 w4", RASP_SCHED_PERSIST_GL, 128, 4, 0, false},
+      {"persist_gl e64 w4", RASP_SCHED_PERSIST_GL, 64, 4, 0, false},
+      {"persist_gl e256 w4", RASP_SCHED_PERSIST_GL, 256, 4, 0, false},
+      {"persist_gl e128 w2", RASP_SCHED_PERSIST_GL, 128, 2, 0, false},
+      {"persist_gl e128 w4 c3", RASP_SCHED_PERSIST_GL, 128, 4, 3, false},
+      {"persist_gl e128 w4 c5", RASP_SCHED_PERSIST_GL, 128, 4, 5, false},
+      {"plain", RASP_SCHED_PLAIN, 0, 0, 0, false},
+      {"persist_smem e128 w1", RASP_SCHED_PERSIST, 128, 1, 0, false},
+      {"persist_smem e32 w1 step", RASP_SCHED_PERSIST, 32, 1, 0, true},
+      {"shared", RASP_SCHED_SHARED, 0, 0, 0, false}};
   // the shared-program schedule is a candidate only when programs are shared;
   // the classic opcode set runs on the HBM-slab persistent and plain schedules only
   const bool classic = (b->cfg.flags & RASP_ISA_CLASSIC) != 0;
@@ -1190,7 +1199,7 @@ int rasp_autotune(rasp_batch* b, uint64_t max_steps, uint32_t reps) {
     return RASP_OK;
   };
   auto adopt = [&](rasp_config& c, const Cand& k) {
-    c.flags = (saved.flags & ~RASP_SCHED_MASK) | k.sched;
+    c.flags = (saved.flags & ~RASP_SCHED_MASK) | k.sched | (k.block ? RASP_STEP_BLOCK : 0u);
     c.epoch = k.epoch;
     c.warps_per_cta = k.warps;
     c.ctas_per_sm = k.ctas;
@@ -1237,7 +1246,7 @@ int rasp_autotune(rasp_batch* b, uint64_t max_steps, uint32_t reps) {
         if (k == best_k || cands[k].sched == RASP_SCHED_SHARED || cands[k].epoch == 64 || cands[k].epoch == 256)
           continue;
         const BucketPlan keep = b->over[bi];
-        b->over[bi] = BucketPlan{true, cands[k].sched, cands[k].epoch, cands[k].warps, cands[k].ctas};
+        b->over[bi] = BucketPlan{true, cands[k].sched, cands[k].epoch, cands[k].warps, cands[k].ctas, cands[k].block};
         float tmin = 0;
         rc = trial(tmin);
         if (rc || ce != cudaSuccess) break;

@@ -226,6 +226,18 @@ __device__ __forceinline__ ulonglong2 mem_pair(const NarrowView& V, bool, uint32
 __device__ __forceinline__ uint64_t mem_rd(const NarrowView& V, bool, uint32_t k) { return V.M[k]; }
 __device__ __forceinline__ void mem_wr(const NarrowView& V, bool&, uint32_t k, uint64_t v) { V.M[k] = (uint32_t)v; }
 
+// A lane's memory in shared memory (the SMEM-staged schedule): the plain
+// accessors through a generic pointer; its epoch loop addresses M, the tape
+// and y generically.
+struct SmemView {
+  uint64_t* M;
+};
+__device__ __forceinline__ ulonglong2 mem_pair(const SmemView& V, bool, uint32_t k) {
+  return *reinterpret_cast<const ulonglong2*>(V.M + k);
+}
+__device__ __forceinline__ uint64_t mem_rd(const SmemView& V, bool, uint32_t k) { return V.M[k]; }
+__device__ __forceinline__ void mem_wr(const SmemView& V, bool&, uint32_t k, uint64_t v) { V.M[k] = v; }
+
 // <o, j> = <M[i mod n], M[(i (+) 1) mod n]> when the pair is not one aligned
 // 16-byte word (odd n or odd i mod n, or i = 2^w - 1 where i (+) 1 wraps to 0).
 template <class Mem>
@@ -626,6 +638,22 @@ __device__ __forceinline__ uint32_t fast_step_ptx(uint64_t* M, const uint64_t* T
       "setp.eq.u32 p3, ol, 3;\n\t" \
       "@p2 add.u64 %0, %0, v;\n\t"
 #define RASP_LOOP_B RASP_LOOP_B1 RASP_LOOP_B2 RASP_LOOP_ADDR_GL RASP_LOOP_B3 RASP_LOOP_FETCH_GL RASP_LOOP_B4
+// The same steps through generic addresses (M, tape and y in shared memory:
+// the SMEM-staged schedule).
+#define RASP_LOOP_B4_GEN \
+      "and.b32 t0, m, 0x8C;\n\t" \
+      "setp.ne.u32 pop, t0, 0;\n\t" \
+      "@pop ld.u64 v, [ado];\n\t" \
+      "mad.wide.u32 adt, %4, 8, %10;\n\t" \
+      "@p6 ld.u64 tv, [adt];\n\t" \
+      "setp.eq.u32 p4, ol, 4;\n\t" \
+      "@p4 st.u64 [ado], %0;\n\t" \
+      "@p6 st.u64 [ado], tv;\n\t" \
+      "or.pred pw, p4, p6;\n\t" \
+      "setp.eq.u32 p2, ol, 2;\n\t" \
+      "setp.eq.u32 p3, ol, 3;\n\t" \
+      "@p2 add.u64 %0, %0, v;\n\t"
+#define RASP_LOOP_B_GEN RASP_LOOP_B1 RASP_LOOP_B2 RASP_LOOP_ADDR_GL RASP_LOOP_B3 RASP_LOOP_FETCH_SH RASP_LOOP_B4_GEN
 #define RASP_LOOP_B_SH \
   RASP_LOOP_B1 RASP_LOOP_SH_GUARD RASP_LOOP_B2 RASP_LOOP_ADDR_SH RASP_LOOP_B3 RASP_LOOP_FETCH_SH RASP_LOOP_B4
 // opcode 3 (the guards are exclusive, so each lane updates a at most once):
@@ -637,6 +665,22 @@ __device__ __forceinline__ uint32_t fast_step_ptx(uint64_t* M, const uint64_t* T
       "setp.eq.and.u32 pp, ol, 7, pp;\n\t" \
       "mad.wide.u32 ady, %5, 8, %11;\n\t" \
       "@pp st.global.u64 [ady], v;\n\t" \
+      "@pp add.u32 %5, %5, 1;\n\t" \
+      "@p6 add.u32 %4, %4, 1;\n\t" \
+      "setp.ge.or.u32 pq, t1, 2, !pw;\n\t" \
+      "and.pred ph, pe, pq;\n\t" \
+      "add.u32 %7, %7, -1;\n\t" \
+      "bra.uni RASP_LOOP;\n\t" \
+      "RASP_DONE:\n\t" \
+      "setp.ne.and.u32 px, %7, 0, px;\n\t" \
+      "selp.u32 %8, 1, 0, px;\n\t" \
+      "selp.u32 %6, 1, 0, ph;\n\t" \
+      "}"
+#define RASP_LOOP_D_GEN \
+      "setp.lt.u32 pp, %5, %15;\n\t" \
+      "setp.eq.and.u32 pp, ol, 7, pp;\n\t" \
+      "mad.wide.u32 ady, %5, 8, %11;\n\t" \
+      "@pp st.u64 [ady], v;\n\t" \
       "@pp add.u32 %5, %5, 1;\n\t" \
       "@p6 add.u32 %4, %4, 1;\n\t" \
       "setp.ge.or.u32 pq, t1, 2, !pw;\n\t" \
@@ -673,6 +717,26 @@ __device__ __forceinline__ uint32_t fast_loop_ptx(uint64_t* M, const uint64_t* T
                  RASP_LOOP_OPERANDS);
   } else {
     asm volatile(RASP_LOOP_A RASP_LOOP_PZ_WORD RASP_LOOP_B RASP_LOOP_PD_WORD RASP_LOOP_D
+                 RASP_LOOP_OPERANDS);
+  }
+  return rare;
+}
+
+// The epoch loop of the SMEM-staged schedule: the steps of fast_loop_ptx
+// with every access through a generic address (M, the tape and y of the lane
+// sit in shared memory). Word opcode set, w = 64 or masked.
+template <bool MASKED>
+__device__ __forceinline__ uint32_t fast_loop_ptx_gen(uint64_t* M, const uint64_t* T, uint64_t* Y, uint32_t n,
+                                                      uint32_t ell, uint32_t s, uint32_t ilim, uint64_t wmask,
+                                                      uint32_t mask, uint64_t& a, uint64_t& co, uint64_t& cj,
+                                                      uint32_t& ip, uint32_t& u0, uint32_t& y0, uint32_t& have,
+                                                      uint32_t& kk) {
+  uint32_t rare;
+  if constexpr (MASKED) {
+    asm volatile(RASP_LOOP_A RASP_LOOP_PZ_WORD RASP_LOOP_B_GEN RASP_LOOP_PD_WORD
+                 "and.b64 %0, %0, %18;\n\t" RASP_LOOP_D_GEN RASP_LOOP_OPERANDS);
+  } else {
+    asm volatile(RASP_LOOP_A RASP_LOOP_PZ_WORD RASP_LOOP_B_GEN RASP_LOOP_PD_WORD RASP_LOOP_D_GEN
                  RASP_LOOP_OPERANDS);
   }
   return rare;

@@ -32,6 +32,7 @@ struct PersistShape {
   uint32_t epoch;       // steps between warp scheduling points
   uint32_t refill_min;  // idle lanes that trigger a refill (staged schedule)
   uint32_t idle_exit;   // HBM-slab epoch loop: stopped lanes that end an epoch early (0: never)
+  bool block;           // one step at a time (the per-step form) instead of the epoch loop
   uint32_t grid;        // CTAs
   uint32_t ctas_per_sm; // resident CTAs per SM (occupancy)
   size_t smem;          // dynamic shared memory per CTA

@@ -282,6 +282,10 @@ __device__ __forceinline__ void run_epoch_loop(Mem M, const uint64_t* T, uint64_
           r.a = a32;
           co = co32;
           cj = cj32;
+        } else if constexpr (std::is_same<Mem, SmemView>::value) {
+          // M, tape and y in shared memory: generic addresses, word opcode set
+          rare = fast_loop_ptx_gen<MASKED>(M.M, T, Y, r.n, P.ell, P.s, r.ilim, P.wmask, mask, r.a, co, cj, r.ip,
+                                           r.u0, r.y0, hv, kk);
         } else {
           rare = fast_loop_ptx<MASKED, CLASSIC>(M, T, Y, r.n, P.ell, P.s, r.ilim, P.wmask, mask, r.a, co, cj, r.ip,
                                                 r.u0, r.y0, hv, kk);
@@ -319,7 +323,7 @@ __device__ __forceinline__ void run_epoch_loop(Mem M, const uint64_t* T, uint64_
 }
 
 // ------------------------------------------------------------------ persistent, staged in SMEM
-template <bool MASKED, bool CHECKED, bool HIST, bool VOTE>
+template <bool MASKED, bool CHECKED, bool HIST, bool VOTE, bool LOOP = false>
 __global__ void __launch_bounds__(256) k_persist(DevState S, Params P, Queue Q, uint32_t ncap,
                                                  uint32_t slot_words, uint32_t epoch, uint32_t refill_min,
                                                  uint32_t wait_limit) {
@@ -395,6 +399,7 @@ __global__ void __launch_bounds__(256) k_persist(DevState S, Params P, Queue Q, 
         }
         phase ^= 1u;
         active = fresh;
+        if (LOOP && fresh) prime(M, r);
       }
     }
     if (__all_sync(FULL, exhausted && !active)) break;
@@ -402,7 +407,10 @@ __global__ void __launch_bounds__(256) k_persist(DevState S, Params P, Queue Q, 
 
     // ---- run until enough lanes can be refilled (checked every `epoch` steps)
     for (;;) {
-      run_epoch<MASKED, CHECKED, HIST, VOTE, false>(M, T, Y, P, r, h, active, final_st, epoch);
+      if constexpr (LOOP)
+        run_epoch_loop<MASKED, false>(SmemView{M}, T, Y, P, r, h, active, final_st, epoch, 0u);
+      else
+        run_epoch<MASKED, CHECKED, HIST, VOTE, false>(M, T, Y, P, r, h, active, final_st, epoch);
       if (!__any_sync(FULL, active)) break;
       const uint32_t want = __ballot_sync(FULL, !active && !exhausted);
       if ((uint32_t)__popc(want) >= refill_min) break;
@@ -1151,6 +1159,9 @@ StagedFn staged_fn(bool vote) {
 }
 
 StagedFn pick_staged(const StepVariant& v) {
+  // the epoch loop (generic addresses) unless checked, counting, voting or per-step
+  if (!v.checked && !v.hist && !v.vote && !v.block)
+    return v.masked ? k_persist<true, false, false, false, true> : k_persist<false, false, false, false, true>;
   if (v.checked) return v.hist ? staged_fn<false, true, true>(v.vote) : staged_fn<false, true, false>(v.vote);
   if (v.masked) return v.hist ? staged_fn<true, false, true>(v.vote) : staged_fn<true, false, false>(v.vote);
   return v.hist ? staged_fn<false, false, true>(v.vote) : staged_fn<false, false, false>(v.vote);
@@ -1266,8 +1277,14 @@ cudaError_t launch_plain(const StepVariant& var, const DevState& S, const Params
   return cudaGetLastError();
 }
 
+// The variant of a persistent launch: the shape may choose the per-step form.
+StepVariant shape_variant(StepVariant v, const PersistShape& sh) {
+  v.block = v.block || sh.block;
+  return v;
+}
+
 int persist_configure(const StepVariant& var, PersistShape& sh) {
-  const void* fn = persist_symbol(var, sh.staged);
+  const void* fn = persist_symbol(shape_variant(var, sh), sh.staged);
   const size_t per_warp = sh.staged ? (32ull + 32ull * sh.slot_words) * 8ull : 0u;
   sh.smem = per_warp * sh.warps;
   if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sh.smem) != cudaSuccess) {
@@ -1301,12 +1318,13 @@ cudaError_t launch_persist(const StepVariant& var, const DevState& S, const Para
   Queue q = Q;
   const uint64_t lanes = (uint64_t)grid * sh.warps * 32u;
   q.soft_end = Q.count > lanes ? (uint32_t)(Q.count - lanes) : 0u;
+  const StepVariant v = shape_variant(var, sh);
   if (sh.staged)
-    pick_staged(var)<<<grid, 32u * sh.warps, sh.smem, stream>>>(S, P, q, sh.ncap, sh.slot_words, sh.epoch,
+    pick_staged(v)<<<grid, 32u * sh.warps, sh.smem, stream>>>(S, P, q, sh.ncap, sh.slot_words, sh.epoch,
                                                                  sh.refill_min,
                                                                  inject_wait_expiry() ? 0u : WAIT_LIMIT);
   else
-    pick_global(var)<<<grid, 32u * sh.warps, 0, stream>>>(S, P, q, sh.epoch, sh.idle_exit);
+    pick_global(v)<<<grid, 32u * sh.warps, 0, stream>>>(S, P, q, sh.epoch, sh.idle_exit);
   return cudaGetLastError();
 }
 

@@ -16,7 +16,8 @@ from tests.helpers import U64, assert_same_state, oracle_state
 
 pytestmark = pytest.mark.gpu
 
-SCHEDS = {"auto": 0x00, "plain": 0x10, "staged": 0x20, "slab": 0x30, "vote": 0x130, "block": 0x20030}
+SCHEDS = {"auto": 0x00, "plain": 0x10, "staged": 0x20, "staged-step": 0x20020, "slab": 0x30, "vote": 0x130,
+          "block": 0x20030}
 
 
 @pytest.fixture(scope="module")

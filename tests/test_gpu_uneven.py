@@ -121,7 +121,7 @@ def test_autotune_leaves_state_and_keeps_parity(rasp, uneven64k):
         after = b.read_state()
         for k in before:
             assert np.array_equal(before[k], after[k]), k
-        assert len(rep["trials"]) == 8          # no shared candidate: programs not shared
+        assert len(rep["trials"]) == 9          # no shared candidate: programs not shared
         assert rep["chosen"] in [t["schedule"] for t in rep["trials"]]
         best = min(rep["trials"], key=lambda t: t["ms"])
         assert rep["chosen"] == best["schedule"]

@@ -205,6 +205,27 @@ def run_kernel_name(chosen: str, flags: int) -> str:
     return kernel
 
 
+PROGRAM_WORDS = {True: "int32 (every program word fits; sign-extended on the device, machine words w bits)",
+                 False: "int64"}
+
+
+def programs_fit_int32(wl) -> bool:
+    """Every program word fits in 32 bits (a signed int32)."""
+    return bool(wl.programs.size) and int(wl.programs.min()) >= -(1 << 31) and int(wl.programs.max()) < (1 << 31)
+
+
+def load_wl(R, b, wl, p32=None):
+    """Load a workload into a batch; programs whose words all fit in 32 bits
+    go through rasp_load_programs_i32 (p32: those words as int32), which
+    keeps them as 4-byte words on the device where they fit beside M and
+    sign-extends them in the pack. The machine words stay w bits."""
+    if p32 is not None:
+        R.rasp_load_programs_i32(b.h, p32, wl.prog_off, wl.prog_of_vm)
+    else:
+        b.load_programs(wl.programs, wl.prog_off, wl.prog_of_vm)
+    b.load_inputs(wl.tapes, wl.tape_off, wl.caps)
+
+
 def time_config(R, torch, wl, desc, flags, steps, warmup, flush_l2=False):
     """Times one workload the way the headline is timed (re-pack c_0 + run to
     completion per step, CUDA events on the batch stream, generation and
@@ -212,11 +233,12 @@ def time_config(R, torch, wl, desc, flags, steps, warmup, flush_l2=False):
     run kernel against the measured HBM bandwidth, and the final statuses."""
     stream = torch.cuda.current_stream()
     flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda") if flush_l2 else None
+    p32 = wl.programs.astype(np.int32) if programs_fit_int32(wl) else None
     with R.Batch(wl.mem_words, wl.ell, wl.s, word_bits=wl.w, flags=flags) as b:
-        b.load_workload(wl)
+        load_wl(R, b, wl, p32)
         tuned = b.autotune(reps=2) if (flags & 0xF0) == 0 else None
         with R.Batch(wl.mem_words, wl.ell, wl.s, word_bits=wl.w, flags=flags | R.COLLECT_STATS) as bs:
-            bs.load_workload(wl)
+            load_wl(R, bs, wl, p32)
             bs.run()
             stats = bs.stats()
         chosen = tuned["chosen"] if tuned else "flags %#x" % flags
@@ -251,7 +273,7 @@ def time_config(R, torch, wl, desc, flags, steps, warmup, flush_l2=False):
     return {"workload": desc, "vms": wl.num_vms, "vm_steps": int(stats["vm_steps"]), "steps": steps,
             "warmup": warmup, "ms_per_step": float(np.mean(step_ms)),
             "value": stats["vm_steps"] / (float(np.mean(step_ms)) * 1e-3), "unit": UNIT,
-            "schedule": chosen, "cuda_graph": bool(flags & R.CUDA_GRAPH),
+            "schedule": chosen, "cuda_graph": bool(flags & R.CUDA_GRAPH), "program_words": PROGRAM_WORDS[p32 is not None],
             "l2": ("inputs larger than L2 (M = %.2f GiB)" % (m_bytes / 2 ** 30)) if m_bytes > 129e6
             else ("M = %.2f MB fits in L2: 256 MB written between timed steps" % (m_bytes / 1e6)),
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
@@ -465,6 +487,8 @@ def main():
     ap.add_argument("--tau-max", type=int, default=10 ** 5, help="search: step cap")
     ap.add_argument("--no-serving", action="store_true",
                     help="leave config 5 (60 s of serving) out of the other configurations")
+    ap.add_argument("--e2e-batches", type=int, default=3,
+                    help="end-to-end leg: batches in flight (each on a stream of its own)")
     ap.add_argument("--no-other", action="store_true",
                     help="skip the other configurations (random, uneven, shared) after the headline")
     ap.add_argument("--out-arity", type=int, default=0,
@@ -499,14 +523,15 @@ def main():
     stream = torch.cuda.current_stream()
     b = R.Batch(wl.mem_words, wl.ell, wl.s, word_bits=wl.w, flags=args.flags, epoch=args.epoch,
                 ctas_per_sm=args.ctas_per_sm)
-    b.load_workload(wl)
+    p32 = wl.programs.astype(np.int32) if programs_fit_int32(wl) else None
+    load_wl(R, b, wl, p32)
     tuned = None
     if (args.flags & R.SCHED_PERSIST_GL) == 0 and not args.epoch and not args.ctas_per_sm and not args.no_tune:
         tuned = b.autotune(reps=2)      # untimed: measured schedule choice, state unchanged
 
     # opcode mix (and total steps) from an untimed counting run
     with R.Batch(wl.mem_words, wl.ell, wl.s, word_bits=wl.w, flags=args.flags | R.COLLECT_STATS, epoch=args.epoch) as bs:
-        bs.load_workload(wl)
+        load_wl(R, bs, wl, p32)
         bs.run()
         stats = bs.stats()
     total_steps = stats["vm_steps"]
@@ -608,9 +633,8 @@ def main():
         pin = lambda a: _pinned_copy(torch, a)
         # programs whose words all fit in 32 bits go up as int32 words (half
         # the bytes; the library sign-extends them on the device)
-        narrow_prog = bool(wl.programs.size) and int(wl.programs.min()) >= -(1 << 31) and \
-            int(wl.programs.max()) < (1 << 31)
-        h_prog = pin(wl.programs.astype(np.int32) if narrow_prog else wl.programs)
+        narrow_prog = p32 is not None
+        h_prog = pin(p32 if narrow_prog else wl.programs)
         h_poff = pin(wl.prog_off)
         load_programs = R.rasp_load_programs_i32 if narrow_prog else R.rasp_load_programs
         h_pvm = pin(wl.prog_of_vm) if wl.prog_of_vm is not None else None
@@ -622,32 +646,36 @@ def main():
         h2d = sum(x.nbytes for x in (h_prog, h_poff, h_tape, h_toff, h_caps) + ((h_pvm,) if h_pvm is not None else ()))
         d2h = sum(x.nbytes for x in out.values())
 
-        # Two batches in flight: step t uploads, packs and runs batch t % 2
-        # while the run of the other batch (step t - 1) finishes on its own
-        # stream; a second host thread reads each step's results back as soon
-        # as its run is done, so that the read of step t - 1 (device to host)
-        # overlaps the upload of step t (host to device). A batch is loaded
-        # again only after its previous results have been read. Every step
-        # still copies its own inputs host -> device and its results
-        # device -> host inside the timed region.
+        # NB batches in flight (default 3): step t uploads, packs and runs
+        # batch t % NB while the runs of earlier steps finish on their own
+        # streams; a second host thread reads each step's results back as
+        # soon as its run is done, so that reads (device to host) overlap
+        # uploads (host to device). A batch is loaded again only after its
+        # previous results have been read: with two batches the upload of
+        # step t waits for the read of step t - 2, which ends one read after
+        # the run before it, so upload + read + host work must fit in one
+        # run; a third batch gives them two. Every step still copies its own
+        # inputs host -> device and its results device -> host inside the
+        # timed region.
         from concurrent.futures import ThreadPoolExecutor
         plan = b.describe()["buckets"][0]
         sched = {"plain": R.SCHED_PLAIN, "persist": R.SCHED_PERSIST, "persist_gl": R.SCHED_PERSIST_GL,
                  "shared": R.SCHED_SHARED}[plan["schedule"]]
         # each batch on a stream of its own (not the legacy default stream,
         # which would order every other stream's work around its own)
-        e2e_streams = [torch.cuda.Stream(), torch.cuda.Stream()]
+        nb = max(1, args.e2e_batches)
+        e2e_streams = [torch.cuda.Stream() for _ in range(nb)]
         pair = [R.Batch(wl.mem_words, wl.ell, wl.s, word_bits=wl.w, flags=(args.flags & ~0xF0) | sched,
                         epoch=plan["epoch"], warps_per_cta=plan["warps_per_cta"], ctas_per_sm=plan["ctas_per_sm"],
-                        stream=e2e_streams[k].cuda_stream) for k in range(2)]
-        outs = [out, {k: pin(np.empty_like(v)) for k, v in out.items()}]
+                        stream=e2e_streams[k].cuda_stream) for k in range(nb)]
+        outs = [out] + [{k: pin(np.empty_like(v)) for k, v in out.items()} for _ in range(nb - 1)]
         views = [R.rasp_state_view(*(R._p(o[k]) for k in ("i", "a", "steps", "status", "uhead", "ylen", "y")),
                                    None, 0) for o in outs]
         reader = ThreadPoolExecutor(1)
-        reads = [None, None]
+        reads = [None] * nb
 
         def e2e_step(t):
-            x = t % 2
+            x = t % nb
             if reads[x] is not None:
                 reads[x].result()            # batch x's previous results are out before it is reloaded
             # inputs first: their load queues no kernel, so that neither load's
@@ -658,16 +686,16 @@ def main():
             reads[x] = reader.submit(R.rasp_read_state, pair[x].h, 0, wl.num_vms, views[x])
 
         def e2e_drain():
-            for x in (0, 1):
+            for x in range(nb):
                 if reads[x] is not None:
                     reads[x].result()
                     reads[x] = None
 
-        for t in range(4):
+        for t in range(max(4, 2 * nb)):
             e2e_step(t)
         e2e_drain()
         torch.cuda.synchronize()
-        n_e2e = max(4, args.steps)
+        n_e2e = max(4, 2 * nb, args.steps)
         t0 = time.perf_counter()
         for t in range(n_e2e):
             e2e_step(t)
@@ -696,9 +724,9 @@ def main():
             e2e_val = steps_total / t_max
         e2e = {"value": e2e_val, "unit": UNIT, "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h),
                "ms_per_step": dt * 1e3, "steps": n_e2e, "h2d_gbs_alone": h2d_gbs,
-               "program_words": "int32 (every word fits; widened on the device)" if narrow_prog else "int64",
-               "pipeline": "2 batches in flight, results read back by a second host thread: the upload of step t "
-                           "overlaps the run and the read-back of step t-1"}
+               "program_words": PROGRAM_WORDS[narrow_prog],
+               "pipeline": "%d batches in flight, each on a stream of its own, results read back by a second "
+                           "host thread: uploads overlap earlier steps' runs and read-backs" % nb}
 
     cpu = None
     if rank == 0 and ws == 1 and not args.no_cpu:
@@ -722,7 +750,8 @@ def main():
                            "l2": "inputs larger than L2 (M = %.2f GiB)" % (m_bytes / 2 ** 30)
                                  if m_bytes > 129e6 else "M below L2 size (%.1f MB); no flush" % (m_bytes / 1e6),
                            "schedule_flags": args.flags, "isa": args.isa, "parallelism": "vm shards x%d" % ws,
-                           "schedule": tuned["chosen"] if tuned else "flags %#x" % args.flags},
+                           "schedule": tuned["chosen"] if tuned else "flags %#x" % args.flags,
+                           "program_words": PROGRAM_WORDS[p32 is not None]},
                 "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "plain": plain,
                 "gpu_launches": (1 + run_launches + (1 if hist else 0)) * args.steps, "clocks": clocks,
                 "outcomes": outcomes(st)}

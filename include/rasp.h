@@ -194,11 +194,16 @@ int rasp_load_programs(rasp_batch* b, const int64_t* words,
 
 /* As rasp_load_programs, for programs whose words all lie in
  * [-2^31, 2^31): the words are given as int32 and stand for the same int64
- * values (sign extension), so half as many bytes cross to the device. They
- * are copied into the batch's machine memory (which c_0 overwrites) and
- * widened there on the device once the checks have passed. Same arguments,
- * errors and c_0 as rasp_load_programs; after a failed check the batch holds
- * no programs and its machine memory is undefined until loaded again. */
+ * values (sign extension), so half as many bytes cross to the device. When
+ * the programs take at most half of mem_words words they stay on the device
+ * as 4-byte words, and every pack (this call, rasp_reset) reads them there
+ * and sign-extends them: half the program bytes per pack; the 8-byte copy is
+ * made on the device only for the shared-program schedule and the read-back
+ * of a lazily packed batch. Larger programs are copied into the batch's
+ * machine memory (which c_0 overwrites) and widened on the device once the
+ * checks have passed. Same arguments, errors and c_0 as rasp_load_programs;
+ * after a failed check the batch holds no programs and its machine memory is
+ * undefined until loaded again. */
 int rasp_load_programs_i32(rasp_batch* b, const int32_t* words,
                            const uint64_t* offsets, uint64_t num_programs,
                            const uint32_t* prog_of_vm);

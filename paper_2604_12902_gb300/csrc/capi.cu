@@ -102,6 +102,13 @@ struct rasp_batch {
   bool owns = false;
   DevState S{};
   uint64_t* d_prog = nullptr;
+  // Programs loaded as 4-byte words are kept as such in the upper half of
+  // the program area when they fit beside their widened copy: the pack
+  // reads them there, and d_prog is filled (widened) only when a kernel
+  // that reads 8-byte program words needs it (prog64_valid).
+  const int32_t* prog32 = nullptr;
+  uint64_t prog_words = 0;
+  bool prog64_valid = true;
   uint64_t* d_progoff = nullptr;
   uint32_t* d_progvm = nullptr;
   uint32_t* d_ids = nullptr;
@@ -371,10 +378,21 @@ bool pack_lazy(const rasp_batch* b) {
   return b->planned && (b->cfg.flags & RASP_SCHED_MASK) == RASP_SCHED_SHARED;
 }
 
+// The 8-byte program words of programs kept as 4-byte words, before a
+// kernel other than the pack reads them (materialize, the shared-program
+// schedule).
+cudaError_t ensure_prog64(rasp_batch* b, cudaStream_t st) {
+  if (b->prog64_valid) return cudaSuccess;
+  b->prog64_valid = true;
+  return launch_widen(b->prog32, b->d_prog, b->prog_words, st);
+}
+
 // Before anything but the shared-program kernel reads the slabs of a lazily
 // packed batch: the program words of every VM whose slab lacks them.
 cudaError_t materialize(rasp_batch* b, cudaStream_t st) {
   if (!b->code_lazy) return cudaSuccess;
+  const cudaError_t e = ensure_prog64(b, st);
+  if (e != cudaSuccess) return e;
   b->code_lazy = false;
   return launch_materialize(b->S, b->d_prog, b->d_progoff, b->shared_programs ? b->d_progvm : nullptr, b->V,
                             b->wmask, st);
@@ -627,8 +645,18 @@ int rasp::load_programs(rasp_batch* b, const void* words, int word_size, const u
   // they are in flight (the copies stay inside the batch's program area
   // whatever the offsets say). A failed check discards the programs: the
   // copy has already replaced the earlier ones.
+  //
+  // 4-byte words are kept in the upper half of the program area, at word
+  // offset h = mem_words rounded up to even (8-byte aligned), when their
+  // widened copy [0, 8 total) bytes stays below that offset (2 total <= h)
+  // and they end inside the area: the pack then reads them there and the
+  // widening waits until a kernel needs 8-byte words. Otherwise they are
+  // staged in the M arena (>= 4 total bytes, overwritten by the pack) and
+  // widened into the program area before the pack.
   cudaStream_t st = b->stream;
-  int32_t* staged = reinterpret_cast<int32_t*>(b->S.mem);   // 4-byte words: M arena (>= 4 * total bytes)
+  const uint64_t h = (b->mem_words + 1ull) & ~1ull;
+  const bool keep32 = word_size == 4 && 2ull * total <= h && 4ull * (h + total) <= 8ull * b->mem_words;
+  int32_t* staged = keep32 ? reinterpret_cast<int32_t*>(b->d_prog) + h : reinterpret_cast<int32_t*>(b->S.mem);
   if (total)
     CK(cudaMemcpyAsync(word_size == 8 ? (void*)b->d_prog : (void*)staged, words, (size_t)word_size * total,
                        cudaMemcpyHostToDevice, st));
@@ -683,11 +711,14 @@ int rasp::load_programs(rasp_batch* b, const void* words, int word_size, const u
   CK(cudaStreamSynchronize(st));   // the caller's buffers are read before the call returns
   // widening, like the pack, is left queued on the stream: it may have to
   // wait for SMs that another batch's run holds, and the host need not
-  if (word_size == 4 && total) CK(launch_widen(staged, b->d_prog, total, st));
+  b->prog32 = keep32 && total ? staged : nullptr;
+  b->prog_words = total;
+  b->prog64_valid = !b->prog32;
+  if (word_size == 4 && total && !keep32) CK(launch_widen(staged, b->d_prog, total, st));
   CK(fill_bytes(b->d_hist, 0, 8 * 10, st));
   b->code_lazy = pack_lazy(b);
-  CK(launch_pack(b->S, b->d_prog, b->d_progoff, b->shared_programs ? b->d_progvm : nullptr, b->V, b->wmask, b->sp,
-                 b->code_lazy, st));
+  CK(launch_pack(b->S, b->d_prog, b->prog32, b->d_progoff, b->shared_programs ? b->d_progvm : nullptr, b->V,
+                 b->wmask, b->sp, b->code_lazy, st));
   b->uhead_pending = false;        // the pack resets u_0
   b->programs_loaded = true;
   b->dirty_valid = true;
@@ -763,8 +794,8 @@ int rasp_reset(rasp_batch* b) {
   if (!b->programs_loaded || !b->inputs_loaded) return fail(RASP_ESTATE, "load programs and inputs first");
   CK(cudaMemsetAsync(b->d_hist, 0, 8 * 10, b->stream));
   b->code_lazy = pack_lazy(b);
-  CK(launch_pack(b->S, b->d_prog, b->d_progoff, b->shared_programs ? b->d_progvm : nullptr, b->V, b->wmask, b->sp,
-                 b->code_lazy, b->stream));
+  CK(launch_pack(b->S, b->d_prog, b->prog32, b->d_progoff, b->shared_programs ? b->d_progvm : nullptr, b->V,
+                 b->wmask, b->sp, b->code_lazy, b->stream));
   b->uhead_pending = false;
   b->dirty_valid = true;
   return RASP_OK;
@@ -819,6 +850,7 @@ int enqueue_run(rasp_batch* b, cudaStream_t st, uint64_t max_steps) {
         CK(cudaMemsetAsync(b->S.codedirty, 1, b->V, st));
         b->dirty_valid = true;
       }
+      CK(ensure_prog64(b, st));
       CK(launch_shared(var, b->S, P, b->d_prog, b->d_progoff, b->d_pvoff, b->d_pvids, b->num_programs,
                        b->max_plen, b->cfg.epoch, st));
     } else if (g.sched == RASP_SCHED_PLAIN) {
@@ -877,6 +909,8 @@ int rasp_run(rasp_batch* b, uint64_t max_steps) {
     const int rc = replan(b);
     if (rc) return rc;
   }
+  // 8-byte program words for the kernels that read them, eagerly (outside any captured graph)
+  if (b->code_lazy || (b->cfg.flags & RASP_SCHED_MASK) == RASP_SCHED_SHARED) CK(ensure_prog64(b, b->stream));
   if (!b->cap_stream) return enqueue_run(b, b->stream, max_steps);
   // CUDA graph: capture the run once per budget on a private stream, replay it on the batch stream
   cudaGraphExec_t exec = nullptr;
@@ -1123,6 +1157,7 @@ int rasp_autotune(rasp_batch* b, uint64_t max_steps, uint32_t reps) {
   if (!b->programs_loaded || !b->inputs_loaded) return fail(RASP_ESTATE, "load programs and inputs before tuning");
   if (reps == 0) reps = 1;
   CK(apply_uhead_reset(b, b->stream));
+  if (b->shared_programs || b->code_lazy) CK(ensure_prog64(b, b->stream));   // the shared-program trials
   int rc = check_device_error(b);
   if (rc) return rc;
   cudaStream_t st = b->stream;

@@ -40,7 +40,9 @@ struct PersistShape {
 
 // c_0 of every VM; with `lazy` the program words M[0, plen) are left
 // unwritten (shared-program schedule: the steps read them from the program).
-cudaError_t launch_pack(const DevState& S, const uint64_t* prog, const uint64_t* prog_off,
+// The program words are read from prog32 (4-byte words, sign-extended) when
+// it is not NULL, else from prog.
+cudaError_t launch_pack(const DevState& S, const uint64_t* prog, const int32_t* prog32, const uint64_t* prog_off,
                         const uint32_t* prog_of_vm, uint32_t num_vms, uint64_t wmask, uint32_t sp,
                         bool lazy, cudaStream_t stream);
 

@@ -29,11 +29,24 @@ constexpr uint32_t WAIT_LIMIT = 1u << 22;   // mbarrier polls before giving up (
                                            // staged kernel takes its limit as an argument)
 
 // ------------------------------------------------------------------ pack
+// Program words as the pack reads them: 8-byte words, or 4-byte words
+// (every word of the programs fits in 32 bits) sign-extended to 8 bytes.
+__device__ __forceinline__ ulonglong2 prog_pair(const uint64_t* src, uint32_t k) {
+  return *reinterpret_cast<const ulonglong2*>(src + k);
+}
+__device__ __forceinline__ uint64_t prog_word(const uint64_t* src, uint32_t k) { return src[k]; }
+__device__ __forceinline__ ulonglong2 prog_pair(const int32_t* src, uint32_t k) {
+  const int2 q = *reinterpret_cast<const int2*>(src + k);
+  return make_ulonglong2((uint64_t)(int64_t)q.x, (uint64_t)(int64_t)q.y);
+}
+__device__ __forceinline__ uint64_t prog_word(const int32_t* src, uint32_t k) { return (uint64_t)(int64_t)src[k]; }
+
 // With `lazy` (shared programs on the shared-program schedule) the program
 // words M[0, plen) are not written: the steps read them from the program
 // itself until the VM writes one of them (see ShView), so only the data
 // words are packed.
-__global__ void __launch_bounds__(256) k_pack(DevState S, const uint64_t* __restrict__ prog,
+template <class W>
+__global__ void __launch_bounds__(256) k_pack(DevState S, const W* __restrict__ prog,
                                               const uint64_t* __restrict__ prog_off,
                                               const uint32_t* __restrict__ prog_of_vm, uint32_t num_vms,
                                               uint64_t wmask, uint32_t sp, uint32_t lazy) {
@@ -43,7 +56,7 @@ __global__ void __launch_bounds__(256) k_pack(DevState S, const uint64_t* __rest
     const uint32_t p = prog_of_vm ? prog_of_vm[v] : v;
     const uint64_t po = prog_off[p];
     const uint64_t plen = prog_off[p + 1] - po;
-    const uint64_t* src = prog + po;                   // po is even: 16-byte aligned
+    const W* src = prog + po;                          // po is even: pairs are aligned
     const uint32_t npad = (S.n[v] + 1u) & ~1u;
     if (S.mem32) {
       // narrow batch (w <= 32): 4-byte words, two per 8-byte store
@@ -51,11 +64,11 @@ __global__ void __launch_bounds__(256) k_pack(DevState S, const uint64_t* __rest
       for (uint32_t k = 2u * lane; k < npad; k += 64u) {
         uint2 w;
         if (k + 1u < plen) {
-          const ulonglong2 q = *reinterpret_cast<const ulonglong2*>(src + k);
+          const ulonglong2 q = prog_pair(src, k);
           w.x = (uint32_t)(q.x & wmask);
           w.y = (uint32_t)(q.y & wmask);
         } else {
-          w.x = (k < plen) ? (uint32_t)(src[k] & wmask) : 0u;
+          w.x = (k < plen) ? (uint32_t)(prog_word(src, k) & wmask) : 0u;
           w.y = 0u;
         }
         *reinterpret_cast<uint2*>(dst + k) = w;
@@ -65,11 +78,11 @@ __global__ void __launch_bounds__(256) k_pack(DevState S, const uint64_t* __rest
     for (uint32_t k = (lazy ? (uint32_t)plen : 0u) + 2u * lane; !S.mem32 && k < npad; k += 64u) {
       ulonglong2 w;
       if (k + 1u < plen) {
-        w = *reinterpret_cast<const ulonglong2*>(src + k);
+        w = prog_pair(src, k);
         w.x &= wmask;
         w.y &= wmask;
       } else {
-        w.x = (k < plen) ? (src[k] & wmask) : 0ull;
+        w.x = (k < plen) ? (prog_word(src, k) & wmask) : 0ull;
         w.y = 0ull;
       }
       *reinterpret_cast<ulonglong2*>(dst + k) = w;
@@ -1214,7 +1227,7 @@ cudaError_t launch_widen(const int32_t* src, uint64_t* dst, uint64_t count, cuda
   return cudaGetLastError();
 }
 
-cudaError_t launch_pack(const DevState& S, const uint64_t* prog, const uint64_t* prog_off,
+cudaError_t launch_pack(const DevState& S, const uint64_t* prog, const int32_t* prog32, const uint64_t* prog_off,
                         const uint32_t* prog_of_vm, uint32_t num_vms, uint64_t wmask, uint32_t sp,
                         bool lazy, cudaStream_t stream) {
   if (!num_vms) return cudaSuccess;
@@ -1222,7 +1235,10 @@ cudaError_t launch_pack(const DevState& S, const uint64_t* prog, const uint64_t*
   uint32_t blocks = (warps_needed + 7u) / 8u;
   const uint32_t cap = (uint32_t)num_sms() * 64u;   // eight waves of resident blocks: 9 % faster than two
   if (blocks > cap) blocks = cap;
-  k_pack<<<blocks, 256, 0, stream>>>(S, prog, prog_off, prog_of_vm, num_vms, wmask, sp, lazy ? 1u : 0u);
+  if (prog32)
+    k_pack<int32_t><<<blocks, 256, 0, stream>>>(S, prog32, prog_off, prog_of_vm, num_vms, wmask, sp, lazy ? 1u : 0u);
+  else
+    k_pack<uint64_t><<<blocks, 256, 0, stream>>>(S, prog, prog_off, prog_of_vm, num_vms, wmask, sp, lazy ? 1u : 0u);
   return cudaGetLastError();
 }
 
@@ -1409,8 +1425,8 @@ int serve_configure(const StepVariant& var, ServeShape& sh) {
   // the kernels a request's admission launches while the serving kernel is
   // resident (state resets, pack, ring fill and publish) ask for the same L1/shared split,
   // so that an SM can host them beside it
-  const void* beside[] = {(const void*)fn, (const void*)k_pack, (const void*)k_ring_fill, (const void*)k_ring_publish,
-                          (const void*)k_fill};
+  const void* beside[] = {(const void*)fn, (const void*)k_pack<uint64_t>, (const void*)k_pack<int32_t>,
+                          (const void*)k_ring_fill, (const void*)k_ring_publish, (const void*)k_fill};
   for (const void* f : beside)
     cudaFuncSetAttribute(f, cudaFuncAttributePreferredSharedMemoryCarveout, (int)cudaSharedmemCarveoutMaxL1);
   cudaGetLastError();

@@ -439,20 +439,40 @@ def test_programs_loaded_as_int32_words(rasp):
     w = 64 and w = 32 (4-byte machine words), shared programs; a reset
     re-packs from the widened programs; a failed load leaves no programs."""
     R = rasp
-    cases = [(W.template_programs(num_vms=3000, seed=31), 64), (W.random_programs(num_vms=2000, seed=32), 64),
-             (W.random_programs(num_vms=2000, seed=33), 32), (W.shared_programs(num_programs=64, vms_per_program=16), 64)]
-    for wl, w in cases:
+    # Templates and shared programs fill at most half of M: their 4-byte
+    # words stay as such (the pack reads them, the 8-byte copy is made only
+    # for the shared-program kernel or a read-back of a lazily packed batch).
+    # Random programs fill all of M: widened before the pack.
+    SHARED, GRAPH = 0x40, 0x4000
+    cases = [(W.template_programs(num_vms=3000, seed=31), 64, 0), (W.template_programs(num_vms=3000, seed=34), 64, GRAPH),
+             (W.template_programs(num_vms=3000, seed=35), 32, 0),
+             (W.random_programs(num_vms=2000, seed=32), 64, 0), (W.random_programs(num_vms=2000, seed=33), 32, 0),
+             (W.shared_programs(num_programs=64, vms_per_program=16), 64, 0),
+             (W.shared_programs(num_programs=64, vms_per_program=16), 64, SHARED),
+             (W.shared_programs(num_programs=64, vms_per_program=16), 64, SHARED | GRAPH)]
+    for wl, w, flags in cases:
         wl.w = w
         assert np.all(np.abs(wl.programs) < (1 << 31))
         st, _ = oracle_state(wl)
-        with R.Batch(wl.mem_words, wl.ell, wl.s, word_bits=w) as b:
+        with R.Batch(wl.mem_words, wl.ell, wl.s, word_bits=w, flags=flags) as b:
             R.rasp_load_programs_i32(b.h, wl.programs.astype(np.int32), wl.prog_off, wl.prog_of_vm)
             b.load_inputs(wl.tapes, wl.tape_off, wl.caps)
+            if flags & SHARED:
+                b.run(20)                 # lazily packed: the read-back fills in the program words
+                mid = b.read_state()
+                assert mid["steps"].max() == 20
             b.run()
-            assert_same_state(b.read_state(), st, wl.ell, wl.s, what="int32 programs, %s w %d" % (wl.name, w))
+            what = "int32 programs, %s w %d flags %#x" % (wl.name, w, flags)
+            assert_same_state(b.read_state(), st, wl.ell, wl.s, what=what)
             b.reset()
             b.run()
-            assert_same_state(b.read_state(), st, wl.ell, wl.s, what="int32 programs after reset, %s" % wl.name)
+            assert_same_state(b.read_state(), st, wl.ell, wl.s, what="after reset, " + what)
+            if wl.prog_of_vm is not None:
+                b.reset()
+                rep = b.autotune(reps=1)  # the shared-program trial reads the 8-byte words
+                assert "shared" in [t["schedule"] for t in rep["trials"]]
+                b.run()
+                assert_same_state(b.read_state(), st, wl.ell, wl.s, what="after autotune, " + what)
             bad = wl.prog_off.copy()
             bad[1] = 3
             with pytest.raises(R.RaspError):

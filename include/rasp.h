@@ -280,8 +280,7 @@ int rasp_top_halting(rasp_batch* b, uint32_t k, uint64_t* steps_out, uint32_t* v
  * this batch from its current state with the
  * given step budget, `reps` times each, restoring the state after every
  * trial, then adopts the fastest for later rasp_run calls (replacing any
- * schedule flag of the config; the one-step staged form adds
- * RASP_STEP_BLOCK). The machine state is left unchanged.
+ * schedule flag of the config). The machine state is left unchanged.
  * Allocates a temporary snapshot of the state (ENOMEM if it does not fit).
  * Synchronises the stream. The trial times appear in rasp_describe.
  * With more than one memory-size bucket a second pass follows (coordinate

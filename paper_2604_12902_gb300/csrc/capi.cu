@@ -137,6 +137,7 @@ struct rasp_batch {
   uint32_t max_plen = 0;
   bool dirty_valid = false;    // codedirty is up to date (only the shared kernel tracks it)
   bool code_lazy = false;      // slabs of VMs with codedirty = 0 lack their program words (lazy pack)
+  bool tuned_block = false;    // autotuned: the SMEM-staged schedule one step at a time
   bool narrow = false;         // M in 4-byte words (w <= 32)
   bool uhead_pending = false;  // u_0 = 0 owed since rasp_load_inputs (done by the pack or before the next use)
   bool ids_uploaded = false;   // d_ids holds h_ids
@@ -277,7 +278,9 @@ void plan_buckets(rasp_batch* b) {
     sh.ncap = k.ncap;
     sh.slot_words = slot;
     sh.epoch = cfg_epoch ? cfg_epoch : 32u;
-    sh.block = own && b->over[bi].block;
+    // the one-step form of an autotuned staged plan; a bucket too large for
+    // shared memory keeps the HBM-slab loop
+    sh.block = (own ? b->over[bi].block : b->tuned_block) && sched == RASP_SCHED_PERSIST;
     if (sched == RASP_SCHED_PERSIST) {
       sh.staged = true;
       sh.warps = 1;
@@ -1234,7 +1237,8 @@ int rasp_autotune(rasp_batch* b, uint64_t max_steps, uint32_t reps) {
     return RASP_OK;
   };
   auto adopt = [&](rasp_config& c, const Cand& k) {
-    c.flags = (saved.flags & ~RASP_SCHED_MASK) | k.sched | (k.block ? RASP_STEP_BLOCK : 0u);
+    c.flags = (saved.flags & ~RASP_SCHED_MASK) | k.sched;
+    b->tuned_block = k.block;
     c.epoch = k.epoch;
     c.warps_per_cta = k.warps;
     c.ctas_per_sm = k.ctas;
@@ -1257,6 +1261,7 @@ int rasp_autotune(rasp_batch* b, uint64_t max_steps, uint32_t reps) {
   }
   rep += "]";
   b->cfg = saved;
+  b->tuned_block = false;
   if (best_k >= 0) adopt(b->cfg, cands[best_k]);
   // Per-bucket pass (coordinate descent over the memory-size buckets): with
   // every other bucket on its current choice, each bucket tries the other

@@ -1,7 +1,7 @@
 // kernels.cu -- sm_103a kernels of the batched word-RASP engine.
 //
 //   k_pack     c_0(P, x) for every VM (Sec. 2.1): M = P 0^(n-2m), y = 0,
-//              i = a = steps = u_0 = y_0 = 0. One warp per VM, 16-byte stores.
+//              i = a = steps = u_0 = y_0 = 0. One warp per 32 VMs, 16-byte stores.
 //   k_plain    the plain form: one thread per VM, state in HBM, each VM run
 //              until it stops, one launch per batch.
 //   k_persist  persistent workers (cf. the striped workers of App. A,
@@ -45,6 +45,13 @@ __device__ __forceinline__ uint64_t prog_word(const int32_t* src, uint32_t k) { 
 // words M[0, plen) are not written: the steps read them from the program
 // itself until the VM writes one of them (see ShView), so only the data
 // words are packed.
+//
+// A warp packs chunks of 32 consecutive VMs. Each lane first fetches the
+// layout of one VM of the chunk (program offset and length, n, slab
+// offset) and resets that VM's registers, so that the chunk's dependent
+// layout loads take one round trip and the register and y stores are
+// coalesced; then the warp writes the chunk's slabs one VM at a time, with
+// 16-byte stores.
 template <class W>
 __global__ void __launch_bounds__(256) k_pack(DevState S, const W* __restrict__ prog,
                                               const uint64_t* __restrict__ prog_off,
@@ -52,44 +59,19 @@ __global__ void __launch_bounds__(256) k_pack(DevState S, const W* __restrict__ 
                                               uint64_t wmask, uint32_t sp, uint32_t lazy) {
   const uint32_t lane = threadIdx.x & 31u;
   const uint32_t warps = (gridDim.x * blockDim.x) >> 5;
-  for (uint32_t v = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; v < num_vms; v += warps) {
-    const uint32_t p = prog_of_vm ? prog_of_vm[v] : v;
-    const uint64_t po = prog_off[p];
-    const uint64_t plen = prog_off[p + 1] - po;
-    const W* src = prog + po;                          // po is even: pairs are aligned
-    const uint32_t npad = (S.n[v] + 1u) & ~1u;
-    if (S.mem32) {
-      // narrow batch (w <= 32): 4-byte words, two per 8-byte store
-      uint32_t* dst = S.mem32 + S.mem_off[v];
-      for (uint32_t k = 2u * lane; k < npad; k += 64u) {
-        uint2 w;
-        if (k + 1u < plen) {
-          const ulonglong2 q = prog_pair(src, k);
-          w.x = (uint32_t)(q.x & wmask);
-          w.y = (uint32_t)(q.y & wmask);
-        } else {
-          w.x = (k < plen) ? (uint32_t)(prog_word(src, k) & wmask) : 0u;
-          w.y = 0u;
-        }
-        *reinterpret_cast<uint2*>(dst + k) = w;
-      }
-    }
-    uint64_t* dst = S.mem + S.mem_off[v];
-    for (uint32_t k = (lazy ? (uint32_t)plen : 0u) + 2u * lane; !S.mem32 && k < npad; k += 64u) {
-      ulonglong2 w;
-      if (k + 1u < plen) {
-        w = prog_pair(src, k);
-        w.x &= wmask;
-        w.y &= wmask;
-      } else {
-        w.x = (k < plen) ? (prog_word(src, k) & wmask) : 0ull;
-        w.y = 0ull;
-      }
-      *reinterpret_cast<ulonglong2*>(dst + k) = w;
-    }
-    uint64_t* Y = S.y + (uint64_t)v * sp;
-    for (uint32_t k = lane; k < sp; k += 32u) Y[k] = 0ull;
-    if (lane == 0) {
+  const uint32_t chunks = (num_vms + 31u) >> 5;
+  for (uint32_t c = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; c < chunks; c += warps) {
+    const uint32_t v0 = c << 5;
+    const uint32_t cnt = min(32u, num_vms - v0);
+    const uint32_t v = v0 + lane;
+    uint64_t po_l = 0, plen_l = 0, mo_l = 0;
+    uint32_t npad_l = 0;
+    if (lane < cnt) {
+      const uint32_t p = prog_of_vm ? prog_of_vm[v] : v;
+      po_l = prog_off[p];
+      plen_l = prog_off[p + 1] - po_l;
+      npad_l = (S.n[v] + 1u) & ~1u;
+      mo_l = S.mem_off[v];
       S.i[v] = 0;
       S.a[v] = 0;
       S.steps[v] = 0;
@@ -97,6 +79,45 @@ __global__ void __launch_bounds__(256) k_pack(DevState S, const W* __restrict__ 
       S.uhead[v] = 0;
       S.ylen[v] = 0;
       if (S.codedirty) S.codedirty[v] = 0;
+    }
+    uint64_t* Y = S.y + (uint64_t)v0 * sp;             // the chunk's outputs are one range
+    for (uint32_t k = lane; k < cnt * sp; k += 32u) Y[k] = 0ull;
+    for (uint32_t j = 0; j < cnt; ++j) {
+      const uint64_t po = __shfl_sync(FULL, po_l, j);
+      const uint64_t plen = __shfl_sync(FULL, plen_l, j);
+      const uint32_t npad = __shfl_sync(FULL, npad_l, j);
+      const uint64_t mo = __shfl_sync(FULL, mo_l, j);
+      const W* src = prog + po;                        // po is even: pairs are aligned
+      if (S.mem32) {
+        // narrow batch (w <= 32): 4-byte words, two per 8-byte store
+        uint32_t* dst = S.mem32 + mo;
+        for (uint32_t k = 2u * lane; k < npad; k += 64u) {
+          uint2 w;
+          if (k + 1u < plen) {
+            const ulonglong2 q = prog_pair(src, k);
+            w.x = (uint32_t)(q.x & wmask);
+            w.y = (uint32_t)(q.y & wmask);
+          } else {
+            w.x = (k < plen) ? (uint32_t)(prog_word(src, k) & wmask) : 0u;
+            w.y = 0u;
+          }
+          *reinterpret_cast<uint2*>(dst + k) = w;
+        }
+        continue;
+      }
+      uint64_t* dst = S.mem + mo;
+      for (uint32_t k = (lazy ? (uint32_t)plen : 0u) + 2u * lane; k < npad; k += 64u) {
+        ulonglong2 w;
+        if (k + 1u < plen) {
+          w = prog_pair(src, k);
+          w.x &= wmask;
+          w.y &= wmask;
+        } else {
+          w.x = (k < plen) ? (prog_word(src, k) & wmask) : 0ull;
+          w.y = 0ull;
+        }
+        *reinterpret_cast<ulonglong2*>(dst + k) = w;
+      }
     }
   }
 }
@@ -1231,9 +1252,9 @@ cudaError_t launch_pack(const DevState& S, const uint64_t* prog, const int32_t* 
                         const uint32_t* prog_of_vm, uint32_t num_vms, uint64_t wmask, uint32_t sp,
                         bool lazy, cudaStream_t stream) {
   if (!num_vms) return cudaSuccess;
-  const uint32_t warps_needed = num_vms;
+  const uint32_t warps_needed = (num_vms + 31u) / 32u;   // one warp per chunk of 32 VMs
   uint32_t blocks = (warps_needed + 7u) / 8u;
-  const uint32_t cap = (uint32_t)num_sms() * 64u;   // eight waves of resident blocks: 9 % faster than two
+  const uint32_t cap = (uint32_t)num_sms() * 64u;   // up to eight waves of resident blocks
   if (blocks > cap) blocks = cap;
   if (prog32)
     k_pack<int32_t><<<blocks, 256, 0, stream>>>(S, prog32, prog_off, prog_of_vm, num_vms, wmask, sp, lazy ? 1u : 0u);

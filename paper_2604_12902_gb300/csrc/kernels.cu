@@ -1,7 +1,7 @@
 // kernels.cu -- sm_103a kernels of the batched word-RASP engine.
 //
 //   k_pack     c_0(P, x) for every VM (Sec. 2.1): M = P 0^(n-2m), y = 0,
-//              i = a = steps = u_0 = y_0 = 0. One warp per 32 VMs, 16-byte stores.
+//              i = a = steps = u_0 = y_0 = 0. One warp per chunk of VMs, 16-byte stores.
 //   k_plain    the plain form: one thread per VM, state in HBM, each VM run
 //              until it stops, one launch per batch.
 //   k_persist  persistent workers (cf. the striped workers of App. A,
@@ -46,23 +46,23 @@ __device__ __forceinline__ uint64_t prog_word(const int32_t* src, uint32_t k) { 
 // itself until the VM writes one of them (see ShView), so only the data
 // words are packed.
 //
-// A warp packs chunks of 32 consecutive VMs. Each lane first fetches the
-// layout of one VM of the chunk (program offset and length, n, slab
-// offset) and resets that VM's registers, so that the chunk's dependent
-// layout loads take one round trip and the register and y stores are
-// coalesced; then the warp writes the chunk's slabs one VM at a time, with
-// 16-byte stores.
+// A warp packs chunks of cl consecutive VMs (cl a power of two <= 32). Each
+// lane below cl first fetches the layout of one VM of the chunk (program
+// offset and length, n, slab offset) and resets that VM's registers, so
+// that the chunk's dependent layout loads take one round trip and the
+// register and y stores are coalesced; then the warp writes the chunk's
+// slabs one VM at a time, with 16-byte stores.
 template <class W>
 __global__ void __launch_bounds__(256) k_pack(DevState S, const W* __restrict__ prog,
                                               const uint64_t* __restrict__ prog_off,
                                               const uint32_t* __restrict__ prog_of_vm, uint32_t num_vms,
-                                              uint64_t wmask, uint32_t sp, uint32_t lazy) {
+                                              uint64_t wmask, uint32_t sp, uint32_t lazy, uint32_t cl) {
   const uint32_t lane = threadIdx.x & 31u;
   const uint32_t warps = (gridDim.x * blockDim.x) >> 5;
-  const uint32_t chunks = (num_vms + 31u) >> 5;
+  const uint32_t chunks = (num_vms + cl - 1u) / cl;
   for (uint32_t c = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; c < chunks; c += warps) {
-    const uint32_t v0 = c << 5;
-    const uint32_t cnt = min(32u, num_vms - v0);
+    const uint32_t v0 = c * cl;
+    const uint32_t cnt = min(cl, num_vms - v0);
     const uint32_t v = v0 + lane;
     uint64_t po_l = 0, plen_l = 0, mo_l = 0;
     uint32_t npad_l = 0;
@@ -1252,14 +1252,21 @@ cudaError_t launch_pack(const DevState& S, const uint64_t* prog, const int32_t* 
                         const uint32_t* prog_of_vm, uint32_t num_vms, uint64_t wmask, uint32_t sp,
                         bool lazy, cudaStream_t stream) {
   if (!num_vms) return cudaSuccess;
-  const uint32_t warps_needed = (num_vms + 31u) / 32u;   // one warp per chunk of 32 VMs
+  // chunks of cl VMs per warp: 32, or fewer while that leaves under four
+  // waves of chunks for the resident warps (small batches keep every SM busy)
+  const uint32_t resident = (uint32_t)num_sms() * 64u;
+  uint32_t cl = 32u;
+  while (cl > 1u && num_vms / cl < 4u * resident) cl >>= 1;
+  const uint32_t warps_needed = (num_vms + cl - 1u) / cl;
   uint32_t blocks = (warps_needed + 7u) / 8u;
   const uint32_t cap = (uint32_t)num_sms() * 64u;   // up to eight waves of resident blocks
   if (blocks > cap) blocks = cap;
   if (prog32)
-    k_pack<int32_t><<<blocks, 256, 0, stream>>>(S, prog32, prog_off, prog_of_vm, num_vms, wmask, sp, lazy ? 1u : 0u);
+    k_pack<int32_t><<<blocks, 256, 0, stream>>>(S, prog32, prog_off, prog_of_vm, num_vms, wmask, sp, lazy ? 1u : 0u,
+                                                cl);
   else
-    k_pack<uint64_t><<<blocks, 256, 0, stream>>>(S, prog, prog_off, prog_of_vm, num_vms, wmask, sp, lazy ? 1u : 0u);
+    k_pack<uint64_t><<<blocks, 256, 0, stream>>>(S, prog, prog_off, prog_of_vm, num_vms, wmask, sp, lazy ? 1u : 0u,
+                                                 cl);
   return cudaGetLastError();
 }
 

@@ -53,3 +53,27 @@ def test_algorithmic_bytes_per_opcode():
     want = 16 * 10 + 24 * 20 + 24 * 30 + 24 * 40 + 16 * 50 + 32 * 60 + 32 * 65 + 24 * 5
     assert bench.algorithmic_bytes(st) == want
     assert bench.algorithmic_bytes(st, fetch_from_smem=True) == want - 16 * sum(ops)
+
+
+def test_program_words_go_up_as_int32_only_when_every_word_fits():
+    """bench.py uploads programs through rasp_load_programs_i32 only when
+    every word lies in [-2^31, 2^31) (the int32 values then stand for the
+    same int64 words); the run kernel name follows the autotuner's report."""
+    import numpy as np
+    import bench
+    from paper_2604_12902_gb300 import workloads as W
+    wl = W.template_programs(num_vms=64, seed=2)
+    assert bench.programs_fit_int32(wl)
+    assert np.array_equal(wl.programs.astype(np.int32).astype(np.int64), wl.programs)
+    for big in (1 << 31, -(1 << 31) - 1):
+        wl2 = W.template_programs(num_vms=64, seed=2)
+        wl2.programs = wl2.programs.copy()
+        wl2.programs[1] = big
+        assert not bench.programs_fit_int32(wl2)
+    wl3 = W.template_programs(num_vms=64, seed=2)
+    wl3.programs = wl3.programs.copy()
+    wl3.programs[1], wl3.programs[3] = (1 << 31) - 1, -(1 << 31)
+    assert bench.programs_fit_int32(wl3)
+    assert bench.run_kernel_name("persist_smem e32 w1 step", 0) == "k_persist"
+    assert bench.run_kernel_name("persist_gl e256 w4", 0) == "k_persist_gl"
+    assert bench.run_kernel_name("shared", 0x20000) == "k_shared"

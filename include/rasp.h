@@ -304,8 +304,12 @@ int rasp_plan_bucket(rasp_batch* b, uint32_t bucket, uint32_t sched, uint32_t ep
 
 /* Describe the launch plan as JSON into buf (NUL-terminated): per memory
  * bucket its size class, VM count, schedule, grid, warps per CTA, resident
- * CTAs per SM, shared memory, epoch and refill threshold. EINVAL if buf is
- * too small. Does not touch the GPU. */
+ * CTAs per SM, shared memory, epoch and refill threshold; the launches of a
+ * run; the bytes of a word of M ("word_bytes": 4 for w <= 32 on the plain
+ * and HBM-slab schedules, else 8) and of a program word as the pack reads it
+ * ("program_word_bytes": 4 for programs kept as loaded by
+ * rasp_load_programs_i32, else 8); whether runs replay a CUDA graph; the
+ * autotuner's report. EINVAL if buf is too small. Does not touch the GPU. */
 int rasp_describe(const rasp_batch* b, char* buf, uint64_t size);
 
 /* ---- running a caller-owned state store without allocating ---------------

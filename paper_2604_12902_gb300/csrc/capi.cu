@@ -1386,6 +1386,8 @@ int rasp_describe(const rasp_batch* b, char* buf, uint64_t size) {
   }
   s += "], \"word_bytes\": ";
   s += b->narrow ? "4" : "8";
+  s += ", \"program_word_bytes\": ";      // how the pack reads the loaded programs
+  s += b->prog32 ? "4" : "8";
   s += ", \"cuda_graph\": ";
   s += b->cap_stream ? "true" : "false";
   s += ", \"autotune\": ";

@@ -442,7 +442,8 @@ def test_programs_loaded_as_int32_words(rasp):
     # Templates and shared programs fill at most half of M: their 4-byte
     # words stay as such (the pack reads them, the 8-byte copy is made only
     # for the shared-program kernel or a read-back of a lazily packed batch).
-    # Random programs fill all of M: widened before the pack.
+    # Random programs fill all of M: widened before the pack. rasp_describe
+    # reports which.
     SHARED, GRAPH = 0x40, 0x4000
     cases = [(W.template_programs(num_vms=3000, seed=31), 64, 0), (W.template_programs(num_vms=3000, seed=34), 64, GRAPH),
              (W.template_programs(num_vms=3000, seed=35), 32, 0),
@@ -457,6 +458,8 @@ def test_programs_loaded_as_int32_words(rasp):
         with R.Batch(wl.mem_words, wl.ell, wl.s, word_bits=w, flags=flags) as b:
             R.rasp_load_programs_i32(b.h, wl.programs.astype(np.int32), wl.prog_off, wl.prog_of_vm)
             b.load_inputs(wl.tapes, wl.tape_off, wl.caps)
+            kept = 2 * int(wl.prog_off[-1]) <= int(((wl.mem_words.astype(np.uint64) + 1) // 2 * 2).sum())
+            assert b.describe()["program_word_bytes"] == (4 if kept else 8), wl.name
             if flags & SHARED:
                 b.run(20)                 # lazily packed: the read-back fills in the program words
                 mid = b.read_state()
